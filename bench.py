@@ -1,0 +1,385 @@
+"""Benchmark: time-resolved path tracing on GB300 (arXiv 2510.25660).
+
+One step = one transient render of the large static scene (1.16M triangles,
+512x512 pixels, T = 2048 bins of 0.005 m, 256 spp, max_depth 8, NEE + MIS),
+through the C ABI, with the scene resident in HBM.  Prints one JSON line:
+value = path vertices/s (whole job), roofline of the render kernel, e2e
+through host buffers, the oracle timed on the host cores as cpu_baseline,
+and secondary figures (backward grads/s on the differentiable scene, batched
+NLOS connections/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+WORKLOAD = "large static scene: 1,164,296-triangle fBm heightfield + 200 icospheres, 4 area lights, " \
+           "512x512 px, T=2048 bins x 0.005 m from 12 m, 256 spp, max_depth 8, NEE+MIS, FP32 film"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_25660_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel_hash):
+    """dram bytes per launch of the render kernel from the committed ncu summary,
+    or None if the kernel sources changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "k_render_large_scene.json")
+    if not os.path.exists(p):
+        return None, None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash:
+        return None, d.get("kernel_hash")
+    return d.get("dram_bytes_per_launch"), d.get("kernel_hash")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(sc, film_spec, spp, depth, budget_s=15.0):
+    """The oracle as it stands, single-threaded on this host, on a centred pixel
+    crop of the same workload at full spp and depth (bounded to ~budget_s)."""
+    from oracle import oracle as O
+    O.build()
+    osc = O.OracleScene(sc)
+    f = film_spec
+    cx, cy = f.W // 2, f.H // 2
+    total_v, total_t, px = 0, 0.0, 0
+    side = 1
+    while total_t < budget_s and side <= 16:
+        crop = (cx - (side + 1) // 2, cx - (side + 1) // 2 + side, cy + 8 * side, cy + 8 * side + side)
+        t0 = time.perf_counter()
+        r = osc.render(f.H, f.W, 16, f.start_opl, f.bin_width, spp, 25660, depth, crop=crop)
+        dt = time.perf_counter() - t0
+        total_v += r["counters"]["vertices"]
+        total_t += dt
+        px += side * side
+        if dt < budget_s / 8:
+            side *= 2
+    return {"value": total_v / total_t, "unit": "path vertices/s", "cores": 1, "kind": "oracle",
+            "sample": f"{px} pixels of the 512x512 frame (central crops) x {spp} spp, max_depth {depth}, "
+                      f"FP64 single-threaded, {total_t:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2510_25660_gb300 import scenes
+    sc = scenes.large_scene()
+    f = scenes.LARGE_FILM
+    from oracle import oracle as O
+    O.build()
+    osc = O.OracleScene(sc)
+    spp, depth = 256, 8
+    times, verts = [], []
+    cx, cy = f.W // 2, f.H // 2
+    for k in range(args.warmup + args.steps):
+        crop = (cx + 4 * k, cx + 4 * k + 2, cy, cy + 1)   # 2 pixels x 256 spp per step
+        t0 = time.perf_counter()
+        r = osc.render(f.H, f.W, 16, f.start_opl, f.bin_width, spp, 25660, depth, crop=crop)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            verts.append(r["counters"]["vertices"])
+    v = sum(verts) / sum(times)
+    line = {"impl": "reference", "metric": "time-resolved path vertices/s", "value": v, "unit": "path vertices/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "2 pixels x 256 spp per step"},
+            "cpu_baseline": {"value": v, "unit": "path vertices/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of 2 central pixels x 256 spp, max_depth 8, FP64"},
+            "e2e": {"value": v, "unit": "path vertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2510_25660_gb300 import api, autotune, scenes
+    from paper_2510_25660_gb300 import build as b
+    if rank == 0 or ws == 1:
+        b.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    api.load()
+
+    sc = scenes.large_scene()
+    f = scenes.LARGE_FILM
+    spp, depth, seed = 256, 8, scenes.RENDER_SEED
+    s = api.Scene(sc)
+    autotune.apply(s, "render", sc, f, spp, depth)
+    film, steady = api.new_film(f.H, f.W, f.T)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, spp, seed, depth, out=(film, steady))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    s.sync()
+    # algorithmic traffic per launch from the counters of one identical launch
+    s.read_counters(reset=True)
+    api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, spp, seed, depth, flags=api.MT_COUNTERS,
+               out=(film, steady))
+    cnt = s.read_counters(reset=True)
+    s.sync()
+    film_bytes = film.numel() * 4 + steady.numel() * 4
+    alg_bytes = cnt["node_visits"] * 32 + cnt["tri_tests"] * 48 + cnt["vertices"] * 32 + film_bytes
+    # timed region
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    s.read_counters(reset=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))                 # write > L2 between timed iterations
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    s.sync()
+    run_cnt = s.read_counters(reset=True)
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    total_s = sum(step_ms) / 1000.0
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        vt = torch.tensor([float(run_cnt["vertices"])], device="cuda")
+        torch.distributed.all_reduce(vt)
+        total_vertices = float(vt.item())
+    else:
+        total_vertices = float(run_cnt["vertices"])
+    value = total_vertices / total_s
+    mean_ms = 1000.0 * total_s / args.steps
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (mean_ms / 1000.0) / 1e9
+    khash = _kernel_hash()
+    traffic, _ = _traffic_from_profile(khash)
+
+    # e2e: host arrays in, film out, through the public API (scene load + render + read-back)
+    e2e = None
+    if rank == 0 or ws == 1:
+        pin = torch.empty(film.shape, dtype=torch.float32, pin_memory=True)
+        pin_s = torch.empty(steady.shape, dtype=torch.float32, pin_memory=True)
+        h2d = sc.tris.nbytes + sc.n_tris * 20 + len(sc.emitters) * 36
+        e_times, e_verts = [], 0
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = api.Scene(sc)
+            autotune.apply(s2, "render", sc, f, spp, depth)
+            api.render(s2, f.H, f.W, f.T, f.start_opl, f.bin_width, spp, seed, depth, out=(film, steady))
+            pin.copy_(film, non_blocking=True)
+            pin_s.copy_(steady, non_blocking=True)
+            torch.cuda.synchronize()
+            e_times.append(time.perf_counter() - t0)
+            e_verts = s2.read_counters(reset=True)["vertices"]
+            del s2
+        e2e = {"value": e_verts / min(e_times), "unit": "path vertices/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(film_bytes),
+               "note": "scene arrays from host (BVH build included) + render + film/steady read back to pinned host"}
+
+    extras = {}
+    if not args.no_extras and (rank == 0 or ws == 1):
+        extras = secondary(api, autotune, scenes)
+
+    line = {
+        "metric": "time-resolved path vertices/s on 1 GB300",
+        "value": value, "unit": "path vertices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MB buffer written between timed steps; film output "
+                         f"{film_bytes / 1e9:.2f} GB per step",
+                   "bvh": s.stats()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "per_vertex": "node visits x 32 B + triangle tests x 48 B + 32 B material/emitter per vertex "
+                                   "+ film and steady image written once",
+                     "counts": cnt, "kernel_hash": khash},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "step_ms": step_ms,
+    }
+    line.update(extras)
+    if (rank == 0 or ws == 1) and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sc, f, spp, depth)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def secondary(api, autotune, scenes):
+    """Backward grads/s on the differentiable scene and batched NLOS throughput."""
+    import torch
+    out = {}
+    # backward: 97k-triangle scene, 256x256x512 film, 64 spp, depth 8
+    sc = scenes.diff_scene()
+    f = scenes.DIFF_FILM
+    s = api.Scene(sc)
+    autotune.apply(s, "backward", sc, f, 64, 8)
+    film, steady = api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8)
+    g = torch.randn_like(film)
+    gs = torch.randn_like(steady)
+    outg = (torch.zeros((sc.n_tris, 3), device="cuda"), torch.zeros((len(sc.emitters), 3), device="cuda"),
+            torch.zeros(1, device="cuda"))
+    for _ in range(2):
+        api.render_backward(s, f.T, f.start_opl, f.bin_width, 64, 1, 8, g, gs, out=outg)
+    s.sync()
+    s.read_counters(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        api.render_backward(s, f.T, f.start_opl, f.bin_width, 64, 1, 8, g, gs, out=outg)
+    e1.record()
+    s.sync()
+    c = s.read_counters(reset=True)
+    ms = e0.elapsed_time(e1) / 3
+    fwd0, fwd1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fwd0.record()
+    for _ in range(3):
+        api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8, out=(film, steady))
+    fwd1.record()
+    s.sync()
+    out["backward"] = {"grads_per_s": c["vertices"] / 3 / (ms / 1000.0), "unit": "adjoint path vertices/s",
+                       "ms_per_backward": ms, "forward_ms": fwd0.elapsed_time(fwd1) / 3,
+                       "params_per_s": sc.n_tris * 3 / (ms / 1000.0),
+                       "workload": "97k-triangle scene, 256x256x512 film, 64 spp, max_depth 8"}
+    del s
+    # NLOS confocal 64x64 x 1024 spp, T=4096
+    sc = scenes.nlos_scene()
+    s = api.Scene(sc)
+    lasers = torch.from_numpy(scenes.wall_grid(64, 64)).cuda()
+    autotune.apply(s, "nlos", sc, None, 1024, 0)
+    nf = None
+    for _ in range(2):
+        nf = api.render_nlos(s, lasers, None, api.MT_CONFOCAL, scenes.NLOS_T, scenes.NLOS_START, scenes.NLOS_W,
+                             1024, 1, out=nf)
+    s.sync()
+    e0.record()
+    for _ in range(5):
+        nf = api.render_nlos(s, lasers, None, api.MT_CONFOCAL, scenes.NLOS_T, scenes.NLOS_START, scenes.NLOS_W,
+                             1024, 1, out=nf)
+    e1.record()
+    s.sync()
+    ms = e0.elapsed_time(e1) / 5
+    out["nlos"] = {"confocal_connections_per_s": 4096 * 1024 / (ms / 1000.0), "ms_per_capture": ms,
+                   "workload": "64x64 confocal grid x 1024 spp, T=4096 x 0.003 m, 49.4k hidden triangles, "
+                               "one graph launch"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * mt_api.h -- C ABI of libmt.so: time-resolved Monte Carlo path tracing on
+ * GB300 (sm_103a), after arXiv 2510.25660 ("mitransient").
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2 listing: load a
+ * scene, render it with a sample count and get back a steady image and a
+ * transient image; Sec. 4.4: gradients of a scalar loss in backward mode;
+ * Sec. 4.5: impulse responses over a relay-wall scan grid).
+ *
+ * Conventions
+ *   - Every function returns mt_status and never throws.  On failure
+ *     mt_last_error() returns a thread-local message valid until the next call
+ *     on the same thread.
+ *   - Argument checks run synchronously.  Kernel faults and device watchdog
+ *     timeouts surface at mt_sync() or at the next call on the stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - "host" pointers are read during the call and may be freed afterwards;
+ *     "device" pointers are CUDA device memory owned by the caller.
+ *   - Time is optical path length (OPL) in metres (speed of light c = 1,
+ *     Sec. 3 Eq. 3): time bin k covers [start + k*width, start + (k+1)*width).
+ *   - Films are row-major float32 [H][W][T][C], steady images [H][W][C].
+ *     The film holds (1/spp) * sum of contributions per bin (Sec. 3 Eq. 9 with
+ *     path reuse); with MT_ACCUMULATE it holds unnormalised sums added to its
+ *     previous contents (progressive / resumable rendering).
+ *   - Handles are not thread-safe per object; distinct handles may be used
+ *     from distinct threads.
+ */
+#ifndef MT_API_H
+#define MT_API_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MT_OK = 0,
+    MT_ERR_INVALID_ARGUMENT = 1,
+    MT_ERR_OUT_OF_MEMORY = 2,
+    MT_ERR_CUDA = 3,
+    MT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (error word set by a kernel) */
+    MT_ERR_UNSUPPORTED = 5, /* valid request outside what this build implements */
+    MT_ERR_INTERNAL = 6
+} mt_status;
+
+typedef struct mt_scene_s *mt_scene;
+typedef struct mt_film_s *mt_film;
+
+/* Material per triangle (Sec. 4.1 "complex materials").  LAMBERT: f = albedo/pi,
+ * two-sided.  GGX_CONDUCTOR: isotropic GGX with alpha = roughness, Smith
+ * height-correlated masking, Schlick Fresnel with F0 = albedo, two-sided. */
+#define MT_LAMBERT 0u
+#define MT_GGX_CONDUCTOR 1u
+typedef struct {
+    float albedo[3];
+    float roughness;
+    uint32_t type;
+} mt_material;
+
+/* Emitters (delta pulse in time at t = 0, Sec. 3 Eq. 5).  AREA: triangles
+ * [first_tri, first_tri + n_tris) emit `radiance` (RGB, W sr^-1 m^-2) from the
+ * side of their winding normal (v1-v0)x(v2-v0).  POINT: isotropic point at
+ * `position` with intensity `radiance` (W sr^-1); not hit by rays. */
+#define MT_EMITTER_AREA 0u
+#define MT_EMITTER_POINT 1u
+typedef struct {
+    uint32_t type;
+    uint32_t first_tri;
+    uint32_t n_tris;
+    float radiance[3];
+    float position[3];
+} mt_emitter;
+
+/* Pinhole camera; fov_x_deg is the horizontal field of view. */
+typedef struct {
+    float origin[3];
+    float target[3];
+    float up[3];
+    float fov_x_deg;
+} mt_camera;
+
+/* Heterogeneous participating medium filling the box [lo, hi] (Sec. 4.1,
+ * "Volumetric scattering"): extinction sigma_t (1/m) on a res[0] x res[1] x
+ * res[2] grid, host array laid out [z][y][x], sampled trilinearly with voxel
+ * centres at lo + (i + 0.5) (hi - lo) / res; scalar single-scatter albedo and
+ * Henyey-Greenstein g; index-matched (eta = 1), invisible boundary. */
+typedef struct {
+    float lo[3];
+    float hi[3];
+    int32_t res[3];
+    const float *density; /* host */
+    float albedo;
+    float g;
+} mt_medium;
+
+/* film flags */
+#define MT_UNWARP 1u       /* drop the camera segment's time of flight (Sec. 3, "Camera warp") */
+#define MT_ACCUMULATE 2u   /* add unnormalised sums into the film instead of overwriting it */
+#define MT_PIXEL_CENTER 4u /* no pixel jitter: every sample goes through the pixel centre */
+#define MT_COUNTERS 8u     /* count node visits / triangle tests / rays (slower; see mt_read_counters) */
+
+/* NLOS relay-wall scan (Sec. 4.5).  CONFOCAL: laser and sensor at the same wall
+ * point, one film row per point (n_sensors ignored).  EXHAUSTIVE: every laser
+ * against every sensor, film row = laser * n_sensors + sensor.  Paths are
+ * laser -> x_l -> y -> x_s -> sensor with y on the hidden triangles
+ * [hidden_first, hidden_first + hidden_count); time is the relay-wall clock
+ * |x_l - y| + |y - x_s|.  Points are device arrays float32 [n][3]. */
+#define MT_CONFOCAL 0u
+#define MT_EXHAUSTIVE 1u
+typedef struct {
+    const float *lasers;  /* device [n_lasers][3] */
+    int32_t n_lasers;
+    const float *sensors; /* device [n_sensors][3], EXHAUSTIVE only */
+    int32_t n_sensors;
+    uint32_t mode;
+    float wall_normal[3];
+    float wall_albedo;
+    uint32_t hidden_first;
+    uint32_t hidden_count;
+} mt_scan;
+
+/* Thread-local message of the last failing call on this thread. */
+const char *mt_last_error(void);
+
+/* Load a scene (Sec. 2 listing, "load_dict").  Copies the host arrays tris
+ * [n_tris][3][3], materials [n_tris], emitters [n_emitters], the camera and the
+ * optional medium into library-owned device memory, builds the SAH BVH and the
+ * emitter sampling table on the device, and returns a handle in *out.  The
+ * emitter table weights triangles by area * mean radiance at creation time and
+ * is kept fixed by mt_scene_set_params.  Errors: INVALID_ARGUMENT (NULL
+ * pointers, n_tris < 1, non-finite vertices, emitter ranges out of bounds),
+ * OUT_OF_MEMORY, CUDA.  Synchronises `stream`. */
+mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials,
+                          const mt_emitter *emitters, int32_t n_emitters, const mt_camera *camera,
+                          const mt_medium *medium, void *stream, mt_scene *out);
+
+/* Replace per-triangle albedos (device float32 [n_tris][3]), emitter radiances
+ * (device float32 [n_emitters][3]) and/or the medium albedo (device float32
+ * [1]); NULL leaves a parameter unchanged.  Asynchronous on `stream`. */
+mt_status mt_scene_set_params(mt_scene scene, const float *d_albedo, const float *d_radiance,
+                              const float *d_medium_albedo, void *stream);
+
+/* Describe a caller-owned film: d_film device float32 [H][W][T][C] and the
+ * optional d_steady device float32 [H][W][C] (Sec. 2 listing returns both; the
+ * steady image is the time integral including contributions outside the
+ * window, Sec. 3 "Path reuse").  C must be 3 for mt_render / mt_render_backward
+ * and 1 for mt_render_nlos.  bin_width > 0, T >= 1. */
+mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start_opl, float bin_width,
+                         float *d_film, float *d_steady, uint32_t flags, mt_film *out);
+
+/* Transient path tracing (Sec. 3, transient_path integrator): for each pixel,
+ * spp paths with samples sample_offset .. sample_offset + spp - 1 from the
+ * Philox stream keyed by `seed`, at most max_depth segments each (1 = emitters
+ * seen directly), next-event estimation with power-heuristic MIS (no MIS in a
+ * medium), every contribution splatted into the bin of its own optical path
+ * length and into the steady image.  Asynchronous on `stream`; allocates
+ * nothing.  Errors: INVALID_ARGUMENT (spp < 1, max_depth outside [1, 64],
+ * film C != 3), CUDA. */
+mt_status mt_render(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, int32_t max_depth,
+                    uint64_t sample_offset, void *stream);
+
+/* Relay-wall impulse responses H(x_l, x_s, t) for all scan pairs in one
+ * persistent launch (Sec. 4.5): spp hidden-surface samples per pair (shared by
+ * all sensors of a laser in EXHAUSTIVE mode), film rows = pairs, C = 1, H * W
+ * must equal the number of pairs.  Asynchronous; allocates nothing after the
+ * first call for a scene (scratch grows to the largest exhaustive grid seen). */
+mt_status mt_render_nlos(mt_scene scene, mt_film film, const mt_scan *scan, int32_t spp, uint64_t seed,
+                         uint64_t sample_offset, void *stream);
+
+/* Backward mode by path replay (Sec. 4.4, Eqs. 13-15): regenerate every path of
+ * mt_render(scene, film, spp, seed, max_depth, sample_offset) from its Philox
+ * key and add dL/dalbedo (device [n_tris][3]), dL/dradiance (device
+ * [n_emitters][3]) and dL/dmedium_albedo (device [1], nullable) given
+ * d_grad_film = dL/dfilm (device, film layout) and the optional d_grad_steady.
+ * Gradients are ADDED to the outputs.  Requires albedos > 0.  Asynchronous. */
+mt_status mt_render_backward(mt_scene scene, mt_film film, const float *d_grad_film,
+                             const float *d_grad_steady, int32_t spp, uint64_t seed, int32_t max_depth,
+                             uint64_t sample_offset, float *d_grad_albedo, float *d_grad_radiance,
+                             float *d_grad_medium_albedo, void *stream);
+
+/* Synchronise `stream` and report device-side errors raised since the last
+ * call (traversal stack overflow -> INTERNAL, bounded waits -> TIMEOUT). */
+mt_status mt_sync(mt_scene scene, void *stream);
+
+/* Counters accumulated by launches on this scene since the last reset:
+ * out[0] path vertices, out[1] paths, out[2] contributions, out[3] rays,
+ * out[4] node visits*, out[5] triangle tests*, out[6] splats into shared
+ * memory, out[7] splats into global memory (* only with MT_COUNTERS).
+ * Synchronises `stream`; reset != 0 zeroes them afterwards. */
+mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *stream);
+
+/* Scene statistics: out[0] n_tris, out[1] BVH internal nodes, out[2] BVH
+ * depth, out[3] SAH cost x 1000 (sum of node areas / root area, with unit
+ * traversal and intersection costs), out[4] light units, out[5] scene bytes
+ * on the device, out[6] BVH build time in microseconds. */
+mt_status mt_scene_stats(mt_scene scene, int64_t *out);
+
+/* Launch configuration used by the next renders of this scene: threads per
+ * CTA, pixels (or scan pairs) per tile, CTAs per SM (0 = occupancy maximum).
+ * Set by the autotuner; 0 keeps a field at its default. */
+mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm);
+#define MT_LAUNCH_RENDER 0
+#define MT_LAUNCH_BACKWARD 1
+#define MT_LAUNCH_NLOS 2
+
+void mt_scene_destroy(mt_scene scene);
+void mt_film_destroy(mt_film film);
+
+/* ---- parity probes: the same device code as the renderer, on fixed inputs ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters (device uint32 [n][4]) under
+ * key (seed_lo, seed_hi) into device uint32 [n][4]. */
+mt_status mt_probe_philox(uint64_t seed, const uint32_t *d_counters, int64_t n, uint32_t *d_out, void *stream);
+
+/* Closest hits of n rays (device float32 [n][6] = origin, unit direction) with
+ * t in (0, tmax): device int32 [n] triangle index (-1 = miss, ties to the
+ * smaller index) and device float32 [n] distance.  any_hit != 0 instead writes
+ * 1/0 occlusion into d_tri. */
+mt_status mt_probe_trace(mt_scene scene, const float *d_rays, int64_t n, float tmax, int32_t any_hit,
+                         int32_t *d_tri, float *d_t, void *stream);
+
+/* Time-bin index floor((opl - start) / width) of n optical path lengths
+ * (device float32 [n]) into device int32 [n], -1 outside [0, T). */
+mt_status mt_probe_bins(const float *d_opl, int64_t n, float start, float width, int32_t T, int32_t *d_bin,
+                        void *stream);
+
+/* One contribution record of the per-path dump. */
+typedef struct {
+    int32_t pixel, sample, depth, kind, tri, bin;
+    float opl;
+    float c[3];
+} mt_contrib;
+
+/* mt_render, additionally writing every contribution (kind 0 = emission found
+ * by the path, 1 = next-event estimate, 2 = NLOS connection) into d_dump
+ * (capacity `cap`); *d_count (device int64) receives the total number of
+ * contributions, which may exceed cap.  For NLOS pass a scan (non-NULL). */
+mt_status mt_render_dump(mt_scene scene, mt_film film, const mt_scan *scan, int32_t spp, uint64_t seed,
+                         int32_t max_depth, uint64_t sample_offset, mt_contrib *d_dump, int64_t cap,
+                         int64_t *d_count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

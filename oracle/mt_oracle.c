@@ -56,6 +56,11 @@ void mo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void mo_philox_batch(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; i++) mo_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 /* four uniforms in [0,1) from counter (a, b, c, d): top 24 bits * 2^-24 */
 static void rng4(uint64_t seed, uint32_t a, uint32_t b, uint32_t c, uint32_t d, double u[4]) {
     uint32_t ctr[4] = {a, b, c, d}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, o[4];

@@ -78,6 +78,7 @@ void mo_scene_destroy(mo_scene *s);
 void mo_scene_set_params(mo_scene *s, const double *albedo, const double *radiance, double medium_albedo);
 
 void mo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void mo_philox_batch(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out);
 
 int64_t mo_intersect(const mo_scene *s, const double *o, const double *d, double tmax, int brute,
                      double *t_out);

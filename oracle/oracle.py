@@ -68,6 +68,7 @@ def lib():
         _lib.mo_scene_destroy.argtypes = [P]
         _lib.mo_scene_set_params.argtypes = [P, P, P, C.c_double]
         _lib.mo_philox4x32_10.argtypes = [P, P, P]
+        _lib.mo_philox_batch.argtypes = [P, C.c_int64, C.c_uint64, P]
         _lib.mo_intersect.restype = C.c_int64
         _lib.mo_intersect.argtypes = [P, P, P, C.c_double, C.c_int, P]
         _lib.mo_occluded.restype = C.c_int
@@ -107,6 +108,14 @@ def philox(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, np.uint32)
     o = np.zeros(4, np.uint32)
     lib().mo_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def philox_batch(ctr, seed) -> np.ndarray:
+    """Philox4x32-10 of n counters [n, 4] under key (seed_lo, seed_hi)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    o = np.zeros_like(c)
+    lib().mo_philox_batch(_p(c), c.shape[0], int(seed), _p(o))
     return o
 
 

@@ -1,0 +1,438 @@
+"""ctypes binding of libmt.so (the C ABI in include/mt_api.h).
+
+Argument marshalling only: torch tensors supply device memory and the current
+CUDA stream; every step of the rendering path runs in libmt's kernels.  The
+functions ``mt_*`` mirror the C entry points one to one; ``Scene``,
+``render``, ``render_nlos``, ``render_backward`` and ``TransientRender`` are
+thin conveniences over them.  There is no fallback: if libmt.so is missing
+or no CUDA device is present, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import scenes as _scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmt.so")
+
+MT_OK, MT_ERR_INVALID_ARGUMENT, MT_ERR_OUT_OF_MEMORY, MT_ERR_CUDA, MT_ERR_TIMEOUT, MT_ERR_UNSUPPORTED, \
+    MT_ERR_INTERNAL = range(7)
+MT_LAMBERT, MT_GGX_CONDUCTOR = 0, 1
+MT_EMITTER_AREA, MT_EMITTER_POINT = 0, 1
+MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
+MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
+MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
+STATUS_NAMES = ["MT_OK", "MT_ERR_INVALID_ARGUMENT", "MT_ERR_OUT_OF_MEMORY", "MT_ERR_CUDA", "MT_ERR_TIMEOUT",
+                "MT_ERR_UNSUPPORTED", "MT_ERR_INTERNAL"]
+
+
+class mt_material(C.Structure):
+    _fields_ = [("albedo", C.c_float * 3), ("roughness", C.c_float), ("type", C.c_uint32)]
+
+
+class mt_emitter(C.Structure):
+    _fields_ = [("type", C.c_uint32), ("first_tri", C.c_uint32), ("n_tris", C.c_uint32),
+                ("radiance", C.c_float * 3), ("position", C.c_float * 3)]
+
+
+class mt_camera(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_x_deg", C.c_float)]
+
+
+class mt_medium(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("res", C.c_int32 * 3), ("density", C.c_void_p),
+                ("albedo", C.c_float), ("g", C.c_float)]
+
+
+class mt_scan(C.Structure):
+    _fields_ = [("lasers", C.c_void_p), ("n_lasers", C.c_int32), ("sensors", C.c_void_p), ("n_sensors", C.c_int32),
+                ("mode", C.c_uint32), ("wall_normal", C.c_float * 3), ("wall_albedo", C.c_float),
+                ("hidden_first", C.c_uint32), ("hidden_count", C.c_uint32)]
+
+
+class mt_contrib(C.Structure):
+    _fields_ = [("pixel", C.c_int32), ("sample", C.c_int32), ("depth", C.c_int32), ("kind", C.c_int32),
+                ("tri", C.c_int32), ("bin", C.c_int32), ("opl", C.c_float), ("c", C.c_float * 3)]
+
+
+CONTRIB_DTYPE = np.dtype([("pixel", np.int32), ("sample", np.int32), ("depth", np.int32), ("kind", np.int32),
+                          ("tri", np.int32), ("bin", np.int32), ("opl", np.float32), ("c", np.float32, (3,))])
+
+# name -> (restype, argtypes)
+_P, _I32, _I64, _U32, _U64, _F = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float
+SIGNATURES = {
+    "mt_last_error": (C.c_char_p, []),
+    "mt_scene_create": (C.c_int, [_P, _I64, _P, _P, _I32, _P, _P, _P, _P]),
+    "mt_scene_set_params": (C.c_int, [_P, _P, _P, _P, _P]),
+    "mt_film_create": (C.c_int, [_I32, _I32, _I32, _I32, _F, _F, _P, _P, _U32, _P]),
+    "mt_render": (C.c_int, [_P, _P, _I32, _U64, _I32, _U64, _P]),
+    "mt_render_nlos": (C.c_int, [_P, _P, _P, _I32, _U64, _U64, _P]),
+    "mt_render_backward": (C.c_int, [_P, _P, _P, _P, _I32, _U64, _I32, _U64, _P, _P, _P, _P]),
+    "mt_sync": (C.c_int, [_P, _P]),
+    "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
+    "mt_scene_stats": (C.c_int, [_P, _P]),
+    "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "mt_scene_destroy": (None, [_P]),
+    "mt_film_destroy": (None, [_P]),
+    "mt_probe_philox": (C.c_int, [_U64, _P, _I64, _P, _P]),
+    "mt_probe_trace": (C.c_int, [_P, _P, _I64, _F, _I32, _P, _P, _P]),
+    "mt_probe_bins": (C.c_int, [_P, _I64, _F, _F, _I32, _P, _P]),
+    "mt_render_dump": (C.c_int, [_P, _P, _P, _I32, _U64, _I32, _U64, _P, _I64, _P, _P]),
+}
+
+_lib = None
+
+
+class MtError(RuntimeError):
+    def __init__(self, status, name, msg):
+        super().__init__(f"{name}: {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libmt.so (no build, no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmt.so not built at {path}; run paper_2510_25660_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _call(name, *args):
+    rc = getattr(load(), name)(*args)
+    if rc != MT_OK:
+        raise MtError(rc, name, load().mt_last_error().decode())
+    return rc
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+# --- mirrors of the C entry points ---------------------------------------------
+def mt_last_error() -> str:
+    return load().mt_last_error().decode()
+
+
+def mt_scene_create(tris, n_tris, materials, emitters, n_emitters, camera, medium, stream, out):
+    return _call("mt_scene_create", tris, n_tris, materials, emitters, n_emitters, camera, medium, stream, out)
+
+
+def mt_scene_set_params(scene, d_albedo, d_radiance, d_medium_albedo, stream):
+    return _call("mt_scene_set_params", scene, d_albedo, d_radiance, d_medium_albedo, stream)
+
+
+def mt_film_create(H, W, T, Cc, start, width, d_film, d_steady, flags, out):
+    return _call("mt_film_create", H, W, T, Cc, start, width, d_film, d_steady, flags, out)
+
+
+def mt_render(scene, film, spp, seed, max_depth, sample_offset, stream):
+    return _call("mt_render", scene, film, spp, seed, max_depth, sample_offset, stream)
+
+
+def mt_render_nlos(scene, film, scan, spp, seed, sample_offset, stream):
+    return _call("mt_render_nlos", scene, film, scan, spp, seed, sample_offset, stream)
+
+
+def mt_render_backward(scene, film, d_grad_film, d_grad_steady, spp, seed, max_depth, sample_offset, d_grad_albedo,
+                       d_grad_radiance, d_grad_medium_albedo, stream):
+    return _call("mt_render_backward", scene, film, d_grad_film, d_grad_steady, spp, seed, max_depth, sample_offset,
+                 d_grad_albedo, d_grad_radiance, d_grad_medium_albedo, stream)
+
+
+def mt_sync(scene, stream):
+    return _call("mt_sync", scene, stream)
+
+
+def mt_read_counters(scene, out, reset, stream):
+    return _call("mt_read_counters", scene, out, reset, stream)
+
+
+def mt_scene_stats(scene, out):
+    return _call("mt_scene_stats", scene, out)
+
+
+def mt_set_launch(scene, kind, threads, tile, ctas_per_sm):
+    return _call("mt_set_launch", scene, kind, threads, tile, ctas_per_sm)
+
+
+def mt_scene_destroy(scene):
+    load().mt_scene_destroy(scene)
+
+
+def mt_film_destroy(film):
+    load().mt_film_destroy(film)
+
+
+def mt_probe_philox(seed, d_counters, n, d_out, stream):
+    return _call("mt_probe_philox", seed, d_counters, n, d_out, stream)
+
+
+def mt_probe_trace(scene, d_rays, n, tmax, any_hit, d_tri, d_t, stream):
+    return _call("mt_probe_trace", scene, d_rays, n, tmax, any_hit, d_tri, d_t, stream)
+
+
+def mt_probe_bins(d_opl, n, start, width, T, d_bin, stream):
+    return _call("mt_probe_bins", d_opl, n, start, width, T, d_bin, stream)
+
+
+def mt_render_dump(scene, film, scan, spp, seed, max_depth, sample_offset, d_dump, cap, d_count, stream):
+    return _call("mt_render_dump", scene, film, scan, spp, seed, max_depth, sample_offset, d_dump, cap, d_count, stream)
+
+
+# --- conveniences ---------------------------------------------------------------
+def _f3(v):
+    return (C.c_float * 3)(*[float(x) for x in v])
+
+
+class Scene:
+    """A scene on the device (libmt handle) built from a scenes.Scene."""
+
+    def __init__(self, sc: "_scenes.Scene", stream=None):
+        self.sc = sc
+        n = sc.n_tris
+        tris = np.ascontiguousarray(sc.tris, np.float32)
+        mats = (mt_material * n)()
+        alb = np.ascontiguousarray(sc.albedo, np.float32)
+        rough = np.ascontiguousarray(sc.roughness, np.float32)
+        mt = np.ascontiguousarray(sc.mtype, np.uint32)
+        arr = np.frombuffer(mats, dtype=np.dtype([("albedo", np.float32, 3), ("roughness", np.float32),
+                                                  ("type", np.uint32)]))
+        arr["albedo"] = alb
+        arr["roughness"] = rough
+        arr["type"] = mt
+        ne = len(sc.emitters)
+        ems = (mt_emitter * max(ne, 1))()
+        for i, e in enumerate(sc.emitters):
+            ems[i] = mt_emitter(int(e["type"]), int(e["first_tri"]), int(e["n_tris"]), _f3(e["radiance"]),
+                                _f3(e.get("position", (0, 0, 0))))
+        cam = mt_camera(_f3(sc.camera["origin"]), _f3(sc.camera["target"]), _f3(sc.camera["up"]),
+                        float(sc.camera["fov_x_deg"]))
+        med = None
+        self._dens = None
+        if sc.medium is not None:
+            m = sc.medium
+            self._dens = np.ascontiguousarray(m["density"], np.float32)
+            rz, ry, rx = self._dens.shape
+            med = mt_medium(_f3(m["lo"]), _f3(m["hi"]), (C.c_int32 * 3)(rx, ry, rz),
+                            self._dens.ctypes.data_as(C.c_void_p), float(m["albedo"]), float(m["g"]))
+        h = C.c_void_p()
+        mt_scene_create(tris.ctypes.data_as(C.c_void_p), n, mats, ems, ne, C.byref(cam),
+                        C.byref(med) if med is not None else None, _stream(stream), C.byref(h))
+        self.h = h
+        self.n_tris = n
+        self.n_em = ne
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                mt_scene_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def set_params(self, albedo=None, radiance=None, medium_albedo=None, stream=None):
+        mt_scene_set_params(self.h, _ptr(albedo), _ptr(radiance), _ptr(medium_albedo), _stream(stream))
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 8)()
+        mt_scene_stats(self.h, out)
+        keys = ["n_tris", "bvh_nodes", "bvh_depth", "sah_x1000", "light_units", "device_bytes", "build_us"]
+        return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def read_counters(self, reset=True, stream=None) -> dict:
+        out = (C.c_uint64 * 8)()
+        mt_read_counters(self.h, out, int(reset), _stream(stream))
+        keys = ["vertices", "paths", "contributions", "rays", "node_visits", "tri_tests", "smem_splats", "gmem_splats"]
+        return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def sync(self, stream=None):
+        mt_sync(self.h, _stream(stream))
+
+    def set_launch(self, kind, threads=0, tile=0, ctas_per_sm=0):
+        mt_set_launch(self.h, kind, threads, tile, ctas_per_sm)
+
+
+class Film:
+    """A film handle over caller-owned torch tensors."""
+
+    def __init__(self, film, steady, start, width, flags=0):
+        H, W, T, Cc = film.shape
+        self.film, self.steady = film, steady
+        h = C.c_void_p()
+        mt_film_create(H, W, T, Cc, float(start), float(width), _ptr(film), _ptr(steady), int(flags), C.byref(h))
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                mt_film_destroy(h)
+            except Exception:
+                pass
+
+
+def new_film(H, W, T, Cc=3, device="cuda"):
+    import torch
+    return (torch.empty((H, W, T, Cc), dtype=torch.float32, device=device),
+            torch.empty((H, W, Cc), dtype=torch.float32, device=device))
+
+
+def render(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_offset=0, flags=0, out=None,
+           stream=None):
+    """Transient render; returns (film [H,W,T,3], steady [H,W,3]) torch tensors."""
+    film, steady = out if out is not None else new_film(H, W, T, 3)
+    f = Film(film, steady, start, width, flags)
+    mt_render(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
+    return film, steady
+
+
+def render_backward(scene: Scene, T, start, width, spp, seed, max_depth, grad_film, grad_steady=None,
+                    sample_offset=0, flags=0, out=None, stream=None):
+    """Path-replay gradients (accumulated into `out` if given)."""
+    import torch
+    H, W = grad_film.shape[:2]
+    if out is None:
+        out = (torch.zeros((scene.n_tris, 3), dtype=torch.float32, device="cuda"),
+               torch.zeros((max(scene.n_em, 1), 3), dtype=torch.float32, device="cuda"),
+               torch.zeros(1, dtype=torch.float32, device="cuda"))
+    galb, grad, gmed = out
+    f = Film(grad_film, None, start, width, flags)
+    mt_render_backward(scene.h, f.h, _ptr(grad_film), _ptr(grad_steady), spp, seed, max_depth, sample_offset,
+                       _ptr(galb), _ptr(grad), _ptr(gmed), _stream(stream))
+    del H, W
+    return galb, grad, gmed
+
+
+def make_scan(lasers, sensors, mode, wall_normal, wall_albedo, hidden):
+    return mt_scan(_ptr(lasers), int(lasers.shape[0]), _ptr(sensors) if sensors is not None else None,
+                   int(sensors.shape[0]) if sensors is not None else 0, int(mode), _f3(wall_normal),
+                   float(wall_albedo), int(hidden[0]), int(hidden[1]))
+
+
+def render_nlos(scene: Scene, lasers, sensors, mode, T, start, width, spp, seed, sample_offset=0, flags=0,
+                out=None, stream=None):
+    """Relay-wall impulse responses; returns (film [rows, T], steady [rows])."""
+    import torch
+    rows = lasers.shape[0] * (sensors.shape[0] if mode == MT_EXHAUSTIVE else 1)
+    if out is None:
+        out = (torch.empty((rows, T), dtype=torch.float32, device="cuda"),
+               torch.empty((rows,), dtype=torch.float32, device="cuda"))
+    film, steady = out
+    sc = scene.sc
+    scan = make_scan(lasers, sensors if mode == MT_EXHAUSTIVE else None, mode, sc.wall["normal"], sc.wall["albedo"],
+                     sc.hidden)
+    f = Film(film.view(rows, 1, T, 1), steady, start, width, flags)
+    mt_render_nlos(scene.h, f.h, C.byref(scan), spp, seed, sample_offset, _stream(stream))
+    return film, steady
+
+
+def render_dump(scene: Scene, H, W, T, start, width, spp, seed, max_depth, cap, sample_offset=0, flags=0,
+                scan_args=None, stream=None):
+    """Forward render (or NLOS when scan_args is given) that also returns every
+    contribution record as a numpy structured array (CONTRIB_DTYPE)."""
+    import torch
+    dump = torch.empty((max(cap, 1), 10), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    if scan_args is None:
+        film, steady = new_film(H, W, T, 3)
+        f = Film(film, steady, start, width, flags)
+        mt_render_dump(scene.h, f.h, None, spp, seed, max_depth, sample_offset, _ptr(dump), cap, _ptr(cnt),
+                       _stream(stream))
+    else:
+        lasers, sensors, mode = scan_args
+        rows = lasers.shape[0] * (sensors.shape[0] if mode == MT_EXHAUSTIVE else 1)
+        film = torch.empty((rows, 1, T, 1), dtype=torch.float32, device="cuda")
+        steady = torch.empty((rows, 1, 1), dtype=torch.float32, device="cuda")
+        sc = scene.sc
+        scan = make_scan(lasers, sensors if mode == MT_EXHAUSTIVE else None, mode, sc.wall["normal"],
+                         sc.wall["albedo"], sc.hidden)
+        f = Film(film, steady, start, width, flags)
+        mt_render_dump(scene.h, f.h, C.byref(scan), spp, seed, max_depth, sample_offset, _ptr(dump), cap,
+                       _ptr(cnt), _stream(stream))
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    n = int(cnt.item())
+    rec = dump[:min(n, cap)].cpu().numpy().view(CONTRIB_DTYPE).reshape(-1)
+    return film, steady, rec, n
+
+
+def probe_philox(seed, counters):
+    import torch
+    out = torch.empty_like(counters)
+    mt_probe_philox(int(seed), _ptr(counters), counters.shape[0], _ptr(out), _stream())
+    return out
+
+
+def probe_trace(scene: Scene, rays, tmax=float("inf"), any_hit=False):
+    import torch
+    n = rays.shape[0]
+    tri = torch.empty(n, dtype=torch.int32, device="cuda")
+    t = torch.empty(n, dtype=torch.float32, device="cuda")
+    mt_probe_trace(scene.h, _ptr(rays), n, float(tmax), int(any_hit), _ptr(tri), _ptr(t), _stream())
+    return tri, t
+
+
+def probe_bins(opl, start, width, T):
+    import torch
+    out = torch.empty(opl.shape[0], dtype=torch.int32, device="cuda")
+    mt_probe_bins(_ptr(opl), opl.shape[0], float(start), float(width), int(T), _ptr(out), _stream())
+    return out
+
+
+def _autograd():
+    import torch
+
+    class TransientRender(torch.autograd.Function):
+        """(albedo [n,3], radiance [e,3]) -> (film [H,W,T,3], steady [H,W,3]).
+
+        Forward is mt_render with the given parameters; backward is
+        mt_render_backward (path replay, Sec. 4.4) with the same seed."""
+
+        @staticmethod
+        def forward(ctx, albedo, radiance, scene, H, W, T, start, width, spp, seed, max_depth):
+            scene.set_params(albedo=albedo.detach().contiguous(), radiance=radiance.detach().contiguous())
+            film, steady = render(scene, H, W, T, start, width, spp, seed, max_depth)
+            ctx.args = (scene, T, start, width, spp, seed, max_depth)
+            ctx.save_for_backward(albedo, radiance)
+            return film, steady
+
+        @staticmethod
+        def backward(ctx, g_film, g_steady):
+            scene, T, start, width, spp, seed, max_depth = ctx.args
+            albedo, radiance = ctx.saved_tensors
+            scene.set_params(albedo=albedo.detach().contiguous(), radiance=radiance.detach().contiguous())
+            g_film = g_film.contiguous() if g_film is not None else None
+            g_steady = g_steady.contiguous() if g_steady is not None else None
+            if g_film is None:
+                g_film = torch.zeros((scene.H, scene.W, T, 3), device="cuda")
+            ga, gr, _ = render_backward(scene, T, start, width, spp, seed, max_depth, g_film, g_steady)
+            return ga, gr[:radiance.shape[0]], None, None, None, None, None, None, None, None, None
+
+    return TransientRender
+
+
+def __getattr__(name):
+    if name == "TransientRender":
+        return _autograd()
+    raise AttributeError(name)

@@ -1,0 +1,855 @@
+// mt_api.cu -- the C ABI of libmt (declared in include/mt_api.h).
+//
+// Host-side orchestration only: argument validation, device memory of scenes,
+// launch configuration and error reporting.  Every step of the rendering path
+// runs in the kernels of mt_render.cu / mt_nlos.cu / mt_bvh.cu or in the small
+// set-up kernels below.
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+
+#include "mt_common.cuh"
+#include "mt_internal.h"
+#include "mt_launch.h"
+#include "mt_trace.cuh"
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+namespace mt {
+static thread_local std::string g_err;
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+const char *get_error() { return g_err.c_str(); }
+
+static std::atomic<long long> g_alloc_count{0};
+static long long fault_at() {
+    static long long v = [] {
+        const char *e = getenv("MT_FAULT_INJECT");
+        if (!e || strncmp(e, "alloc:", 6) != 0) return -1LL;
+        return atoll(e + 6);
+    }();
+    return v;
+}
+
+mt_status alloc_device(void **p, size_t bytes, const char *what) {
+    const long long k = ++g_alloc_count;
+    if (fault_at() > 0 && k == fault_at()) {
+        set_error("injected allocation failure (%s, %zu bytes)", what, bytes);
+        return MT_ERR_OUT_OF_MEMORY;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MT_ERR_OUT_OF_MEMORY : MT_ERR_CUDA;
+    }
+    return MT_OK;
+}
+}  // namespace mt
+
+struct mt_film_s {
+    int32_t H, W, T, C;
+    float start, width;
+    float *film, *steady;
+    uint32_t flags;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+};
+
+struct mt_scene_s {
+    mt::AllocList al;
+    DevScene dev{};
+    int num_sms = 0;
+    int smem_optin = 0;
+    int64_t n_tris = 0;
+    int32_t n_em = 0;
+    BvhResult bvh;
+    LaunchCfg cfg[3];
+    // scratch
+    int *tile_counter = nullptr;   // [4]
+    uint32_t *err = nullptr;
+    unsigned long long *counters = nullptr;
+    float *m_params = nullptr;
+    // NLOS state
+    int32_t h_first = -1, h_count = -1;
+    uint32_t *hcdf = nullptr;
+    float h_area = 0.f;
+    float4 *ysamp = nullptr;
+    int32_t *ysamp_tri = nullptr;
+    long long ysamp_cap = 0;
+    GraphCache nlos_graph;
+    cudaStream_t cap_stream = nullptr;  // private stream the NLOS graph is captured on
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// set-up kernels
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_pack_mats(const mt_material *m, int n, float4 *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const mt_material a = m[i];
+        out[i] = make_float4(a.albedo[0], a.albedo[1], a.albedo[2], a.type == MT_GGX_CONDUCTOR ? a.roughness : -1.0f);
+    }
+}
+
+__global__ void k_set_albedo(const float *alb, int n, float4 *mats) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 m = mats[i];
+        mats[i] = make_float4(alb[3 * i], alb[3 * i + 1], alb[3 * i + 2], m.w);
+    }
+}
+
+__global__ void k_set_radiance(const float *rad, int n, float4 *em) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        em[i] = make_float4(rad[3 * i], rad[3 * i + 1], rad[3 * i + 2], 0.f);
+}
+
+__global__ void k_leaf_of(const float4 *tris, int n, int32_t *leaf_of) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        leaf_of[__float_as_int(tris[3 * k].w)] = k;
+}
+
+// double-precision area of a triangle, evaluated without contraction
+__device__ double tri_area_d(const float *t) {
+    const double ax = __dsub_rn((double)t[3], (double)t[0]), ay = __dsub_rn((double)t[4], (double)t[1]),
+                 az = __dsub_rn((double)t[5], (double)t[2]);
+    const double bx = __dsub_rn((double)t[6], (double)t[0]), by = __dsub_rn((double)t[7], (double)t[1]),
+                 bz = __dsub_rn((double)t[8], (double)t[2]);
+    const double cx = __dsub_rn(__dmul_rn(ay, bz), __dmul_rn(az, by));
+    const double cy = __dsub_rn(__dmul_rn(az, bx), __dmul_rn(ax, bz));
+    const double cz = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
+    const double l2 = __dadd_rn(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)), __dmul_rn(cz, cz));
+    return __dmul_rn(0.5, __dsqrt_rn(l2));
+}
+
+// Emitter sampling table: units (area-emitter triangles, point emitters)
+// weighted by area * mean radiance; the normalised running sum is kept in
+// double and stored as ceil(cdf * 2^24) so that comparing the top 24 bits of a
+// Philox output against it is the comparison u < cdf.
+__global__ void k_setup_units(const float *tris, const int32_t *unit_tri, const int32_t *unit_em, int nu,
+                              const mt_emitter *em, LightUnit *units, uint32_t *cdf, int32_t *tri_unit) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double tot = 0.0;
+    for (int i = 0; i < nu; ++i) {
+        const mt_emitter e = em[unit_em[i]];
+        const double mean = __ddiv_rn(__dadd_rn(__dadd_rn((double)e.radiance[0], (double)e.radiance[1]),
+                                                (double)e.radiance[2]), 3.0);
+        const double a = unit_tri[i] >= 0 ? tri_area_d(tris + 9 * (size_t)unit_tri[i]) : 1.0;
+        tot = __dadd_rn(tot, unit_tri[i] >= 0 ? __dmul_rn(a, mean) : mean);
+    }
+    double acc = 0.0;
+    for (int i = 0; i < nu; ++i) {
+        const mt_emitter e = em[unit_em[i]];
+        const double mean = __ddiv_rn(__dadd_rn(__dadd_rn((double)e.radiance[0], (double)e.radiance[1]),
+                                                (double)e.radiance[2]), 3.0);
+        const int t = unit_tri[i];
+        const double a = t >= 0 ? tri_area_d(tris + 9 * (size_t)t) : 0.0;
+        const double w = t >= 0 ? __dmul_rn(a, mean) : mean;
+        acc = __dadd_rn(acc, w);
+        double c = tot > 0.0 ? __ddiv_rn(acc, tot) : 0.0;
+        if (i == nu - 1 && tot > 0.0) c = 1.0;
+        const double q = ceil(c * 16777216.0);
+        cdf[i] = (uint32_t)(q > 16777216.0 ? 16777216.0 : q);
+        LightUnit u;
+        const float pick = tot > 0.0 ? (float)__ddiv_rn(w, tot) : 0.0f;
+        if (t >= 0) {
+            const float *v = tris + 9 * (size_t)t;
+            const float3 v0 = f3(v[0], v[1], v[2]), v1 = f3(v[3], v[4], v[5]), v2 = f3(v[6], v[7], v[8]);
+            const float3 n = normalize(cross(v1 - v0, v2 - v0));
+            u.v0 = make_float4(v0.x, v0.y, v0.z, (float)a);
+            u.v1 = make_float4(v1.x, v1.y, v1.z, pick);
+            u.v2 = make_float4(v2.x, v2.y, v2.z, __int_as_float(unit_em[i]));
+            u.n = make_float4(n.x, n.y, n.z, __int_as_float(t));
+            tri_unit[t] = i;
+        } else {
+            u.v0 = make_float4(e.position[0], e.position[1], e.position[2], 0.f);
+            u.v1 = make_float4(0.f, 0.f, 0.f, pick);
+            u.v2 = make_float4(0.f, 0.f, 0.f, __int_as_float(unit_em[i]));
+            u.n = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        }
+        units[i] = u;
+    }
+}
+
+// hidden-surface area table for NLOS (same construction, weight = area)
+__global__ void k_setup_hidden(const float *tris_leaf4, const int32_t *leaf_of, int first, int n, uint32_t *cdf,
+                               float *area_out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const float4 *t4 = reinterpret_cast<const float4 *>(tris_leaf4);
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int k = leaf_of[first + i];
+        const float4 a = t4[3 * k], b = t4[3 * k + 1], c = t4[3 * k + 2];
+        const float v[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
+        tot = __dadd_rn(tot, tri_area_d(v));
+    }
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int k = leaf_of[first + i];
+        const float4 a = t4[3 * k], b = t4[3 * k + 1], c = t4[3 * k + 2];
+        const float v[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
+        acc = __dadd_rn(acc, tri_area_d(v));
+        double cc = __ddiv_rn(acc, tot);
+        if (i == n - 1) cc = 1.0;
+        const double q = ceil(cc * 16777216.0);
+        cdf[i] = (uint32_t)(q > 16777216.0 ? 16777216.0 : q);
+    }
+    *area_out = (float)tot;
+}
+
+struct CamOut {
+    float o[3], f[3], r[3], u[3], tan_half;
+};
+
+__global__ void k_camera(mt_camera c, CamOut *out) {
+    const double o[3] = {c.origin[0], c.origin[1], c.origin[2]};
+    double f[3] = {c.target[0] - o[0], c.target[1] - o[1], c.target[2] - o[2]};
+    double l = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int k = 0; k < 3; ++k) f[k] /= l;
+    const double up[3] = {c.up[0], c.up[1], c.up[2]};
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    l = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int k = 0; k < 3; ++k) r[k] /= l;
+    const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    for (int k = 0; k < 3; ++k) {
+        out->o[k] = (float)o[k];
+        out->f[k] = (float)f[k];
+        out->r[k] = (float)r[k];
+        out->u[k] = (float)u[k];
+    }
+    out->tan_half = (float)tan((double)c.fov_x_deg * 3.14159265358979323846 / 360.0);
+}
+
+__global__ void k_max(const float *v, size_t n, unsigned int *out) {
+    float m = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
+}
+
+__global__ void k_probe_philox(uint32_t k0, uint32_t k1, const uint4 *c, long long n, uint4 *o) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        o[i] = philox4x32_10(c[i], k0, k1);
+}
+
+__global__ void k_probe_trace(const DevScene s, const float *rays, long long n, float tmax, int any, int32_t *tri,
+                              float *tt) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float *r = rays + 6 * i;
+        const RayT ray = make_ray(s, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]));
+        TraceCnt c{0, 0};
+        if (any) {
+            tri[i] = trace_any<false>(s, ray, tmax, c) ? 1 : 0;
+        } else {
+            float t;
+            int orig;
+            const int k = trace_closest<false>(s, ray, tmax, t, orig, c);
+            tri[i] = k >= 0 ? orig : -1;
+            if (tt) tt[i] = k >= 0 ? t : INFINITY;
+        }
+    }
+}
+
+__global__ void k_probe_bins(const float *opl, long long n, float start, float width, int T, int32_t *bin) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float x = (opl[i] - start) / width;
+        bin[i] = (x >= 0.f && x < (float)T) ? (int)x : -1;
+    }
+}
+
+int grid_for(long long n, int threads, int num_sms) {
+    return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, (long long)num_sms * 32));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define MT_CHECK_ARG(cond, ...)            \
+    do {                                   \
+        if (!(cond)) {                     \
+            mt::set_error(__VA_ARGS__);    \
+            return MT_ERR_INVALID_ARGUMENT; \
+        }                                  \
+    } while (0)
+
+extern "C" {
+
+const char *mt_last_error(void) { return mt::get_error(); }
+
+static mt_status scene_create_impl(const float *tris, int64_t n, const mt_material *mats, const mt_emitter *ems,
+                                   int32_t n_em, const mt_camera *cam, const mt_medium *med, cudaStream_t st,
+                                   mt_scene_s *sc) {
+    int dev = 0;
+    MT_CUDA_TRY(cudaGetDevice(&dev));
+    MT_CUDA_TRY(cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    MT_CUDA_TRY(cudaDeviceGetAttribute(&sc->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    sc->n_tris = n;
+    sc->n_em = n_em;
+    auto &al = sc->al;
+    float *d_tris;
+    mt_material *d_mats;
+    mt_emitter *d_em;
+    MT_TRY(al.alloc(&d_tris, (size_t)n * 9, "triangles"));
+    MT_TRY(al.alloc(&d_mats, (size_t)n, "materials"));
+    MT_TRY(al.alloc(&d_em, (size_t)std::max(1, n_em), "emitters"));
+    MT_CUDA_TRY(cudaMemcpyAsync(d_tris, tris, (size_t)n * 9 * sizeof(float), cudaMemcpyHostToDevice, st));
+    MT_CUDA_TRY(cudaMemcpyAsync(d_mats, mats, (size_t)n * sizeof(mt_material), cudaMemcpyHostToDevice, st));
+    if (n_em > 0) MT_CUDA_TRY(cudaMemcpyAsync(d_em, ems, (size_t)n_em * sizeof(mt_emitter), cudaMemcpyHostToDevice, st));
+    MT_TRY(mt_build_bvh(d_tris, (int32_t)n, st, al, &sc->bvh));
+    DevScene &D = sc->dev;
+    D.nodes = sc->bvh.nodes;
+    D.tris = sc->bvh.tris;
+    D.n_tris = (int32_t)n;
+    D.n_em = n_em;
+    for (int k = 0; k < 3; ++k) {
+        (&D.q_lo.x)[k] = sc->bvh.q_lo[k];
+        (&D.q_scale.x)[k] = sc->bvh.q_scale[k];
+    }
+    float4 *mats4, *emrad;
+    int32_t *tri_unit, *leaf_of;
+    MT_TRY(al.alloc(&mats4, (size_t)n, "packed materials"));
+    MT_TRY(al.alloc(&tri_unit, (size_t)n, "triangle light units"));
+    MT_TRY(al.alloc(&leaf_of, (size_t)n, "leaf order"));
+    MT_TRY(al.alloc(&emrad, (size_t)std::max(1, n_em), "emitter radiance"));
+    const int g = grid_for(n, 256, sc->num_sms);
+    k_pack_mats<<<g, 256, 0, st>>>(d_mats, (int)n, mats4);
+    k_leaf_of<<<g, 256, 0, st>>>(sc->bvh.tris, (int)n, leaf_of);
+    MT_CUDA_TRY(cudaMemsetAsync(tri_unit, 0xFF, (size_t)n * sizeof(int32_t), st));
+    // light units (index bookkeeping on the host, arithmetic on the device)
+    std::vector<int32_t> ut, ue;
+    std::vector<float> rad(3 * (size_t)std::max(1, n_em), 0.f);
+    for (int e = 0; e < n_em; ++e) {
+        for (int k = 0; k < 3; ++k) rad[3 * e + k] = ems[e].radiance[k];
+        if (ems[e].type == MT_EMITTER_AREA) {
+            for (uint32_t t = 0; t < ems[e].n_tris; ++t) {
+                ut.push_back((int32_t)(ems[e].first_tri + t));
+                ue.push_back(e);
+            }
+        } else {
+            ut.push_back(-1);
+            ue.push_back(e);
+        }
+    }
+    const int nu = (int)ut.size();
+    int32_t *d_ut, *d_ue;
+    LightUnit *units;
+    uint32_t *cdf;
+    MT_TRY(al.alloc(&d_ut, std::max(1, nu), "light units"));
+    MT_TRY(al.alloc(&d_ue, std::max(1, nu), "light units"));
+    MT_TRY(al.alloc(&units, std::max(1, nu), "light units"));
+    MT_TRY(al.alloc(&cdf, std::max(1, nu), "light cdf"));
+    if (nu > 0) {
+        MT_CUDA_TRY(cudaMemcpyAsync(d_ut, ut.data(), nu * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(d_ue, ue.data(), nu * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_setup_units<<<1, 1, 0, st>>>(d_tris, d_ut, d_ue, nu, d_em, units, cdf, tri_unit);
+    }
+    // radiance rows -> float4
+    {
+        float *tmp;
+        MT_TRY(al.alloc(&tmp, rad.size(), "radiance staging"));
+        MT_CUDA_TRY(cudaMemcpyAsync(tmp, rad.data(), rad.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        k_set_radiance<<<1, 64, 0, st>>>(tmp, std::max(1, n_em), emrad);
+    }
+    D.mats = mats4;
+    D.tri_unit = tri_unit;
+    D.leaf_of = leaf_of;
+    D.units = units;
+    D.unit_cdf = cdf;
+    D.n_units = nu;
+    D.em_rad = emrad;
+    // camera
+    CamOut *dcam, hcam;
+    MT_TRY(al.alloc(&dcam, 1, "camera"));
+    k_camera<<<1, 1, 0, st>>>(*cam, dcam);
+    MT_CUDA_TRY(cudaMemcpyAsync(&hcam, dcam, sizeof(CamOut), cudaMemcpyDeviceToHost, st));
+    // medium
+    MT_TRY(al.alloc(&sc->m_params, 2, "medium parameters"));
+    float mp[2] = {med ? med->albedo : 0.f, med ? med->g : 0.f};
+    MT_CUDA_TRY(cudaMemcpyAsync(sc->m_params, mp, sizeof(mp), cudaMemcpyHostToDevice, st));
+    D.m_params = sc->m_params;
+    D.has_medium = med != nullptr;
+    unsigned int hmax = 0;
+    if (med) {
+        const size_t nv = (size_t)med->res[0] * med->res[1] * med->res[2];
+        float *dens;
+        unsigned int *dmax;
+        MT_TRY(al.alloc(&dens, nv, "density grid"));
+        MT_TRY(al.alloc(&dmax, 1, "majorant"));
+        MT_CUDA_TRY(cudaMemcpyAsync(dens, med->density, nv * sizeof(float), cudaMemcpyHostToDevice, st));
+        MT_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st));
+        k_max<<<grid_for((long long)nv, 256, sc->num_sms), 256, 0, st>>>(dens, nv, dmax);
+        MT_CUDA_TRY(cudaMemcpyAsync(&hmax, dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        D.dens = dens;
+        D.rx = med->res[0];
+        D.ry = med->res[1];
+        D.rz = med->res[2];
+        D.m_lo = make_float3(med->lo[0], med->lo[1], med->lo[2]);
+        D.m_hi = make_float3(med->hi[0], med->hi[1], med->hi[2]);
+    }
+    // scratch
+    MT_TRY(al.alloc(&sc->tile_counter, 4, "tile counters"));
+    MT_TRY(al.alloc(&sc->err, 1, "error word"));
+    MT_TRY(al.alloc(&sc->counters, 8, "counters"));
+    MT_CUDA_TRY(cudaMemsetAsync(sc->err, 0, sizeof(uint32_t), st));
+    MT_CUDA_TRY(cudaMemsetAsync(sc->counters, 0, 8 * sizeof(unsigned long long), st));
+    MT_CUDA_TRY(cudaGetLastError());
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (med) {
+        float mj;
+        memcpy(&mj, &hmax, 4);
+        D.m_major = mj;
+        if (!(mj > 0.f)) {
+            mt::set_error("medium density must have a positive maximum");
+            return MT_ERR_INVALID_ARGUMENT;
+        }
+    }
+    D.cam_o = make_float3(hcam.o[0], hcam.o[1], hcam.o[2]);
+    D.cam_f = make_float3(hcam.f[0], hcam.f[1], hcam.f[2]);
+    D.cam_r = make_float3(hcam.r[0], hcam.r[1], hcam.r[2]);
+    D.cam_u = make_float3(hcam.u[0], hcam.u[1], hcam.u[2]);
+    D.tan_half = hcam.tan_half;
+    D.err = sc->err;
+    D.counters = sc->counters;
+    for (int k = 0; k < 3; ++k) sc->cfg[k] = LaunchCfg{256, 0, 0, sc->num_sms, 0};
+    return MT_OK;
+}
+
+mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials, const mt_emitter *emitters,
+                          int32_t n_emitters, const mt_camera *camera, const mt_medium *medium, void *stream,
+                          mt_scene *out) {
+    MT_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MT_CHECK_ARG(tris != nullptr && materials != nullptr && camera != nullptr, "tris, materials and camera must not be NULL");
+    MT_CHECK_ARG(n_tris >= 1 && n_tris < (1LL << 29), "n_tris = %lld outside [1, 2^29)", (long long)n_tris);
+    MT_CHECK_ARG(n_emitters >= 0 && (n_emitters == 0 || emitters != nullptr), "bad emitter list");
+    for (int64_t i = 0; i < n_tris * 9; ++i)
+        MT_CHECK_ARG(std::isfinite(tris[i]), "non-finite vertex coordinate at triangle %lld", (long long)(i / 9));
+    for (int64_t i = 0; i < n_tris; ++i) {
+        const mt_material &m = materials[i];
+        MT_CHECK_ARG(m.type == MT_LAMBERT || m.type == MT_GGX_CONDUCTOR, "triangle %lld: unknown material type %u",
+                     (long long)i, m.type);
+        for (int k = 0; k < 3; ++k)
+            MT_CHECK_ARG(std::isfinite(m.albedo[k]) && m.albedo[k] >= 0.f, "triangle %lld: bad albedo", (long long)i);
+        MT_CHECK_ARG(m.type != MT_GGX_CONDUCTOR || (m.roughness > 0.f && m.roughness <= 1.f),
+                     "triangle %lld: GGX roughness must lie in (0, 1]", (long long)i);
+    }
+    for (int e = 0; e < n_emitters; ++e) {
+        const mt_emitter &em = emitters[e];
+        MT_CHECK_ARG(em.type == MT_EMITTER_AREA || em.type == MT_EMITTER_POINT, "emitter %d: unknown type", e);
+        for (int k = 0; k < 3; ++k)
+            MT_CHECK_ARG(std::isfinite(em.radiance[k]) && em.radiance[k] >= 0.f, "emitter %d: bad radiance", e);
+        if (em.type == MT_EMITTER_AREA)
+            MT_CHECK_ARG(em.n_tris >= 1 && (int64_t)em.first_tri + em.n_tris <= n_tris,
+                         "emitter %d: triangle range out of bounds", e);
+        else
+            for (int k = 0; k < 3; ++k) MT_CHECK_ARG(std::isfinite(em.position[k]), "emitter %d: bad position", e);
+    }
+    if (medium) {
+        MT_CHECK_ARG(medium->density != nullptr && medium->res[0] > 0 && medium->res[1] > 0 && medium->res[2] > 0,
+                     "medium: bad grid");
+        for (int k = 0; k < 3; ++k) MT_CHECK_ARG(medium->hi[k] > medium->lo[k], "medium: empty box");
+        MT_CHECK_ARG(medium->albedo > 0.f && medium->albedo <= 1.f && std::fabs(medium->g) < 1.f,
+                     "medium: albedo must lie in (0, 1] and |g| < 1");
+        const size_t nv = (size_t)medium->res[0] * medium->res[1] * medium->res[2];
+        for (size_t i = 0; i < nv; ++i)
+            MT_CHECK_ARG(std::isfinite(medium->density[i]) && medium->density[i] >= 0.f, "medium: bad density");
+    }
+    MT_CHECK_ARG(std::isfinite(camera->fov_x_deg) && camera->fov_x_deg > 0.f && camera->fov_x_deg < 180.f,
+                 "camera: fov_x_deg must lie in (0, 180)");
+    mt_scene_s *sc = new (std::nothrow) mt_scene_s();
+    if (!sc) {
+        mt::set_error("host allocation failed");
+        return MT_ERR_OUT_OF_MEMORY;
+    }
+    const mt_status st = scene_create_impl(tris, n_tris, materials, emitters, n_emitters, camera, medium,
+                                           (cudaStream_t)stream, sc);
+    if (st != MT_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        sc->al.free_all();
+        delete sc;
+        return st;
+    }
+    *out = sc;
+    return MT_OK;
+}
+
+void mt_scene_destroy(mt_scene s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    if (s->nlos_graph.exec) cudaGraphExecDestroy(s->nlos_graph.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    s->al.free_all();
+    delete s;
+}
+
+mt_status mt_scene_set_params(mt_scene s, const float *d_albedo, const float *d_radiance,
+                              const float *d_medium_albedo, void *stream) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_albedo)
+        k_set_albedo<<<grid_for(s->n_tris, 256, s->num_sms), 256, 0, st>>>(d_albedo, (int)s->n_tris,
+                                                                           const_cast<float4 *>(s->dev.mats));
+    if (d_radiance && s->n_em > 0)
+        k_set_radiance<<<1, 64, 0, st>>>(d_radiance, s->n_em, const_cast<float4 *>(s->dev.em_rad));
+    if (d_medium_albedo)
+        MT_CUDA_TRY(cudaMemcpyAsync(s->m_params, d_medium_albedo, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start_opl, float bin_width, float *d_film,
+                         float *d_steady, uint32_t flags, mt_film *out) {
+    MT_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MT_CHECK_ARG(H >= 1 && W >= 1 && T >= 1, "film size H=%d W=%d T=%d must be positive", H, W, T);
+    MT_CHECK_ARG(C == 1 || C == 3, "C must be 1 or 3");
+    MT_CHECK_ARG(std::isfinite(start_opl) && std::isfinite(bin_width) && bin_width > 0.f, "bad time window");
+    MT_CHECK_ARG(d_film != nullptr, "film pointer is NULL");
+    MT_CHECK_ARG((flags & ~(MT_UNWARP | MT_ACCUMULATE | MT_PIXEL_CENTER | MT_COUNTERS)) == 0, "unknown flags 0x%x", flags);
+    MT_CHECK_ARG((int64_t)H * W < (1LL << 31), "too many pixels");
+    mt_film_s *f = new (std::nothrow) mt_film_s{H, W, T, C, start_opl, bin_width, d_film, d_steady, flags};
+    if (!f) return MT_ERR_OUT_OF_MEMORY;
+    *out = f;
+    return MT_OK;
+}
+
+void mt_film_destroy(mt_film f) { delete f; }
+
+static void seed_key(uint64_t seed, uint32_t &k0, uint32_t &k1) {
+    k0 = (uint32_t)seed;
+    k1 = (uint32_t)(seed >> 32);
+}
+
+// pick tile size and privatisation depth for a film within the shared-memory budget
+static LaunchCfg render_cfg(const mt_scene_s *s, int kind, int32_t W, int32_t T, int C, int extra_floats, int &D) {
+    LaunchCfg c = s->cfg[kind];
+    const size_t budget = (size_t)std::min(s->smem_optin, 220 * 1024) - 1024;
+    int tile = c.tile > 0 ? c.tile : 0;
+    if (tile == 0) {
+        // default: aim for >= 48 KB histograms, up to 32 pixels
+        const size_t per_px = (size_t)T * C * 4;
+        tile = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024) / std::max<size_t>(per_px, 1)));
+        if (kind == MT_LAUNCH_RENDER || kind == MT_LAUNCH_BACKWARD) tile = std::min(tile, W);
+    }
+    size_t fixed = ((size_t)tile * (C == 3 ? 3 : 1) + extra_floats) * 4 + 64;
+    size_t avail = budget > fixed ? budget - fixed : 0;
+    D = (int)std::min<size_t>((size_t)T, avail / ((size_t)tile * C * 4));
+    if (D < 1) D = 0;
+    c.tile = tile;
+    c.smem_bytes = (((size_t)tile * D * C + (size_t)tile * (C == 3 ? 3 : 1) + extra_floats) * 4 + 15) & ~(size_t)15;
+    return c;
+}
+
+static mt_status check_err_word(mt_scene s) {
+    uint32_t e = 0;
+    MT_CUDA_TRY(cudaMemcpy(&e, s->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) {
+        MT_CUDA_TRY(cudaMemset(s->err, 0, sizeof(e)));
+        if (e & MT_EFLAG_STACK) {
+            mt::set_error("device: traversal stack overflow");
+            return MT_ERR_INTERNAL;
+        }
+        mt::set_error("device: bounded wait or tracking loop gave up (flags 0x%x)", e);
+        return MT_ERR_TIMEOUT;
+    }
+    return MT_OK;
+}
+
+static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
+                               uint64_t sample_offset, int mode, const float *gfilm, const float *gsteady,
+                               float *galb, float *grad, float *gmed, mt_contrib *dump, int64_t cap,
+                               int64_t *dcount, cudaStream_t st) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
+    MT_CHECK_ARG(f->C == 3, "path-traced films have C = 3");
+    MT_CHECK_ARG(spp >= 1, "spp must be >= 1");
+    MT_CHECK_ARG(max_depth >= 1 && max_depth <= MT_MAX_DEPTH, "max_depth must lie in [1, %d]", MT_MAX_DEPTH);
+    MT_CHECK_ARG(sample_offset + (uint64_t)spp <= 0xFFFFFFFFull, "sample indices must fit in 32 bits");
+    MT_CHECK_ARG((int64_t)f->W * spp < (1LL << 31), "tile path count overflows");
+    if (mode == 2) {
+        MT_CHECK_ARG(max_depth <= MT_MAX_BWD_DEPTH, "backward supports max_depth <= %d", MT_MAX_BWD_DEPTH);
+        MT_CHECK_ARG(gfilm != nullptr && galb != nullptr && grad != nullptr, "gradient buffers must not be NULL");
+    }
+    const int kind = mode == 2 ? MT_LAUNCH_BACKWARD : MT_LAUNCH_RENDER;
+    const int n_em_smem = (mode == 2 && s->n_em <= 64) ? s->n_em : 0;
+    int D;
+    LaunchCfg cfg = render_cfg(s, kind, f->W, f->T, 3, n_em_smem * 3, D);
+    RenderParams p{};
+    p.H = f->H;
+    p.W = f->W;
+    p.T = f->T;
+    p.D = D;
+    p.start = f->start;
+    p.width = f->width;
+    const bool acc = f->flags & MT_ACCUMULATE;
+    p.scale = acc ? 1.0f : 1.0f / (float)spp;
+    p.flags = f->flags;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.sample_offset = (uint32_t)sample_offset;
+    seed_key(seed, p.k0, p.k1);
+    p.tile_px = cfg.tile;
+    p.tiles_per_row = (f->W + cfg.tile - 1) / cfg.tile;
+    p.n_tiles = p.tiles_per_row * f->H;
+    p.film = f->film;
+    p.steady = f->steady;
+    p.gfilm = gfilm;
+    p.gsteady = gsteady;
+    p.galb = galb;
+    p.grad = grad;
+    p.gmed = gmed;
+    p.dump = dump;
+    p.dump_cap = cap;
+    p.dump_count = (unsigned long long *)dcount;
+    p.tile_counter = s->tile_counter;
+    p.n_em_smem = n_em_smem;
+    if (mode != 2 && D < f->T && !acc) {
+        MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
+    }
+    if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
+    MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
+    return mt_launch_render(s->dev, p, cfg, mode, (f->flags & MT_COUNTERS) != 0, st);
+}
+
+mt_status mt_render(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth, uint64_t sample_offset,
+                    void *stream) {
+    return render_common(s, f, spp, seed, max_depth, sample_offset, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+mt_status mt_render_backward(mt_scene s, mt_film f, const float *d_grad_film, const float *d_grad_steady, int32_t spp,
+                             uint64_t seed, int32_t max_depth, uint64_t sample_offset, float *d_grad_albedo,
+                             float *d_grad_radiance, float *d_grad_medium_albedo, void *stream) {
+    return render_common(s, f, spp, seed, max_depth, sample_offset, 2, d_grad_film, d_grad_steady, d_grad_albedo,
+                         d_grad_radiance, d_grad_medium_albedo, nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed,
+                              uint64_t sample_offset, NlosParams &p, LaunchCfg &cfg, cudaStream_t st) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr && sc != nullptr, "scene, film or scan is NULL");
+    MT_CHECK_ARG(f->C == 1, "NLOS films have C = 1");
+    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || sc->mode == MT_EXHAUSTIVE, "unknown scan mode");
+    MT_CHECK_ARG(sc->lasers != nullptr && sc->n_lasers >= 1, "no laser points");
+    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || (sc->sensors != nullptr && sc->n_sensors >= 1), "no sensor points");
+    const long long rows = sc->mode == MT_EXHAUSTIVE ? (long long)sc->n_lasers * sc->n_sensors : sc->n_lasers;
+    MT_CHECK_ARG((long long)f->H * f->W == rows, "film H*W = %lld must equal the number of scan pairs %lld",
+                 (long long)f->H * f->W, rows);
+    MT_CHECK_ARG(sc->hidden_count >= 1 && (int64_t)sc->hidden_first + sc->hidden_count <= s->n_tris,
+                 "hidden triangle range out of bounds");
+    MT_CHECK_ARG(spp >= 1 && sample_offset + (uint64_t)spp <= 0xFFFFFFFFull, "bad spp / sample_offset");
+    const float nl = std::sqrt(sc->wall_normal[0] * sc->wall_normal[0] + sc->wall_normal[1] * sc->wall_normal[1] +
+                               sc->wall_normal[2] * sc->wall_normal[2]);
+    MT_CHECK_ARG(std::fabs(nl - 1.0f) < 1e-3f, "wall normal must be a unit vector");
+    if (s->h_first != (int32_t)sc->hidden_first || s->h_count != (int32_t)sc->hidden_count) {
+        cudaStreamCaptureStatus cs;
+        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                     "the first NLOS call for a hidden range must not be captured (it builds the sampling table)");
+        if (!s->hcdf || s->h_count < (int32_t)sc->hidden_count) MT_TRY(s->al.alloc(&s->hcdf, sc->hidden_count, "hidden cdf"));
+        float *darea;
+        MT_TRY(s->al.alloc(&darea, 1, "hidden area"));
+        k_setup_hidden<<<1, 1, 0, st>>>(reinterpret_cast<const float *>(s->dev.tris), s->dev.leaf_of,
+                                        (int)sc->hidden_first, (int)sc->hidden_count, s->hcdf, darea);
+        MT_CUDA_TRY(cudaMemcpyAsync(&s->h_area, darea, sizeof(float), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        s->h_first = (int32_t)sc->hidden_first;
+        s->h_count = (int32_t)sc->hidden_count;
+    }
+    if (sc->mode == MT_EXHAUSTIVE) {
+        const long long need = (long long)sc->n_lasers * spp;
+        if (need > s->ysamp_cap) {
+            cudaStreamCaptureStatus cs;
+            MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+            MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                         "the first exhaustive NLOS call of this size must not be captured (it sizes its scratch)");
+            MT_TRY(s->al.alloc(&s->ysamp, (size_t)need * 2, "nlos hidden samples"));
+            MT_TRY(s->al.alloc(&s->ysamp_tri, (size_t)need, "nlos hidden samples"));
+            s->ysamp_cap = need;
+        }
+    }
+    int D;
+    cfg = render_cfg(s, MT_LAUNCH_NLOS, (int)rows, f->T, 1, 0, D);
+    MT_CHECK_ARG(D >= 1, "film row too long");
+    p = NlosParams{};
+    p.T = f->T;
+    p.D = D;
+    p.start = f->start;
+    p.width = f->width;
+    const bool acc = f->flags & MT_ACCUMULATE;
+    p.scale = acc ? 1.0f : 1.0f / (float)spp;
+    p.flags = f->flags;
+    p.spp = spp;
+    p.mode = (int32_t)sc->mode;
+    p.sample_offset = (uint32_t)sample_offset;
+    seed_key(seed, p.k0, p.k1);
+    p.lasers = sc->lasers;
+    p.sensors = sc->sensors;
+    p.n_l = sc->n_lasers;
+    p.n_s = sc->mode == MT_EXHAUSTIVE ? sc->n_sensors : 0;
+    p.nw = make_float3(sc->wall_normal[0], sc->wall_normal[1], sc->wall_normal[2]);
+    p.fw = sc->wall_albedo / MT_PI;
+    p.hidden_first = (int32_t)sc->hidden_first;
+    p.hidden_n = (int32_t)sc->hidden_count;
+    p.hcdf = s->hcdf;
+    p.hidden_area = s->h_area;
+    p.tile = cfg.tile;
+    if (sc->mode == MT_EXHAUSTIVE) p.n_tiles = sc->n_lasers * ((sc->n_sensors + cfg.tile - 1) / cfg.tile);
+    else p.n_tiles = (int)((rows + cfg.tile - 1) / cfg.tile);
+    p.film = f->film;
+    p.steady = f->steady;
+    p.ysamp = s->ysamp;
+    p.ysamp_tri = s->ysamp_tri;
+    p.tile_counter = s->tile_counter + 1;
+    return MT_OK;
+}
+
+static mt_status nlos_enqueue(mt_scene s, mt_film f, const NlosParams &p, const LaunchCfg &cfg, bool dump,
+                              cudaStream_t st) {
+    if (p.D < p.T && !(p.flags & MT_ACCUMULATE))
+        MT_CUDA_TRY(cudaMemsetAsync(p.film, 0, (size_t)f->H * f->W * f->T * sizeof(float), st));
+    if (dump) MT_CUDA_TRY(cudaMemsetAsync(p.dump_count, 0, sizeof(int64_t), st));
+    MT_CUDA_TRY(cudaMemsetAsync(p.tile_counter, 0, sizeof(int), st));
+    return mt_launch_nlos(s->dev, p, cfg, dump, (f->flags & MT_COUNTERS) != 0, st);
+}
+
+mt_status mt_render_nlos(mt_scene s, mt_film f, const mt_scan *scan, int32_t spp, uint64_t seed,
+                         uint64_t sample_offset, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    NlosParams p;
+    LaunchCfg cfg;
+    MT_TRY(nlos_prepare(s, f, scan, spp, seed, sample_offset, p, cfg, st));
+    cudaStreamCaptureStatus cs;
+    MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || (f->flags & MT_COUNTERS))
+        return nlos_enqueue(s, f, p, cfg, false, st);
+    // replay a cached graph of [zero counters, (sample pass,) connection pass];
+    // re-capture when any launch parameter changed
+    std::vector<unsigned char> key(sizeof(NlosParams) + sizeof(LaunchCfg) + sizeof(mt_film_s));
+    memcpy(key.data(), &p, sizeof(NlosParams));
+    memcpy(key.data() + sizeof(NlosParams), &cfg, sizeof(LaunchCfg));
+    memcpy(key.data() + sizeof(NlosParams) + sizeof(LaunchCfg), f, sizeof(mt_film_s));
+    GraphCache &gc = s->nlos_graph;
+    if (!gc.exec || gc.key != key) {
+        if (!s->cap_stream) MT_CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        MT_CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const mt_status es = nlos_enqueue(s, f, p, cfg, false, s->cap_stream);
+        const cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+        if (es != MT_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(g);
+            return es;
+        }
+        MT_CUDA_TRY(ce);
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        MT_CUDA_TRY(ie);
+        gc.key = key;
+    }
+    MT_CUDA_TRY(cudaGraphLaunch(gc.exec, st));
+    return MT_OK;
+}
+
+mt_status mt_render_dump(mt_scene s, mt_film f, const mt_scan *scan, int32_t spp, uint64_t seed, int32_t max_depth,
+                         uint64_t sample_offset, mt_contrib *d_dump, int64_t cap, int64_t *d_count, void *stream) {
+    MT_CHECK_ARG(d_dump != nullptr && d_count != nullptr && cap >= 0, "dump buffers must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (scan) {
+        NlosParams p;
+        LaunchCfg cfg;
+        MT_TRY(nlos_prepare(s, f, scan, spp, seed, sample_offset, p, cfg, st));
+        p.dump = d_dump;
+        p.dump_cap = cap;
+        p.dump_count = (unsigned long long *)d_count;
+        return nlos_enqueue(s, f, p, cfg, true, st);
+    }
+    return render_common(s, f, spp, seed, max_depth, sample_offset, 1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         d_dump, cap, d_count, st);
+}
+
+mt_status mt_sync(mt_scene s, void *stream) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    MT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    MT_CUDA_TRY(cudaGetLastError());
+    return check_err_word(s);
+}
+
+mt_status mt_read_counters(mt_scene s, uint64_t *out, int32_t reset, void *stream) {
+    MT_CHECK_ARG(s != nullptr && out != nullptr, "NULL argument");
+    MT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    MT_CUDA_TRY(cudaMemcpy(out, s->counters, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (reset) MT_CUDA_TRY(cudaMemset(s->counters, 0, 8 * sizeof(uint64_t)));
+    return MT_OK;
+}
+
+mt_status mt_scene_stats(mt_scene s, int64_t *out) {
+    MT_CHECK_ARG(s != nullptr && out != nullptr, "NULL argument");
+    out[0] = s->n_tris;
+    out[1] = s->bvh.n_nodes;
+    out[2] = s->bvh.depth;
+    out[3] = (int64_t)llround(s->bvh.sah * 1000.0);
+    out[4] = s->dev.n_units;
+    out[5] = (int64_t)s->bvh.n_nodes * 32 + s->n_tris * 48 + s->n_tris * 24;
+    out[6] = (int64_t)llround(s->bvh.build_us);
+    return MT_OK;
+}
+
+mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    MT_CHECK_ARG(kind >= 0 && kind <= 2, "unknown launch kind");
+    MT_CHECK_ARG(threads == 0 || (threads >= 32 && threads <= 256 && threads % 32 == 0), "threads must be 32..256, x32");
+    MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
+    LaunchCfg &c = s->cfg[kind];
+    c.threads = threads ? threads : 256;
+    c.tile = tile;
+    c.ctas_per_sm = ctas_per_sm;
+    return MT_OK;
+}
+
+mt_status mt_probe_philox(uint64_t seed, const uint32_t *d_counters, int64_t n, uint32_t *d_out, void *stream) {
+    MT_CHECK_ARG(d_counters != nullptr && d_out != nullptr && n >= 0, "bad arguments");
+    if (n == 0) return MT_OK;
+    uint32_t k0, k1;
+    seed_key(seed, k0, k1);
+    k_probe_philox<<<grid_for(n, 256, 152), 256, 0, (cudaStream_t)stream>>>(k0, k1, (const uint4 *)d_counters, n,
+                                                                           (uint4 *)d_out);
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+mt_status mt_probe_trace(mt_scene s, const float *d_rays, int64_t n, float tmax, int32_t any_hit, int32_t *d_tri,
+                         float *d_t, void *stream) {
+    MT_CHECK_ARG(s != nullptr && d_rays != nullptr && d_tri != nullptr && n >= 0, "bad arguments");
+    if (n == 0) return MT_OK;
+    k_probe_trace<<<grid_for(n, 128, s->num_sms), 128, 0, (cudaStream_t)stream>>>(s->dev, d_rays, n, tmax, any_hit,
+                                                                                 d_tri, d_t);
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+mt_status mt_probe_bins(const float *d_opl, int64_t n, float start, float width, int32_t T, int32_t *d_bin,
+                        void *stream) {
+    MT_CHECK_ARG(d_opl != nullptr && d_bin != nullptr && n >= 0 && width > 0.f && T >= 1, "bad arguments");
+    if (n == 0) return MT_OK;
+    k_probe_bins<<<grid_for(n, 256, 152), 256, 0, (cudaStream_t)stream>>>(d_opl, n, start, width, T, d_bin);
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,844 @@
+// mt_bvh.cu -- SAH BVH builder on the device.
+//
+// Top-down binned SAH (32 bins per axis, unit traversal and intersection
+// costs).  Nodes with more than SMALL_T triangles are split level by level,
+// each level binning fixed-size chunks of the node's index range in many CTAs
+// (shared-memory bins merged with global atomics), choosing the split with one
+// warp per node and partitioning stably per chunk.  Smaller nodes are built
+// completely by one CTA each with an explicit stack.  Leaves hold at most four
+// triangles; a node of two to four triangles becomes a leaf when that is
+// cheaper under the SAH.  The binary tree is then written as 32-byte nodes
+// holding both children's boxes as outward-rounded 16-bit planes, and the
+// triangles are reordered into leaf order as 48-byte records.
+#include <cub/cub.cuh>
+
+#include <chrono>
+#include <cmath>
+
+#include "mt_common.cuh"
+#include "mt_internal.h"
+#include "mt_trace.cuh"
+
+namespace {
+
+constexpr int NB = 32;          // bins per axis
+constexpr int SMALL_T = 2048;   // nodes at or below this size are built by one CTA
+constexpr int CHUNK = 4096;     // index positions binned/partitioned per CTA for large nodes
+constexpr int BIN_INTS = 13;    // count, box lo3 hi3, centroid lo3 hi3 (ordered ints)
+constexpr int SMALL_STACK = 96;
+
+struct BNode {
+    float lo[3], hi[3];
+    int32_t left, right;   // child build ids, -1 for a leaf
+    int32_t first, count;  // index range
+};
+
+struct Task {
+    int32_t node, first, count, depth;
+    float clo[3], chi[3];  // centroid bounds
+    float box_lo[3], box_hi[3];
+};
+
+struct Decision {
+    int32_t axis;     // -1: object median without reordering
+    int32_t split;    // bins <= split go left
+    int32_t nL;
+    int32_t cntL, cntR; // partition cursors
+    float llo[3], lhi[3], rlo[3], rhi[3];   // child boxes
+    float lclo[3], lchi[3], rclo[3], rchi[3]; // child centroid bounds
+};
+
+struct Chunk {
+    int32_t task, begin, end;
+};
+
+__device__ __forceinline__ int f2o(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+__device__ __forceinline__ float area_of(const float *lo, const float *hi) {
+    const float dx = fmaxf(0.f, hi[0] - lo[0]), dy = fmaxf(0.f, hi[1] - lo[1]), dz = fmaxf(0.f, hi[2] - lo[2]);
+    return 2.0f * (dx * dy + dy * dz + dz * dx);
+}
+
+// bin of a centroid coordinate; identical in the binning and partition passes
+__device__ __forceinline__ int bin_of(float c, float lo, float hi) {
+    const float ext = hi - lo;
+    if (!(ext > 0.f)) return 0;
+    const float k = (float)NB / ext;
+    int b = (int)((c - lo) * k);
+    return b < 0 ? 0 : (b > NB - 1 ? NB - 1 : b);
+}
+
+__device__ __forceinline__ void bins_init(int *bins) {
+    for (int i = threadIdx.x; i < 3 * NB; i += blockDim.x) {
+        int *b = bins + i * BIN_INTS;
+        b[0] = 0;
+        for (int k = 0; k < 3; ++k) {
+            b[1 + k] = f2o(INFINITY);
+            b[4 + k] = f2o(-INFINITY);
+            b[7 + k] = f2o(INFINITY);
+            b[10 + k] = f2o(-INFINITY);
+        }
+    }
+}
+
+__device__ __forceinline__ void bins_add(int *bins, const float4 lo, const float4 hi, const float4 c, const float *clo,
+                                         const float *chi) {
+    const float cc[3] = {c.x, c.y, c.z};
+    for (int a = 0; a < 3; ++a) {
+        const int bi = bin_of(cc[a], clo[a], chi[a]);
+        int *b = bins + (a * NB + bi) * BIN_INTS;
+        atomicAdd(&b[0], 1);
+        atomicMin(&b[1], f2o(lo.x));
+        atomicMin(&b[2], f2o(lo.y));
+        atomicMin(&b[3], f2o(lo.z));
+        atomicMax(&b[4], f2o(hi.x));
+        atomicMax(&b[5], f2o(hi.y));
+        atomicMax(&b[6], f2o(hi.z));
+        atomicMin(&b[7], f2o(c.x));
+        atomicMin(&b[8], f2o(c.y));
+        atomicMin(&b[9], f2o(c.z));
+        atomicMax(&b[10], f2o(c.x));
+        atomicMax(&b[11], f2o(c.y));
+        atomicMax(&b[12], f2o(c.z));
+    }
+}
+
+// One warp sweeps the NB bins of one axis; returns (cost, split) of the best
+// split (cost = SA_L*nL + SA_R*nR) to all lanes; cost = inf if none is valid.
+__device__ __forceinline__ void sweep_axis(const int *bins_axis, float &best_cost, int &best_split) {
+    const int lane = threadIdx.x & 31;
+    const int *b = bins_axis + lane * BIN_INTS;
+    int cnt = b[0];
+    float lo[3] = {o2f(b[1]), o2f(b[2]), o2f(b[3])}, hi[3] = {o2f(b[4]), o2f(b[5]), o2f(b[6])};
+    // inclusive prefix from the left
+    int pc = cnt;
+    float plo[3] = {lo[0], lo[1], lo[2]}, phi[3] = {hi[0], hi[1], hi[2]};
+    for (int o = 1; o < 32; o <<= 1) {
+        const int c2 = __shfl_up_sync(0xffffffffu, pc, o);
+        float l2[3], h2[3];
+        for (int k = 0; k < 3; ++k) {
+            l2[k] = __shfl_up_sync(0xffffffffu, plo[k], o);
+            h2[k] = __shfl_up_sync(0xffffffffu, phi[k], o);
+        }
+        if (lane >= o) {
+            pc += c2;
+            for (int k = 0; k < 3; ++k) {
+                plo[k] = fminf(plo[k], l2[k]);
+                phi[k] = fmaxf(phi[k], h2[k]);
+            }
+        }
+    }
+    // inclusive suffix from the right
+    int sc = cnt;
+    float slo[3] = {lo[0], lo[1], lo[2]}, shi[3] = {hi[0], hi[1], hi[2]};
+    for (int o = 1; o < 32; o <<= 1) {
+        const int c2 = __shfl_down_sync(0xffffffffu, sc, o);
+        float l2[3], h2[3];
+        for (int k = 0; k < 3; ++k) {
+            l2[k] = __shfl_down_sync(0xffffffffu, slo[k], o);
+            h2[k] = __shfl_down_sync(0xffffffffu, shi[k], o);
+        }
+        if (lane + o < 32) {
+            sc += c2;
+            for (int k = 0; k < 3; ++k) {
+                slo[k] = fminf(slo[k], l2[k]);
+                shi[k] = fmaxf(shi[k], h2[k]);
+            }
+        }
+    }
+    // right side of a split after bin `lane` is the suffix starting at lane+1
+    const int rc = __shfl_down_sync(0xffffffffu, sc, 1);
+    float rlo[3], rhi[3];
+    for (int k = 0; k < 3; ++k) {
+        rlo[k] = __shfl_down_sync(0xffffffffu, slo[k], 1);
+        rhi[k] = __shfl_down_sync(0xffffffffu, shi[k], 1);
+    }
+    float cost = INFINITY;
+    if (lane < 31 && pc > 0 && rc > 0) cost = area_of(plo, phi) * pc + area_of(rlo, rhi) * rc;
+    int split = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float c2 = __shfl_xor_sync(0xffffffffu, cost, o);
+        const int s2 = __shfl_xor_sync(0xffffffffu, split, o);
+        if (c2 < cost || (c2 == cost && s2 < split)) {
+            cost = c2;
+            split = s2;
+        }
+    }
+    best_cost = cost;
+    best_split = split;
+}
+
+// union of bins [b0, b1] of an axis into box / centroid bounds
+__device__ void bins_union(const int *bins_axis, int b0, int b1, float *lo, float *hi, float *clo, float *chi) {
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+        clo[k] = INFINITY;
+        chi[k] = -INFINITY;
+    }
+    for (int i = b0; i <= b1; ++i) {
+        const int *b = bins_axis + i * BIN_INTS;
+        if (b[0] == 0) continue;
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], o2f(b[1 + k]));
+            hi[k] = fmaxf(hi[k], o2f(b[4 + k]));
+            clo[k] = fminf(clo[k], o2f(b[7 + k]));
+            chi[k] = fmaxf(chi[k], o2f(b[10 + k]));
+        }
+    }
+}
+
+// block-wide exclusive scan of one int per thread; returns the total
+__device__ __forceinline__ int block_exscan(int v, int *s_warp, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) s_warp[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const int before = w > 0 ? s_warp[w - 1] : 0;
+    total = s_warp[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_prim_bounds(const float *tris, int n, float4 *plo, float4 *phi, float4 *cen, int *gbox) {
+    __shared__ int sb[12];
+    if (threadIdx.x < 12) sb[threadIdx.x] = (threadIdx.x % 6) < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+    __syncthreads();
+    float l[6] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    float h[6] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float *t = tris + 9 * (size_t)i;
+        float lo[3], hi[3], c[3];
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(t[k], fminf(t[3 + k], t[6 + k]));
+            hi[k] = fmaxf(t[k], fmaxf(t[3 + k], t[6 + k]));
+            c[k] = (t[k] + t[3 + k] + t[6 + k]) * (1.0f / 3.0f);
+            l[k] = fminf(l[k], lo[k]);
+            h[k] = fmaxf(h[k], hi[k]);
+            l[3 + k] = fminf(l[3 + k], c[k]);
+            h[3 + k] = fmaxf(h[3 + k], c[k]);
+        }
+        plo[i] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        phi[i] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        cen[i] = make_float4(c[0], c[1], c[2], 0.f);
+    }
+    for (int k = 0; k < 6; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            l[k] = fminf(l[k], __shfl_xor_sync(0xffffffffu, l[k], o));
+            h[k] = fmaxf(h[k], __shfl_xor_sync(0xffffffffu, h[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&sb[k], f2o(l[k]));
+            atomicMax(&sb[3 + k], f2o(h[k]));
+            atomicMin(&sb[6 + k], f2o(l[3 + k]));
+            atomicMax(&sb[9 + k], f2o(h[3 + k]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        if ((threadIdx.x % 6) < 3) atomicMin(&gbox[threadIdx.x], sb[threadIdx.x]);
+        else atomicMax(&gbox[threadIdx.x], sb[threadIdx.x]);
+    }
+}
+
+__global__ void k_iota(int *idx, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
+}
+
+__global__ void k_bin_chunks(const Chunk *chunks, const Task *tasks, const int *idx, const float4 *plo,
+                             const float4 *phi, const float4 *cen, int *gbins) {
+    __shared__ int bins[3 * NB * BIN_INTS];
+    const Chunk ch = chunks[blockIdx.x];
+    const Task tk = tasks[ch.task];
+    bins_init(bins);
+    __syncthreads();
+    for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
+        const int p = idx[i];
+        bins_add(bins, plo[p], phi[p], cen[p], tk.clo, tk.chi);
+    }
+    __syncthreads();
+    int *g = gbins + (size_t)ch.task * 3 * NB * BIN_INTS;
+    for (int i = threadIdx.x; i < 3 * NB; i += blockDim.x) {
+        const int *b = bins + i * BIN_INTS;
+        if (b[0] == 0) continue;
+        int *d = g + i * BIN_INTS;
+        atomicAdd(&d[0], b[0]);
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&d[1 + k], b[1 + k]);
+            atomicMax(&d[4 + k], b[4 + k]);
+            atomicMin(&d[7 + k], b[7 + k]);
+            atomicMax(&d[10 + k], b[10 + k]);
+        }
+    }
+}
+
+__global__ void k_init_bins(int *gbins, int n_tasks) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tasks * 3 * NB; i += gridDim.x * blockDim.x) {
+        int *b = gbins + (size_t)i * BIN_INTS;
+        b[0] = 0;
+        for (int k = 0; k < 3; ++k) {
+            b[1 + k] = f2o(INFINITY);
+            b[4 + k] = f2o(-INFINITY);
+            b[7 + k] = f2o(INFINITY);
+            b[10 + k] = f2o(-INFINITY);
+        }
+    }
+}
+
+// decide a split from bins (one warp); writes *dec (lane 0); returns via dec
+__device__ void decide(const int *bins, const Task &tk, Decision *dec) {
+    const int lane = threadIdx.x & 31;
+    float bc = INFINITY;
+    int ba = -1, bs = 0;
+    for (int a = 0; a < 3; ++a) {
+        float c;
+        int s;
+        sweep_axis(bins + a * NB * BIN_INTS, c, s);
+        if (c < bc) {
+            bc = c;
+            ba = a;
+            bs = s;
+        }
+    }
+    if (lane == 0) {
+        Decision d;
+        d.cntL = 0;
+        d.cntR = 0;
+        if (ba < 0) {
+            d.axis = -1;
+            d.split = 0;
+            d.nL = tk.count / 2;
+            for (int k = 0; k < 3; ++k) {
+                d.llo[k] = d.rlo[k] = tk.box_lo[k];
+                d.lhi[k] = d.rhi[k] = tk.box_hi[k];
+                d.lclo[k] = d.rclo[k] = tk.clo[k];
+                d.lchi[k] = d.rchi[k] = tk.chi[k];
+            }
+        } else {
+            const int *ab = bins + ba * NB * BIN_INTS;
+            int nL = 0;
+            for (int i = 0; i <= bs; ++i) nL += ab[i * BIN_INTS];
+            d.axis = ba;
+            d.split = bs;
+            d.nL = nL;
+            bins_union(ab, 0, bs, d.llo, d.lhi, d.lclo, d.lchi);
+            bins_union(ab, bs + 1, NB - 1, d.rlo, d.rhi, d.rclo, d.rchi);
+        }
+        *dec = d;
+    }
+}
+
+__global__ void k_choose(const Task *tasks, const int *gbins, Decision *decs) {
+    decide(gbins + (size_t)blockIdx.x * 3 * NB * BIN_INTS, tasks[blockIdx.x], &decs[blockIdx.x]);
+}
+
+__global__ void k_partition_chunks(const Chunk *chunks, const Task *tasks, Decision *decs, const int *idx,
+                                   const float4 *cen, int *tmp) {
+    __shared__ int s_warp[32];
+    __shared__ int s_base[2];
+    const Chunk ch = chunks[blockIdx.x];
+    const Task tk = tasks[ch.task];
+    Decision *dec = &decs[ch.task];
+    const int axis = dec->axis;
+    if (axis < 0) return;
+    const int split = dec->split, nL = dec->nL;
+    for (int base = ch.begin; base < ch.end; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int p = 0, left = 0;
+        const bool valid = i < ch.end;
+        if (valid) {
+            p = idx[i];
+            const float4 c = cen[p];
+            const float cc = axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
+            left = bin_of(cc, tk.clo[axis], tk.chi[axis]) <= split;
+        }
+        int totL;
+        const int rankL = block_exscan(valid && left, s_warp, totL);
+        const int nvalid = min((int)blockDim.x, ch.end - base);
+        if (threadIdx.x == 0) {
+            s_base[0] = atomicAdd(&dec->cntL, totL);
+            s_base[1] = atomicAdd(&dec->cntR, nvalid - totL);
+        }
+        __syncthreads();
+        if (valid) {
+            const int rankR = (int)threadIdx.x - rankL;
+            const int dst = left ? tk.first + s_base[0] + rankL : tk.first + nL + s_base[1] + rankR;
+            tmp[dst] = p;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_copy_chunks(const Chunk *chunks, const Decision *decs, int *idx, const int *tmp) {
+    const Chunk ch = chunks[blockIdx.x];
+    if (decs[ch.task].axis < 0) return;
+    for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) idx[i] = tmp[i];
+}
+
+__device__ void make_child_tasks(const Task &tk, const Decision &d, int base, BNode *nodes, Task *c) {
+    for (int s = 0; s < 2; ++s) {
+        Task t;
+        t.node = base + s;
+        t.first = s == 0 ? tk.first : tk.first + d.nL;
+        t.count = s == 0 ? d.nL : tk.count - d.nL;
+        t.depth = tk.depth + 1;
+        for (int k = 0; k < 3; ++k) {
+            t.box_lo[k] = s == 0 ? d.llo[k] : d.rlo[k];
+            t.box_hi[k] = s == 0 ? d.lhi[k] : d.rhi[k];
+            t.clo[k] = s == 0 ? d.lclo[k] : d.rclo[k];
+            t.chi[k] = s == 0 ? d.lchi[k] : d.rchi[k];
+        }
+        BNode nd;
+        for (int k = 0; k < 3; ++k) {
+            nd.lo[k] = t.box_lo[k];
+            nd.hi[k] = t.box_hi[k];
+        }
+        nd.left = nd.right = -1;
+        nd.first = t.first;
+        nd.count = t.count;
+        nodes[t.node] = nd;
+        c[s] = t;
+    }
+    nodes[tk.node].left = base;
+    nodes[tk.node].right = base + 1;
+}
+
+__global__ void k_children(const Task *tasks, int n_tasks, const Decision *decs, BNode *nodes, int *counters,
+                           Task *next, Task *small) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tasks) return;
+    const Task tk = tasks[i];
+    const int base = atomicAdd(&counters[0], 2);
+    Task c[2];
+    make_child_tasks(tk, decs[i], base, nodes, c);
+    for (int s = 0; s < 2; ++s) {
+        if (c[s].count > SMALL_T) next[atomicAdd(&counters[1], 1)] = c[s];
+        else small[atomicAdd(&counters[2], 1)] = c[s];
+        atomicMax(&counters[3], c[s].depth);
+    }
+}
+
+// one CTA builds the whole subtree of a small task
+__global__ void __launch_bounds__(128) k_build_small(const Task *small, BNode *nodes, int *idx, int *tmp,
+                                                     const float4 *plo, const float4 *phi, const float4 *cen,
+                                                     int *counters) {
+    __shared__ int bins[3 * NB * BIN_INTS];
+    __shared__ Task stack[SMALL_STACK];
+    __shared__ int s_sp;
+    __shared__ Decision s_dec;
+    __shared__ int s_leaf;
+    __shared__ int s_warp[32];
+    __shared__ Task s_tk;
+    if (threadIdx.x == 0) {
+        stack[0] = small[blockIdx.x];
+        s_sp = 1;
+    }
+    for (;;) {
+        __syncthreads();
+        const int sp_now = s_sp;  // every thread reads before thread 0 pops
+        __syncthreads();
+        if (sp_now == 0) break;
+        if (threadIdx.x == 0) s_tk = stack[--s_sp];
+        bins_init(bins);
+        __syncthreads();
+        const Task tk = s_tk;
+        if (tk.count <= 1) {
+            if (threadIdx.x == 0) {
+                nodes[tk.node].left = -1;
+                nodes[tk.node].right = -1;
+                atomicMax(&counters[3], tk.depth);
+            }
+            __syncthreads();
+            continue;
+        }
+        for (int i = tk.first + threadIdx.x; i < tk.first + tk.count; i += blockDim.x) {
+            const int p = idx[i];
+            bins_add(bins, plo[p], phi[p], cen[p], tk.clo, tk.chi);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) decide(bins, tk, &s_dec);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const Decision &d = s_dec;
+            const float sa = area_of(tk.box_lo, tk.box_hi);
+            const float split_cost = sa + area_of(d.llo, d.lhi) * d.nL + area_of(d.rlo, d.rhi) * (tk.count - d.nL);
+            const float leaf_cost = sa * tk.count;
+            s_leaf = tk.count <= 4 && leaf_cost <= split_cost;
+            if (s_leaf) {
+                nodes[tk.node].left = -1;
+                nodes[tk.node].right = -1;
+                atomicMax(&counters[3], tk.depth);
+            }
+        }
+        __syncthreads();
+        if (s_leaf) continue;
+        const int axis = s_dec.axis;
+        if (axis >= 0) {
+            const int split = s_dec.split, nL = s_dec.nL;
+            int cL = 0, cR = 0;
+            for (int base = tk.first; base < tk.first + tk.count; base += blockDim.x) {
+                const int i = base + threadIdx.x;
+                const bool valid = i < tk.first + tk.count;
+                int p = 0, left = 0;
+                if (valid) {
+                    p = idx[i];
+                    const float4 c = cen[p];
+                    const float cc = axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
+                    left = bin_of(cc, tk.clo[axis], tk.chi[axis]) <= split;
+                }
+                int totL;
+                const int rankL = block_exscan(valid && left, s_warp, totL);
+                const int nvalid = min((int)blockDim.x, tk.first + tk.count - base);
+                if (valid) {
+                    const int rankR = (int)threadIdx.x - rankL;
+                    tmp[left ? tk.first + cL + rankL : tk.first + nL + cR + rankR] = p;
+                }
+                cL += totL;
+                cR += nvalid - totL;
+            }
+            __syncthreads();
+            for (int i = tk.first + threadIdx.x; i < tk.first + tk.count; i += blockDim.x) idx[i] = tmp[i];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const int base = atomicAdd(&counters[0], 2);
+            Task c[2];
+            make_child_tasks(tk, s_dec, base, nodes, c);
+            if (s_sp + 2 <= SMALL_STACK) {
+                stack[s_sp++] = c[1];
+                stack[s_sp++] = c[0];
+            } else {
+                atomicOr(&counters[4], 1);  // stack overflow: children stay leaves
+                for (int s = 0; s < 2; ++s) {
+                    nodes[c[s].node].left = -1;
+                    nodes[c[s].node].right = -1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_internal_flags(const BNode *nodes, int n, int *flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flags[i] = nodes[i].left >= 0 ? 1 : 0;
+}
+
+__device__ __forceinline__ uint32_t qfloor(float v, double lo, double sc) {
+    double q = floor(((double)v - lo) / sc) - 1.0;
+    q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
+    return (uint32_t)q;
+}
+__device__ __forceinline__ uint32_t qceil(float v, double lo, double sc) {
+    double q = ceil(((double)v - lo) / sc) + 1.0;
+    q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
+    return (uint32_t)q;
+}
+
+__device__ __forceinline__ uint32_t child_ref(const BNode *nodes, const int *map, int c) {
+    const BNode &n = nodes[c];
+    if (n.left >= 0) return (uint32_t)map[c];
+    if (n.count <= 0) return MT_EMPTY_REF;
+    return 0x80000000u | ((uint32_t)(n.count - 1) << 29) | (uint32_t)n.first;
+}
+
+__device__ __forceinline__ void quant_box(const BNode &n, const float *qlo, const float *qs, uint32_t *q) {
+    for (int k = 0; k < 3; ++k) {
+        q[k] = qfloor(n.lo[k], qlo[k], qs[k]);
+        q[3 + k] = qceil(n.hi[k], qlo[k], qs[k]);
+    }
+}
+
+__global__ void k_emit(const BNode *nodes, int n, const int *map, const int *flags, uint4 *out, float qlx, float qly,
+                       float qlz, float qsx, float qsy, float qsz) {
+    const float qlo[3] = {qlx, qly, qlz}, qs[3] = {qsx, qsy, qsz};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        const BNode &nd = nodes[i];
+        uint32_t a[6], b[6];
+        quant_box(nodes[nd.left], qlo, qs, a);
+        quant_box(nodes[nd.right], qlo, qs, b);
+        const int m = map[i];
+        out[2 * m] = make_uint4(a[0] | (a[1] << 16), a[2] | (a[3] << 16), a[4] | (a[5] << 16), b[0] | (b[1] << 16));
+        out[2 * m + 1] = make_uint4(b[2] | (b[3] << 16), b[4] | (b[5] << 16), child_ref(nodes, map, nd.left),
+                                    child_ref(nodes, map, nd.right));
+    }
+}
+
+__global__ void k_emit_root_leaf(const BNode *nodes, uint4 *out, float qlx, float qly, float qlz, float qsx, float qsy,
+                                 float qsz) {
+    const float qlo[3] = {qlx, qly, qlz}, qs[3] = {qsx, qsy, qsz};
+    uint32_t a[6];
+    quant_box(nodes[0], qlo, qs, a);
+    const uint32_t ref = 0x80000000u | ((uint32_t)(nodes[0].count - 1) << 29) | (uint32_t)nodes[0].first;
+    out[0] = make_uint4(a[0] | (a[1] << 16), a[2] | (a[3] << 16), a[4] | (a[5] << 16), 0xFFFFu);
+    out[1] = make_uint4(0u, 0u, ref, MT_EMPTY_REF);
+}
+
+__global__ void k_reorder(const float *tris, const int *idx, int n, float4 *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int p = idx[k];
+        const float *t = tris + 9 * (size_t)p;
+        out[3 * k] = make_float4(t[0], t[1], t[2], __int_as_float(p));
+        out[3 * k + 1] = make_float4(t[3], t[4], t[5], 0.f);
+        out[3 * k + 2] = make_float4(t[6], t[7], t[8], 0.f);
+    }
+}
+
+__global__ void k_sah(const BNode *nodes, int n, double inv_root, double *acc) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const BNode &nd = nodes[i];
+        const double a = area_of(nd.lo, nd.hi) * inv_root;
+        s += nd.left >= 0 ? a : a * nd.count;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+// every child reference in range and every triangle in exactly one leaf slot
+__global__ void k_validate(const uint4 *nodes, int n_int, int n, int *bad, unsigned long long *leaf_sum) {
+    unsigned long long cnt = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_int; i += gridDim.x * blockDim.x) {
+        const uint4 b = nodes[2 * i + 1];
+        const uint32_t refs[2] = {b.z, b.w};
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t r = refs[c];
+            if (r == MT_EMPTY_REF) continue;
+            if (!(r & 0x80000000u)) {
+                if (r >= (uint32_t)n_int || r == 0u) atomicOr(bad, 1);
+            } else {
+                const uint32_t first = r & 0x1FFFFFFFu, k = ((r >> 29) & 3u) + 1u;
+                if ((unsigned long long)first + k > (unsigned long long)n) atomicOr(bad, 2);
+                cnt += k;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(leaf_sum, cnt);
+}
+
+}  // namespace
+
+mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::AllocList &al, BvhResult *out) {
+    auto t0 = std::chrono::steady_clock::now();
+    mt::AllocList tmpal;
+    struct Guard {
+        mt::AllocList &a;
+        ~Guard() { a.free_all(); }
+    } guard{tmpal};
+    float4 *plo, *phi, *cen;
+    int *idx, *tmp, *gbox, *counters, *flags, *map;
+    BNode *nodes;
+    Task *taskA, *taskB, *small;
+    const int max_nodes = 2 * n + 2;
+    MT_TRY(tmpal.alloc(&plo, n, "bvh prim boxes"));
+    MT_TRY(tmpal.alloc(&phi, n, "bvh prim boxes"));
+    MT_TRY(tmpal.alloc(&cen, n, "bvh centroids"));
+    MT_TRY(tmpal.alloc(&idx, n, "bvh index"));
+    MT_TRY(tmpal.alloc(&tmp, n, "bvh index"));
+    MT_TRY(tmpal.alloc(&gbox, 12, "bvh box"));
+    MT_TRY(tmpal.alloc(&counters, 8, "bvh counters"));
+    MT_TRY(tmpal.alloc(&nodes, max_nodes, "bvh build nodes"));
+    MT_TRY(tmpal.alloc(&flags, max_nodes, "bvh flags"));
+    MT_TRY(tmpal.alloc(&map, max_nodes, "bvh map"));
+    const int max_tasks = n / SMALL_T + 4;
+    MT_TRY(tmpal.alloc(&taskA, max_tasks, "bvh tasks"));
+    MT_TRY(tmpal.alloc(&taskB, max_tasks, "bvh tasks"));
+    MT_TRY(tmpal.alloc(&small, n + 2, "bvh small tasks"));
+
+    // scene box and centroid box
+    {
+        int init[12];
+        for (int k = 0; k < 12; ++k) {
+            const float v = (k % 6) < 3 ? INFINITY : -INFINITY;
+            int i;
+            memcpy(&i, &v, 4);
+            init[k] = i >= 0 ? i : i ^ 0x7FFFFFFF;
+        }
+        MT_CUDA_TRY(cudaMemcpyAsync(gbox, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    }
+    const int nb = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    k_prim_bounds<<<nb, 256, 0, st>>>(d_tris, n, plo, phi, cen, gbox);
+    k_iota<<<nb, 256, 0, st>>>(idx, n);
+    MT_CUDA_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(int), st));
+    int hbox[12];
+    MT_CUDA_TRY(cudaMemcpyAsync(hbox, gbox, sizeof(hbox), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    float box[12];
+    for (int k = 0; k < 12; ++k) {
+        int i = hbox[k];
+        i = i >= 0 ? i : i ^ 0x7FFFFFFF;
+        memcpy(&box[k], &i, 4);
+    }
+    Task root;
+    root.node = 0;
+    root.first = 0;
+    root.count = n;
+    root.depth = 0;
+    for (int k = 0; k < 3; ++k) {
+        root.box_lo[k] = box[k];
+        root.box_hi[k] = box[3 + k];
+        root.clo[k] = box[6 + k];
+        root.chi[k] = box[9 + k];
+        out->scene_lo[k] = box[k];
+        out->scene_hi[k] = box[3 + k];
+    }
+    {
+        BNode rn;
+        for (int k = 0; k < 3; ++k) {
+            rn.lo[k] = box[k];
+            rn.hi[k] = box[3 + k];
+        }
+        rn.left = rn.right = -1;
+        rn.first = 0;
+        rn.count = n;
+        MT_CUDA_TRY(cudaMemcpyAsync(nodes, &rn, sizeof(rn), cudaMemcpyHostToDevice, st));
+    }
+    int hc[8] = {1, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<Task> large;
+    if (n > SMALL_T) large.push_back(root);
+    else {
+        MT_CUDA_TRY(cudaMemcpyAsync(small, &root, sizeof(Task), cudaMemcpyHostToDevice, st));
+        hc[2] = 1;
+    }
+    MT_CUDA_TRY(cudaMemcpyAsync(counters, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+
+    int *gbins = nullptr;
+    Decision *decs = nullptr;
+    Chunk *dchunks = nullptr;
+    const int max_chunks = n / CHUNK + max_tasks + 4;
+    MT_TRY(tmpal.alloc(&gbins, (size_t)max_tasks * 3 * NB * BIN_INTS, "bvh bins"));
+    MT_TRY(tmpal.alloc(&decs, max_tasks, "bvh decisions"));
+    MT_TRY(tmpal.alloc(&dchunks, max_chunks, "bvh chunks"));
+    std::vector<Chunk> chunks;
+    while (!large.empty()) {
+        const int nt = (int)large.size();
+        chunks.clear();
+        for (int t = 0; t < nt; ++t)
+            for (int b = large[t].first; b < large[t].first + large[t].count; b += CHUNK)
+                chunks.push_back(Chunk{t, b, std::min(b + CHUNK, large[t].first + large[t].count)});
+        const int nc = (int)chunks.size();
+        MT_CUDA_TRY(cudaMemcpyAsync(taskA, large.data(), nt * sizeof(Task), cudaMemcpyHostToDevice, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(dchunks, chunks.data(), nc * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+        k_init_bins<<<std::min(1024, (nt * 3 * NB + 255) / 256), 256, 0, st>>>(gbins, nt);
+        k_bin_chunks<<<nc, 512, 0, st>>>(dchunks, taskA, idx, plo, phi, cen, gbins);
+        k_choose<<<nt, 32, 0, st>>>(taskA, gbins, decs);
+        k_partition_chunks<<<nc, 512, 0, st>>>(dchunks, taskA, decs, idx, cen, tmp);
+        k_copy_chunks<<<nc, 512, 0, st>>>(dchunks, decs, idx, tmp);
+        MT_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, sizeof(int), st));
+        k_children<<<(nt + 127) / 128, 128, 0, st>>>(taskA, nt, decs, nodes, counters, taskB, small);
+        MT_CUDA_TRY(cudaGetLastError());
+        MT_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        large.resize(hc[1]);
+        if (hc[1] > 0) {
+            MT_CUDA_TRY(cudaMemcpyAsync(large.data(), taskB, hc[1] * sizeof(Task), cudaMemcpyDeviceToHost, st));
+            MT_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+    }
+    if (hc[2] > 0) k_build_small<<<hc[2], 128, 0, st>>>(small, nodes, idx, tmp, plo, phi, cen, counters);
+    MT_CUDA_TRY(cudaGetLastError());
+    MT_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hc[4]) {
+        mt::set_error("BVH build stack overflow");
+        return MT_ERR_INTERNAL;
+    }
+    const int n_build = hc[0];
+    out->depth = hc[3] + 1;
+    if (out->depth > MT_STACK - 2) {
+        mt::set_error("BVH depth %d exceeds the traversal stack (%d)", out->depth, MT_STACK);
+        return MT_ERR_UNSUPPORTED;
+    }
+
+    // quantisation frame: scene box mapped into [1, 65534] so that the
+    // outward-rounded planes never clamp
+    double ext[3], mx = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        ext[k] = (double)box[3 + k] - (double)box[k];
+        mx = std::max(mx, ext[k]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double e = std::max(std::max(ext[k], 1e-4 * mx), 1e-12) * (1.0 + 1.0 / 1024.0);
+        out->q_scale[k] = (float)(e / 65533.0);
+        out->q_lo[k] = (float)((double)box[k] - (double)out->q_scale[k]);
+    }
+
+    // internal nodes -> dense compact nodes
+    k_internal_flags<<<std::min(1024, (n_build + 255) / 256), 256, 0, st>>>(nodes, n_build, flags);
+    size_t scan_bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, flags, map, n_build, st);
+    void *scan_tmp = nullptr;
+    MT_TRY(tmpal.alloc((char **)&scan_tmp, scan_bytes, "bvh scan"));
+    MT_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, flags, map, n_build, st));
+    int last_map = 0, last_flag = 0;
+    MT_CUDA_TRY(cudaMemcpyAsync(&last_map, map + n_build - 1, 4, cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaMemcpyAsync(&last_flag, flags + n_build - 1, 4, cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    int n_int = last_map + last_flag;
+    const bool root_leaf = n_int == 0;
+    if (root_leaf) n_int = 1;
+    MT_TRY(al.alloc(&out->nodes, (size_t)2 * n_int, "bvh nodes"));
+    MT_TRY(al.alloc(&out->tris, (size_t)3 * n, "bvh triangles"));
+    if (root_leaf)
+        k_emit_root_leaf<<<1, 1, 0, st>>>(nodes, out->nodes, out->q_lo[0], out->q_lo[1], out->q_lo[2],
+                                          out->q_scale[0], out->q_scale[1], out->q_scale[2]);
+    else
+        k_emit<<<std::min(2048, (n_build + 255) / 256), 256, 0, st>>>(nodes, n_build, map, flags, out->nodes,
+                                                                      out->q_lo[0], out->q_lo[1], out->q_lo[2],
+                                                                      out->q_scale[0], out->q_scale[1],
+                                                                      out->q_scale[2]);
+    k_reorder<<<std::min(2048, (n + 255) / 256), 256, 0, st>>>(d_tris, idx, n, out->tris);
+    {
+        int *dbad;
+        unsigned long long *dsum;
+        MT_TRY(tmpal.alloc(&dbad, 1, "bvh check"));
+        MT_TRY(tmpal.alloc(&dsum, 1, "bvh check"));
+        MT_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), st));
+        MT_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), st));
+        k_validate<<<std::min(1024, (n_int + 255) / 256), 256, 0, st>>>(out->nodes, n_int, n, dbad, dsum);
+        int hbad = 0;
+        unsigned long long hsum = 0;
+        MT_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(&hsum, dsum, sizeof(hsum), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad || hsum != (unsigned long long)n) {
+            mt::set_error("BVH validation failed (flags %d, %llu leaf slots for %d triangles)", hbad, hsum, n);
+            return MT_ERR_INTERNAL;
+        }
+    }
+    double *dsah;
+    MT_TRY(tmpal.alloc(&dsah, 1, "bvh sah"));
+    MT_CUDA_TRY(cudaMemsetAsync(dsah, 0, sizeof(double), st));
+    float rlo[3] = {box[0], box[1], box[2]}, rhi[3] = {box[3], box[4], box[5]};
+    const double ra = 2.0 * ((double)(rhi[0] - rlo[0]) * (rhi[1] - rlo[1]) + (double)(rhi[1] - rlo[1]) * (rhi[2] - rlo[2]) +
+                             (double)(rhi[2] - rlo[2]) * (rhi[0] - rlo[0]));
+    k_sah<<<std::min(1024, (n_build + 255) / 256), 256, 0, st>>>(nodes, n_build, ra > 0 ? 1.0 / ra : 0.0, dsah);
+    MT_CUDA_TRY(cudaGetLastError());
+    MT_CUDA_TRY(cudaMemcpyAsync(&out->sah, dsah, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    out->n_nodes = n_int;
+    out->build_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    return MT_OK;
+}

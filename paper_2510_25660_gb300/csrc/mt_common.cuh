@@ -1,0 +1,233 @@
+// mt_common.cuh -- shared device code of libmt: Philox RNG, vector math,
+// sampling maps, BSDFs and the device view of a scene.
+//
+// Every function here is FP32 device code for sm_103a.  The estimator follows
+// arXiv 2510.25660 Sec. 3 (paths, time of flight as optical path length,
+// impulse response without scattering delays, Monte Carlo estimator, path
+// reuse); the sampling maps and random-number layout are this library's
+// readings of what the paper leaves open, stated next to each function.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define MT_PI 3.14159265358979323846f
+#define MT_MAX_DEPTH 64
+#define MT_STACK 64
+#define MT_TRACK_STEPS 1024
+
+// device error word bits
+#define MT_EFLAG_STACK 1u
+#define MT_EFLAG_TIMEOUT 2u
+#define MT_EFLAG_TRACK 4u
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 normalize(float3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+__device__ __forceinline__ float maxabs3(float3 p) { return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter layout:
+// (pixel or scan index, sample index, vertex index, group); key = seed.
+// Uniforms are the top 24 bits times 2^-24, exact in float, in [0, 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+
+#define G_NEE 0u
+#define G_SCATTER 1u
+#define G_TRACK 0x100u
+#define G_RATIO 0x10000u
+
+struct Rng {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint4 raw(uint32_t a, uint32_t b, uint32_t c, uint32_t d) const {
+        return philox4x32_10(make_uint4(a, b, c, d), k0, k1);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// frames and sampling maps
+// ---------------------------------------------------------------------------
+// Orthonormal basis from a unit vector (Duff et al., JCGT 2017); n.z >= 0 (and
+// -0) takes the positive branch.
+__device__ __forceinline__ void onb(float3 n, float3 &t, float3 &b) {
+    const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + n.z);
+    const float c = n.x * n.y * a;
+    t = f3(1.0f + sg * n.x * n.x * a, sg * c, -sg * n.x);
+    b = f3(c, sg + n.y * n.y * a, -n.y);
+}
+__device__ __forceinline__ float3 to_local(float3 w, float3 t, float3 b, float3 n) {
+    return f3(dot(w, t), dot(w, b), dot(w, n));
+}
+__device__ __forceinline__ float3 to_world(float3 l, float3 t, float3 b, float3 n) {
+    return t * l.x + b * l.y + n * l.z;
+}
+// ray-origin offset along the side normal: 1e-4 * max(1, |p|_inf)
+__device__ __forceinline__ float eps_of(float3 p) { return 1e-4f * fmaxf(1.0f, maxabs3(p)); }
+
+// uniform point on a triangle: b0 = 1 - sqrt(u1), b1 = u2 sqrt(u1)
+__device__ __forceinline__ float3 tri_point(float3 v0, float3 v1, float3 v2, float u1, float u2) {
+    const float su = sqrtf(u1);
+    const float b0 = 1.0f - su, b1 = u2 * su, b2 = 1.0f - b0 - b1;
+    return v0 * b0 + v1 * b1 + v2 * b2;
+}
+
+// ---------------------------------------------------------------------------
+// BSDFs in the local frame (z = side normal).  Lambert: albedo/pi with cosine
+// sampling.  GGX conductor: D GGX, Smith height-correlated G2, Schlick F with
+// F0 = albedo, visible-normal sampling (Heitz, JCGT 2018).
+// ---------------------------------------------------------------------------
+struct Mat {
+    float3 alb;
+    float rough; // < 0 marks Lambert
+};
+
+__device__ __forceinline__ float ggx_lambda(float a2, float3 w) {
+    const float s2 = w.x * w.x + w.y * w.y;
+    return 0.5f * (-1.0f + sqrtf(1.0f + a2 * s2 / (w.z * w.z)));
+}
+
+// f (per channel) and the solid-angle pdf of bsdf_sample for (wo, wi)
+__device__ __forceinline__ void bsdf_eval(const Mat &m, float3 wo, float3 wi, float3 &f, float &pdf) {
+    f = f3(0.f, 0.f, 0.f);
+    pdf = 0.f;
+    if (wo.z <= 0.f || wi.z <= 0.f) return;
+    if (m.rough < 0.f) {
+        f = m.alb * (1.0f / MT_PI);
+        pdf = wi.z * (1.0f / MT_PI);
+        return;
+    }
+    const float a = fmaxf(m.rough, 1e-4f), a2 = a * a;
+    const float3 h = normalize(wo + wi);
+    const float k = h.z * h.z * (a2 - 1.0f) + 1.0f;
+    const float D = a2 / (MT_PI * k * k);
+    const float lo = ggx_lambda(a2, wo), li = ggx_lambda(a2, wi);
+    const float G2 = 1.0f / (1.0f + lo + li), G1o = 1.0f / (1.0f + lo);
+    const float c = 1.0f - dot(wi, h);
+    const float c2 = c * c, m5 = c2 * c2 * c;
+    const float3 F = f3(m.alb.x + (1.f - m.alb.x) * m5, m.alb.y + (1.f - m.alb.y) * m5, m.alb.z + (1.f - m.alb.z) * m5);
+    f = F * (D * G2 / (4.0f * wo.z * wi.z));
+    pdf = G1o * D / (4.0f * wo.z);
+}
+
+// d f_c / d albedo_c divided by f_c
+__device__ __forceinline__ float3 bsdf_dratio(const Mat &m, float3 wo, float3 wi) {
+    if (m.rough < 0.f) return f3(1.0f / m.alb.x, 1.0f / m.alb.y, 1.0f / m.alb.z);
+    const float3 h = normalize(wo + wi);
+    const float c = 1.0f - dot(wi, h);
+    const float c2 = c * c, m5 = c2 * c2 * c;
+    return f3((1.f - m5) / (m.alb.x + (1.f - m.alb.x) * m5), (1.f - m5) / (m.alb.y + (1.f - m.alb.y) * m5),
+              (1.f - m5) / (m.alb.z + (1.f - m.alb.z) * m5));
+}
+
+__device__ __forceinline__ bool bsdf_sample(const Mat &m, float3 wo, float u0, float u1, float3 &wi) {
+    if (m.rough < 0.f) {
+        const float r = sqrtf(u0), ph = 2.0f * MT_PI * u1;
+        float s, c;
+        sincosf(ph, &s, &c);
+        wi = f3(r * c, r * s, sqrtf(fmaxf(0.f, 1.0f - u0)));
+        return wi.z > 0.f;
+    }
+    const float a = fmaxf(m.rough, 1e-4f);
+    const float3 vh = normalize(f3(a * wo.x, a * wo.y, wo.z));
+    const float l2 = vh.x * vh.x + vh.y * vh.y;
+    const float3 T1 = l2 > 0.f ? f3(-vh.y, vh.x, 0.f) * rsqrtf(l2) : f3(1.f, 0.f, 0.f);
+    const float3 T2 = cross(vh, T1);
+    const float r = sqrtf(u0), ph = 2.0f * MT_PI * u1;
+    float s, c;
+    sincosf(ph, &s, &c);
+    const float t1 = r * c;
+    float t2 = r * s;
+    const float sh = 0.5f * (1.0f + vh.z);
+    t2 = (1.0f - sh) * sqrtf(fmaxf(0.f, 1.0f - t1 * t1)) + sh * t2;
+    const float3 nh = T1 * t1 + T2 * t2 + vh * sqrtf(fmaxf(0.f, 1.0f - t1 * t1 - t2 * t2));
+    const float3 ne = normalize(f3(a * nh.x, a * nh.y, fmaxf(0.f, nh.z)));
+    wi = ne * (2.0f * dot(wo, ne)) - wo;
+    return wi.z > 0.f;
+}
+
+// Henyey-Greenstein phase function; cos_theta between propagation directions
+__device__ __forceinline__ float hg_eval(float g, float c) {
+    const float d = 1.0f + g * g - 2.0f * g * c;
+    return (1.0f - g * g) / (4.0f * MT_PI * d * sqrtf(d));
+}
+__device__ __forceinline__ float3 hg_sample(float g, float3 dir, float u0, float u1) {
+    float c;
+    if (fabsf(g) < 1e-3f) c = 1.0f - 2.0f * u0;
+    else {
+        const float q = (1.0f - g * g) / (1.0f - g + 2.0f * g * u0);
+        c = (1.0f + g * g - q * q) / (2.0f * g);
+    }
+    c = fminf(1.0f, fmaxf(-1.0f, c));
+    const float sn = sqrtf(fmaxf(0.f, 1.0f - c * c)), ph = 2.0f * MT_PI * u1;
+    float s, co;
+    sincosf(ph, &s, &co);
+    float3 t, b;
+    onb(dir, t, b);
+    return to_world(f3(sn * co, sn * s, c), t, b, dir);
+}
+
+// ---------------------------------------------------------------------------
+// device view of a scene (passed by value to kernels)
+// ---------------------------------------------------------------------------
+struct LightUnit {
+    float4 v0;  // xyz, w = area
+    float4 v1;  // xyz, w = pick probability
+    float4 v2;  // xyz, w = emitter index (int bits)
+    float4 n;   // unit winding normal, w = original triangle index (int bits), -1 for a point emitter
+};
+
+struct DevScene {
+    const uint4 *nodes;    // 2 x uint4 per internal node
+    const float4 *tris;    // 3 x float4 per leaf-ordered triangle, v0.w = original index
+    const float4 *mats;    // per original triangle: albedo, w = GGX roughness or -1 (Lambert)
+    const int32_t *tri_unit; // per original triangle: light unit or -1
+    const int32_t *leaf_of;  // per original triangle: its leaf-order index
+    const uint32_t *unit_cdf; // ceil(cdf * 2^24)
+    const LightUnit *units;
+    const float4 *em_rad;  // per emitter: radiance (rgb)
+    int32_t n_units;
+    int32_t n_tris;
+    int32_t n_em;
+    int32_t has_medium;
+    float3 cam_o, cam_f, cam_r, cam_u;
+    float tan_half;
+    float3 q_lo, q_scale;  // BVH plane quantisation: plane = q_lo + q * q_scale
+    // medium
+    const float *dens;     // [z][y][x]
+    int32_t rx, ry, rz;
+    float3 m_lo, m_hi;
+    float m_major;
+    const float *m_params; // device [2]: albedo, g
+    uint32_t *err;
+    unsigned long long *counters; // 8 counters
+};
+
+__device__ __forceinline__ void raise_err(const DevScene &s, uint32_t bit) { atomicOr(s.err, bit); }

@@ -1,0 +1,60 @@
+// mt_launch.h -- parameter blocks passed from the C-ABI layer to the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/mt_api.h"
+#include "mt_common.cuh"
+
+#define MT_MAX_BWD_DEPTH 16
+
+struct RenderParams {
+    int32_t H, W, T, D;        // film size; D = bins per pixel privatised in shared memory
+    float start, width, scale; // time window (OPL metres) and 1/spp (1 when accumulating)
+    uint32_t flags;
+    int32_t spp, max_depth;
+    uint32_t sample_offset;
+    uint32_t k0, k1;           // Philox key = seed
+    int32_t tile_px, n_tiles, tiles_per_row;
+    float *film, *steady;
+    const float *gfilm, *gsteady;
+    float *galb, *grad, *gmed;
+    mt_contrib *dump;
+    long long dump_cap;
+    unsigned long long *dump_count;
+    int *tile_counter;
+    int32_t n_em_smem;         // emitters whose radiance gradients are summed in shared memory
+};
+
+struct NlosParams {
+    int32_t T, D;
+    float start, width, scale;
+    uint32_t flags;
+    int32_t spp, mode;
+    uint32_t sample_offset, k0, k1;
+    const float *lasers, *sensors;
+    int32_t n_l, n_s;
+    float3 nw;
+    float fw;                  // wall albedo / pi
+    int32_t hidden_first, hidden_n;
+    const uint32_t *hcdf;      // ceil(cdf * 2^24) over hidden triangles (original order)
+    float hidden_area;
+    int32_t tile, n_tiles;
+    float *film, *steady;
+    float4 *ysamp;             // exhaustive: 2 per (laser, sample): (y, |x_l - y|), (side normal, partial weight or 0)
+    int32_t *ysamp_tri;        // exhaustive: hidden triangle of each sample
+    mt_contrib *dump;
+    long long dump_cap;
+    unsigned long long *dump_count;
+    int *tile_counter;
+};
+
+struct LaunchCfg {
+    int threads, tile, ctas_per_sm, num_sms;
+    size_t smem_bytes;
+};
+
+mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, int mode, bool counters,
+                           cudaStream_t st);
+mt_status mt_launch_nlos(const DevScene &s, const NlosParams &p, const LaunchCfg &cfg, bool dump, bool counters,
+                         cudaStream_t st);

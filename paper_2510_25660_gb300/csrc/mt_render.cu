@@ -1,0 +1,588 @@
+// mt_render.cu -- persistent transient path-tracing megakernel.
+//
+// One launch renders a whole (H, W, T) film (arXiv 2510.25660 Sec. 3):
+//   * CTAs pull pixel tiles from a global counter; a tile is tile_px
+//     consecutive pixels of one row, so its film rows are one contiguous span.
+//   * The tile's time histograms live in shared memory (bins [0, D) of every
+//     pixel; bins >= D go straight to global memory with red.add) and are
+//     written to HBM once per tile with coalesced stores (path reuse:
+//     every contribution lands in the bin of its own optical path length).
+//   * Warps keep all 32 lanes busy: a lane whose path ended takes the next
+//     path of the tile (warp-aggregated claim on a shared counter), so every
+//     loop iteration advances 32 paths by one vertex.
+//   * Each vertex traces an extension ray (closest hit) and a shadow ray (any
+//     hit) for next-event estimation with power-heuristic MIS; in a medium
+//     (Sec. 4.1) free flights use delta tracking and shadow rays ratio
+//     tracking, and their lengths add to the optical path length.
+//   * MODE_BWD replays the same paths from their Philox keys (Sec. 4.4,
+//     path replay): contributions gather dL/dfilm from the tile (staged in
+//     shared memory), per-vertex sums are kept in local memory and the
+//     per-triangle albedo gradients are scattered once per vertex at path end.
+#include "mt_common.cuh"
+#include "mt_internal.h"
+#include "mt_launch.h"
+#include "mt_trace.cuh"
+
+namespace {
+
+constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2;
+
+struct VRec {
+    int32_t tri;   // original triangle index, -1 for a medium vertex
+    float3 r;      // d(factor)/factor of the continuation
+    float3 S;      // sum of g*C of contributions attached to this vertex
+    float3 own;    // own-direction gradient term of this vertex's next-event estimate
+};
+
+struct PathState {
+    float3 o, d, beta;
+    float opl, prev_pdf;
+    int depth, lp;
+    uint32_t pix, smp;
+    float3 acc;     // steady-image sum of this path (forward)
+};
+
+struct Counters {
+    uint32_t vertices = 0, paths = 0, contribs = 0, rays = 0, smem_splats = 0, gmem_splats = 0;
+    TraceCnt tc{0, 0};
+};
+
+__device__ __forceinline__ float density_at(const DevScene &s, float3 p) {
+    const float gx = (p.x - s.m_lo.x) / (s.m_hi.x - s.m_lo.x) * s.rx - 0.5f;
+    const float gy = (p.y - s.m_lo.y) / (s.m_hi.y - s.m_lo.y) * s.ry - 0.5f;
+    const float gz = (p.z - s.m_lo.z) / (s.m_hi.z - s.m_lo.z) * s.rz - 0.5f;
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const float fx = gx - fx0, fy = gy - fy0, fz = gz - fz0;
+    const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+    const int x0 = min(max(ix, 0), s.rx - 1), x1 = min(max(ix + 1, 0), s.rx - 1);
+    const int y0 = min(max(iy, 0), s.ry - 1), y1 = min(max(iy + 1, 0), s.ry - 1);
+    const int z0 = min(max(iz, 0), s.rz - 1), z1 = min(max(iz + 1, 0), s.rz - 1);
+    auto D = [&](int x, int y, int z) { return __ldg(&s.dens[((size_t)z * s.ry + y) * s.rx + x]); };
+    const float c00 = D(x0, y0, z0) * (1.f - fx) + D(x1, y0, z0) * fx;
+    const float c10 = D(x0, y1, z0) * (1.f - fx) + D(x1, y1, z0) * fx;
+    const float c01 = D(x0, y0, z1) * (1.f - fx) + D(x1, y0, z1) * fx;
+    const float c11 = D(x0, y1, z1) * (1.f - fx) + D(x1, y1, z1) * fx;
+    const float c0 = c00 * (1.f - fy) + c10 * fy, c1 = c01 * (1.f - fy) + c11 * fy;
+    return c0 * (1.f - fz) + c1 * fz;
+}
+
+// overlap of the ray with the medium box, clipped to [0, tmax]
+__device__ __forceinline__ bool medium_span(const DevScene &s, float3 o, float3 d, float tmax, float &a, float &b) {
+    float t0 = 0.f, t1 = tmax;
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    const float lo[3] = {s.m_lo.x, s.m_lo.y, s.m_lo.z}, hi[3] = {s.m_hi.x, s.m_hi.y, s.m_hi.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (dd[k] == 0.f) {
+            if (oo[k] < lo[k] || oo[k] > hi[k]) return false;
+            continue;
+        }
+        float ta = (lo[k] - oo[k]) / dd[k], tb = (hi[k] - oo[k]) / dd[k];
+        if (ta > tb) {
+            const float x = ta;
+            ta = tb;
+            tb = x;
+        }
+        t0 = fmaxf(t0, ta);
+        t1 = fminf(t1, tb);
+    }
+    if (t0 >= t1) return false;
+    a = t0;
+    b = t1;
+    return true;
+}
+
+// ratio-tracking transmittance over [0, dist]; ok = false if the step cap was hit
+__device__ __forceinline__ float transmittance(const DevScene &s, const Rng &rng, float3 o, float3 d, float dist,
+                                               uint32_t pix, uint32_t smp, uint32_t depth, bool &ok) {
+    ok = true;
+    float a, b;
+    if (!medium_span(s, o, d, dist, a, b)) return 1.0f;
+    float T = 1.0f, t = a;
+    const float inv = 1.0f / s.m_major;
+    for (uint32_t j = 0;; ++j) {
+        if (j >= MT_TRACK_STEPS) {
+            ok = false;
+            return 0.f;
+        }
+        const uint4 R = rng.raw(pix, smp, depth, G_RATIO + j);
+        t += -logf(1.0f - u24(R.x)) * inv;
+        if (t >= b) break;
+        T *= 1.0f - density_at(s, o + d * t) * inv;
+    }
+    return T;
+}
+
+__device__ __forceinline__ float mis2(float a, float b) { return a * a / (a * a + b * b); }
+
+__device__ __forceinline__ int pick_unit(const DevScene &s, uint32_t u) {
+    int lo = 0, hi = s.n_units - 1;
+    const uint32_t key = u >> 8;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key < __ldg(&s.unit_cdf[mid])) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int MODE, bool MEDIA, bool CNT>
+struct Tracer {
+    const DevScene &s;
+    const RenderParams &p;
+    float *hist, *steady_s, *em_acc;
+    float &med_acc;
+    Counters &cnt;
+    VRec *vr;  // backward only
+    Rng rng;
+
+    // one contribution c (cb = c without radiance) of emitter em at OPL opl;
+    // kind 0 = found by the path at vertex `vert`, kind 1 = next-event at `vert`
+    __device__ __forceinline__ void deposit(PathState &ps, int vert, int kind, int tri, float opl, float3 c,
+                                            float3 cb, int em, float3 own_r) {
+        const float x = (opl - p.start) / p.width;
+        const bool in = x >= 0.f && x < (float)p.T;
+        const int bin = in ? (int)x : -1;
+        c = c * p.scale;
+        cb = cb * p.scale;
+        cnt.contribs++;
+        if (MODE != MODE_BWD) {
+            if (in) {
+                if (bin < p.D) {
+                    float *h = hist + ((size_t)ps.lp * p.D + bin) * 3;
+                    atomicAdd(h, c.x);
+                    atomicAdd(h + 1, c.y);
+                    atomicAdd(h + 2, c.z);
+                    cnt.smem_splats++;
+                } else {
+                    float *h = p.film + ((size_t)ps.pix * p.T + bin) * 3;
+                    atomicAdd(h, c.x);
+                    atomicAdd(h + 1, c.y);
+                    atomicAdd(h + 2, c.z);
+                    cnt.gmem_splats++;
+                }
+            }
+            ps.acc = ps.acc + c;
+            if (MODE == MODE_DUMP) {
+                const unsigned long long slot = atomicAdd(p.dump_count, 1ull);
+                if ((long long)slot < p.dump_cap) {
+                    mt_contrib r;
+                    r.pixel = (int32_t)ps.pix;
+                    r.sample = (int32_t)ps.smp;
+                    r.depth = vert;
+                    r.kind = kind;
+                    r.tri = tri;
+                    r.bin = in ? bin : (int)floorf(x);
+                    r.opl = opl;
+                    r.c[0] = c.x / p.scale;
+                    r.c[1] = c.y / p.scale;
+                    r.c[2] = c.z / p.scale;
+                    p.dump[slot] = r;
+                }
+            }
+        } else {
+            float3 g = f3(steady_s[ps.lp * 3], steady_s[ps.lp * 3 + 1], steady_s[ps.lp * 3 + 2]);
+            if (in) {
+                const float *h = bin < p.D ? hist + ((size_t)ps.lp * p.D + bin) * 3
+                                           : p.gfilm + ((size_t)ps.pix * p.T + bin) * 3;
+                g = g + f3(h[0], h[1], h[2]);
+            }
+            const float3 gc = mul(g, c);
+            VRec &v = vr[vert];
+            if (kind == 0) v.S = v.S + gc;
+            else {
+                v.S = v.S + gc;
+                v.own = v.own + mul(gc, own_r);
+            }
+            const float3 gr = mul(g, cb);
+            if (p.n_em_smem > 0) {
+                atomicAdd(&em_acc[em * 3], gr.x);
+                atomicAdd(&em_acc[em * 3 + 1], gr.y);
+                atomicAdd(&em_acc[em * 3 + 2], gr.z);
+            } else {
+                atomicAdd(&p.grad[em * 3], gr.x);
+                atomicAdd(&p.grad[em * 3 + 1], gr.y);
+                atomicAdd(&p.grad[em * 3 + 2], gr.z);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void begin(PathState &ps, int j, int pix0, int x0, int ty) {
+        ps.lp = j / p.spp;
+        const int sI = j - ps.lp * p.spp;
+        ps.pix = (uint32_t)(pix0 + ps.lp);
+        ps.smp = p.sample_offset + (uint32_t)sI;
+        const uint4 R = rng.raw(ps.pix, ps.smp, 0, 0);
+        const bool center = p.flags & MT_PIXEL_CENTER;
+        const float jx = center ? 0.5f : u24(R.x), jy = center ? 0.5f : u24(R.y);
+        const int px = x0 + ps.lp;
+        const float sx = (2.0f * ((float)px + jx) / (float)p.W - 1.0f) * s.tan_half;
+        const float sy = (1.0f - 2.0f * ((float)ty + jy) / (float)p.H) * s.tan_half * ((float)p.H / (float)p.W);
+        ps.o = s.cam_o;
+        ps.d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
+        ps.beta = f3(1.f, 1.f, 1.f);
+        ps.opl = 0.f;
+        ps.prev_pdf = 0.f;
+        ps.depth = 1;
+        ps.acc = f3(0.f, 0.f, 0.f);
+        cnt.paths++;
+        if (MODE == MODE_BWD) vr[0].tri = -2;
+    }
+
+    __device__ __forceinline__ void end(PathState &ps) {
+        if (MODE != MODE_BWD) {
+            if (ps.acc.x != 0.f || ps.acc.y != 0.f || ps.acc.z != 0.f) {
+                atomicAdd(&steady_s[ps.lp * 3], ps.acc.x);
+                atomicAdd(&steady_s[ps.lp * 3 + 1], ps.acc.y);
+                atomicAdd(&steady_s[ps.lp * 3 + 2], ps.acc.z);
+            }
+        } else {
+            // suffix sums: vertex i receives the contributions of later vertices
+            float3 P = f3(0.f, 0.f, 0.f);
+            for (int i = ps.depth; i >= 1; --i) {
+                const VRec &v = vr[i];
+                if (v.tri == -2) continue;
+                const float3 gi = mul(P, v.r) + v.own;
+                if (v.tri >= 0) {
+                    if (gi.x != 0.f || gi.y != 0.f || gi.z != 0.f) {
+                        float *g = p.galb + (size_t)v.tri * 3;
+                        atomicAdd(g, gi.x);
+                        atomicAdd(g + 1, gi.y);
+                        atomicAdd(g + 2, gi.z);
+                    }
+                } else {
+                    med_acc_add(gi.x + gi.y + gi.z);
+                }
+                P = P + v.S;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void med_acc_add(float v) {
+        if (v != 0.f) atomicAdd(&med_acc, v);
+    }
+
+    __device__ __forceinline__ void reset_vertex(int i) {
+        if (MODE == MODE_BWD) {
+            vr[i].tri = -2;
+            vr[i].r = f3(0.f, 0.f, 0.f);
+            vr[i].S = f3(0.f, 0.f, 0.f);
+            vr[i].own = f3(0.f, 0.f, 0.f);
+        }
+    }
+
+    // next-event estimate from x (surface: side normal n and frame, or medium)
+    __device__ __forceinline__ void nee(PathState &ps, float3 x, bool surface, float3 n, float3 tb, float3 bb,
+                                        float3 wol, const Mat &m) {
+        const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_NEE);
+        const int un = pick_unit(s, R.x);
+        const LightUnit U = s.units[un];
+        const int em = __float_as_int(U.v2.w);
+        const bool is_pt = __float_as_int(U.n.w) < 0;
+        const float3 y = is_pt ? xyz(U.v0) : tri_point(xyz(U.v0), xyz(U.v1), xyz(U.v2), u24(R.y), u24(R.z));
+        const float3 xo = surface ? x + n * eps_of(x) : x;
+        const float3 dl = y - xo;
+        const float dist = sqrtf(dot(dl, dl));
+        const float3 wi = dl * (1.0f / dist);
+        const float cx = surface ? dot(n, wi) : 1.0f;
+        const float cy = is_pt ? 1.0f : -dot(xyz(U.n), wi);
+        if (!(cx > 0.f && cy > 0.f && dist > 0.f)) return;
+        const float tmax = dist - (is_pt ? 0.0f : eps_of(y));
+        cnt.rays++;
+        const RayT sr = make_ray(s, xo, wi);
+        if (trace_any<CNT>(s, sr, tmax, cnt.tc)) return;
+        float Tr = 1.0f;
+        if (MEDIA) {
+            bool ok;
+            Tr = transmittance(s, rng, xo, wi, tmax, ps.pix, ps.smp, (uint32_t)ps.depth, ok);
+            if (!ok) {
+                raise_err(s, MT_EFLAG_TRACK);
+                return;
+            }
+            if (Tr == 0.f) return;
+        }
+        const float pick = U.v1.w;
+        float3 fc;
+        float3 own = f3(0.f, 0.f, 0.f);
+        float w = 1.0f, geo;
+        if (surface) {
+            const float3 wil = to_local(wi, tb, bb, n);
+            float pb;
+            bsdf_eval(m, wol, wil, fc, pb);
+            fc = fc * cx;
+            if (is_pt) geo = 1.0f / (dist * dist) / pick;
+            else {
+                const float pA = pick / U.v0.w;
+                geo = cy / (dist * dist) / pA;
+                if (!MEDIA) w = mis2(pA * dist * dist / cy, pb);
+            }
+            if (MODE == MODE_BWD) own = bsdf_dratio(m, wol, wil);
+        } else {
+            const float ph = hg_eval(s.m_params[1], dot(ps.d, wi));
+            fc = f3(ph, ph, ph);
+            geo = is_pt ? 1.0f / (dist * dist) / pick : cy / (dist * dist) / (pick / U.v0.w);
+            if (MODE == MODE_BWD) {
+                const float ia = 1.0f / s.m_params[0];
+                own = f3(ia, ia, ia);
+            }
+        }
+        const float k = geo * w * Tr;
+        const float3 cb = mul(ps.beta, fc) * k;
+        const float4 Le = s.em_rad[em];
+        const float3 c = mul(cb, xyz(Le));
+        if (c.x == 0.f && c.y == 0.f && c.z == 0.f) return;
+        deposit(ps, ps.depth, 1, __float_as_int(U.n.w), ps.opl + dist, c, cb, em, own);
+    }
+
+    // advance the path by one vertex; returns false when it ends
+    __device__ bool step(PathState &ps) {
+        if (MODE == MODE_BWD) reset_vertex(ps.depth);
+        const RayT r = make_ray(s, ps.o, ps.d);
+        float th;
+        int orig;
+        cnt.rays++;
+        const int k = trace_closest<CNT>(s, r, INFINITY, th, orig, cnt.tc);
+        if (MEDIA) {
+            float ma, mb;
+            const float tsurf = k >= 0 ? th : 1e30f;
+            if (medium_span(s, ps.o, ps.d, tsurf, ma, mb)) {
+                float t = ma;
+                bool collided = false;
+                const float inv = 1.0f / s.m_major;
+                for (uint32_t j = 0;; ++j) {
+                    if (j >= MT_TRACK_STEPS) {
+                        raise_err(s, MT_EFLAG_TRACK);
+                        return false;
+                    }
+                    const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)(ps.depth - 1), G_TRACK + j);
+                    t += -logf(1.0f - u24(R.x)) * inv;
+                    if (t >= mb) break;
+                    if (u24(R.y) < density_at(s, ps.o + ps.d * t) * inv) {
+                        collided = true;
+                        break;
+                    }
+                }
+                if (collided) {
+                    cnt.vertices++;
+                    const float3 x = ps.o + ps.d * t;
+                    if (!(ps.depth == 1 && (p.flags & MT_UNWARP))) ps.opl += t;
+                    const float alb = s.m_params[0];
+                    ps.beta = ps.beta * alb;
+                    if (MODE == MODE_BWD) {
+                        vr[ps.depth].tri = -1;
+                        const float ia = 1.0f / alb;
+                        vr[ps.depth].r = f3(ia, ia, ia);
+                    }
+                    if (ps.depth == p.max_depth) return false;
+                    if (s.n_units > 0) nee(ps, x, false, f3(0, 0, 1), f3(1, 0, 0), f3(0, 1, 0), f3(0, 0, 1), Mat{});
+                    const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
+                    ps.d = hg_sample(s.m_params[1], ps.d, u24(R.x), u24(R.y));
+                    ps.o = x;
+                    ps.depth++;
+                    return true;
+                }
+            }
+        }
+        if (k < 0) return false;
+        cnt.vertices++;
+        const float3 x = ps.o + ps.d * th;
+        if (!(ps.depth == 1 && (p.flags & MT_UNWARP))) ps.opl += th;
+        const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
+        const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+        const float3 wo = -ps.d;
+        const float cwo = dot(ng, wo);
+        const int unit = __ldg(&s.tri_unit[orig]);
+        if (unit >= 0 && cwo > 0.f && (ps.depth == 1 || !MEDIA)) {
+            const LightUnit U = s.units[unit];
+            float w = 1.0f;
+            if (ps.depth > 1) {
+                const float pl = (U.v1.w / U.v0.w) * th * th / cwo;
+                w = mis2(ps.prev_pdf, pl);
+            }
+            const int em = __float_as_int(U.v2.w);
+            const float3 cb = ps.beta * w;
+            const float3 c = mul(cb, xyz(s.em_rad[em]));
+            deposit(ps, ps.depth, 0, orig, ps.opl, c, cb, em, f3(0.f, 0.f, 0.f));
+        }
+        if (ps.depth == p.max_depth) return false;
+        const float3 n = cwo >= 0.f ? ng : -ng;
+        float3 tb, bb;
+        onb(n, tb, bb);
+        const float3 wol = to_local(wo, tb, bb, n);
+        const float4 mm = __ldg(&s.mats[orig]);
+        const Mat m{xyz(mm), mm.w};
+        if (MODE == MODE_BWD) vr[ps.depth].tri = orig;
+        if (s.n_units > 0) nee(ps, x, true, n, tb, bb, wol, m);
+        const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
+        float3 wil;
+        if (!bsdf_sample(m, wol, u24(R.x), u24(R.y), wil)) return false;
+        float3 f;
+        float pb;
+        bsdf_eval(m, wol, wil, f, pb);
+        if (!(pb > 0.f)) return false;
+        ps.beta = mul(ps.beta, f) * (wil.z / pb);
+        if (MODE == MODE_BWD) vr[ps.depth].r = bsdf_dratio(m, wol, wil);
+        ps.prev_pdf = pb;
+        ps.o = x + n * eps_of(x);
+        ps.d = to_world(wil, tb, bb, n);
+        ps.depth++;
+        return true;
+    }
+};
+
+template <int MODE, bool MEDIA, bool CNT>
+__global__ void __launch_bounds__(256) k_render(const DevScene s, const RenderParams p) {
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    float *hist = smem;
+    float *steady_s = hist + (size_t)p.tile_px * p.D * 3;
+    float *em_acc = steady_s + p.tile_px * 3;
+    __shared__ int s_tile, s_next;
+    __shared__ float s_med;
+    const int lane = threadIdx.x & 31;
+    Counters cnt;
+    VRec vrec[MODE == MODE_BWD ? MT_MAX_BWD_DEPTH + 1 : 1];
+    if (MODE == MODE_BWD) {
+        for (int i = threadIdx.x; i < p.n_em_smem * 3; i += blockDim.x) em_acc[i] = 0.f;
+        if (threadIdx.x == 0) s_med = 0.f;
+    }
+    Tracer<MODE, MEDIA, CNT> tr{s, p, hist, steady_s, em_acc, s_med, cnt, vrec, Rng{p.k0, p.k1}};
+    const int hist_n = p.tile_px * p.D * 3;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(p.tile_counter, 1);
+            s_next = 0;
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= p.n_tiles) break;
+        const int ty = tile / p.tiles_per_row, tx = tile - ty * p.tiles_per_row;
+        const int x0 = tx * p.tile_px;
+        const int npx = min(p.tile_px, p.W - x0);
+        const int pix0 = ty * p.W + x0;
+        // stage the tile: zero the histograms, or load dL/dfilm for replay
+        if (MODE != MODE_BWD) {
+            for (int i = threadIdx.x; i < hist_n + p.tile_px * 3; i += blockDim.x) smem[i] = 0.f;
+        } else {
+            for (int i = threadIdx.x; i < npx * p.D * 3; i += blockDim.x) {
+                const int lp = i / (p.D * 3), r = i - lp * p.D * 3;
+                hist[i] = __ldg(&p.gfilm[((size_t)(pix0 + lp) * p.T) * 3 + r]);
+            }
+            for (int i = threadIdx.x; i < p.tile_px * 3; i += blockDim.x)
+                steady_s[i] = (p.gsteady && i < npx * 3) ? __ldg(&p.gsteady[(size_t)pix0 * 3 + i]) : 0.f;
+        }
+        __syncthreads();
+        const int n_paths = npx * p.spp;
+        PathState ps;
+        bool active = false, exhausted = false;
+        for (;;) {
+            if (!exhausted) {
+                const unsigned need = __ballot_sync(0xffffffffu, !active);
+                if (need) {
+                    const int leader = __ffs(need) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&s_next, __popc(need));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (base + __popc(need) >= n_paths) exhausted = true;
+                    if (!active) {
+                        const int j = base + __popc(need & ((1u << lane) - 1u));
+                        if (j < n_paths) {
+                            tr.begin(ps, j, pix0, x0, ty);
+                            active = true;
+                        }
+                    }
+                }
+            }
+            if (!__any_sync(0xffffffffu, active)) break;
+            if (active) {
+                if (!tr.step(ps)) {
+                    tr.end(ps);
+                    active = false;
+                }
+            }
+        }
+        __syncthreads();
+        if (MODE != MODE_BWD) {
+            // write the tile: bins < D of every pixel, then the steady image
+            const bool acc = p.flags & MT_ACCUMULATE;
+            if (p.D == p.T) {
+                const size_t n = (size_t)npx * p.T * 3;
+                float *dst = p.film + (size_t)pix0 * p.T * 3;
+                if (((n | (size_t)pix0 * p.T * 3) & 3) == 0 && (((uintptr_t)p.film) & 15) == 0) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dst);
+                    const float4 *s4 = reinterpret_cast<const float4 *>(hist);
+                    for (size_t i = threadIdx.x; i < n / 4; i += blockDim.x) {
+                        float4 v = s4[i];
+                        if (acc) {
+                            const float4 o = d4[i];
+                            v = make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w + o.w);
+                        }
+                        d4[i] = v;
+                    }
+                } else {
+                    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = acc ? dst[i] + hist[i] : hist[i];
+                }
+            } else {
+                const int row = p.D * 3;
+                for (int i = threadIdx.x; i < npx * row; i += blockDim.x) {
+                    const int lp = i / row, r = i - lp * row;
+                    float *d = p.film + (size_t)(pix0 + lp) * p.T * 3 + r;
+                    *d = acc ? *d + hist[i] : hist[i];
+                }
+            }
+            if (p.steady)
+                for (int i = threadIdx.x; i < npx * 3; i += blockDim.x) {
+                    float *d = p.steady + (size_t)pix0 * 3 + i;
+                    *d = acc ? *d + steady_s[i] : steady_s[i];
+                }
+        }
+        __syncthreads();
+    }
+    if (MODE == MODE_BWD) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.n_em_smem * 3; i += blockDim.x)
+            if (em_acc[i] != 0.f) atomicAdd(&p.grad[i], em_acc[i]);
+        if (threadIdx.x == 0 && p.gmed && s_med != 0.f) atomicAdd(p.gmed, s_med);
+    }
+    // counters: one atomic per warp and counter
+    unsigned long long v[8] = {cnt.vertices, cnt.paths, cnt.contribs, cnt.rays, cnt.tc.nodes, cnt.tc.tris,
+                               cnt.smem_splats, cnt.gmem_splats};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        unsigned long long x = v[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) atomicAdd(&s.counters[c], x);
+    }
+}
+
+template <int MODE, bool MEDIA, bool CNT>
+mt_status launch_one(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, cudaStream_t st) {
+    auto kern = k_render<MODE, MEDIA, CNT>;
+    const size_t smem = cfg.smem_bytes;
+    MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.threads, smem));
+    if (per_sm < 1) {
+        mt::set_error("render kernel does not fit: %d threads, %zu bytes of shared memory", cfg.threads, smem);
+        return MT_ERR_UNSUPPORTED;
+    }
+    if (cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cfg.ctas_per_sm);
+    const int grid = std::max(1, std::min(p.n_tiles, per_sm * cfg.num_sms));
+    kern<<<grid, cfg.threads, smem, st>>>(s, p);
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+}  // namespace
+
+mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, int mode, bool counters,
+                           cudaStream_t st) {
+    const bool media = s.has_medium;
+#define MT_DISPATCH(M)                                                                 \
+    if (media) return counters ? launch_one<M, true, true>(s, p, cfg, st) : launch_one<M, true, false>(s, p, cfg, st); \
+    return counters ? launch_one<M, false, true>(s, p, cfg, st) : launch_one<M, false, false>(s, p, cfg, st);
+    if (mode == 0) { MT_DISPATCH(MODE_FWD) }
+    if (mode == 1) { MT_DISPATCH(MODE_DUMP) }
+    MT_DISPATCH(MODE_BWD)
+#undef MT_DISPATCH
+}

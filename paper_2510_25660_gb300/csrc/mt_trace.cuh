@@ -1,0 +1,211 @@
+// mt_trace.cuh -- BVH traversal and ray/triangle intersection (device code).
+//
+// Visibility V and segment lengths of the path integral (arXiv 2510.25660,
+// Sec. 3 Eqs. 3 and 8) come from these queries.
+//
+// Node layout (32 bytes = one L2 sector, fetched as two 16-byte loads):
+//   a.x = lo0.x | lo0.y<<16   a.y = lo0.z | hi0.x<<16   a.z = hi0.y | hi0.z<<16
+//   a.w = lo1.x | lo1.y<<16   b.x = lo1.z | hi1.x<<16   b.y = hi1.y | hi1.z<<16
+//   b.z = child 0 reference   b.w = child 1 reference
+// The twelve planes are 16-bit fixed point in the scene box, rounded outward
+// (plane = q_lo + q * q_scale), so boxes are conservative.  A reference with
+// bit 31 clear is an internal node index; with bit 31 set it is a leaf of
+// ((ref >> 29) & 3) + 1 triangles starting at (ref & 0x1FFFFFFF); 0xFFFFFFFF
+// is an empty child.  Triangles are 48-byte records (three float4 vertices,
+// v0.w holding the original triangle index as int bits) in leaf order.
+#pragma once
+#include "mt_common.cuh"
+
+#define MT_EMPTY_REF 0xFFFFFFFFu
+
+struct RayT {
+    float3 o, d;
+    float3 sa, sb;   // slab parameter t = q * sa + sb for a quantised plane q
+    int kx, ky, kz;  // watertight test axes (Woop, Benthin, Wald, JCGT 2013)
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ RayT make_ray(const DevScene &s, float3 o, float3 d) {
+    RayT r;
+    r.o = o;
+    r.d = d;
+    // zero direction components are replaced by +-1e-20 for the slab test only
+    const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
+    const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
+    const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
+    const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
+    r.sa = f3(s.q_scale.x * ix, s.q_scale.y * iy, s.q_scale.z * iz);
+    r.sb = f3((s.q_lo.x - o.x) * ix, (s.q_lo.y - o.y) * iy, (s.q_lo.z - o.z) * iz);
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp3(d, kz) < 0.0f) {
+        const int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    const float dk = comp3(d, kz);
+    r.Sx = comp3(d, kx) / dk;
+    r.Sy = comp3(d, ky) / dk;
+    r.Sz = 1.0f / dk;
+    return r;
+}
+
+// 16-bit fixed point -> exact float via the 2^23 magic exponent
+__device__ __forceinline__ float q_lo16(uint32_t x) {
+    return __int_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8388608.0f;
+}
+__device__ __forceinline__ float q_hi16(uint32_t x) {
+    return __int_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8388608.0f;
+}
+
+__device__ __forceinline__ void slab(const RayT &r, float lx, float ly, float lz, float hx, float hy, float hz,
+                                     float tmax, float &tn, float &tf) {
+    const float x0 = fmaf(lx, r.sa.x, r.sb.x), x1 = fmaf(hx, r.sa.x, r.sb.x);
+    const float y0 = fmaf(ly, r.sa.y, r.sb.y), y1 = fmaf(hy, r.sa.y, r.sb.y);
+    const float z0 = fmaf(lz, r.sa.z, r.sb.z), z1 = fmaf(hz, r.sa.z, r.sb.z);
+    tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+    tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+}
+
+// Watertight ray/triangle test.  The edge functions are evaluated without
+// contraction so that a shared edge gives exactly opposite values in its two
+// triangles (no gaps).  Returns true with t = T/det when the ray crosses the
+// triangle (edges inclusive) at t > 0.
+__device__ __forceinline__ bool tri_hit(const RayT &r, float3 v0, float3 v1, float3 v2, float &t) {
+    const float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+    const float Akz = comp3(A, r.kz), Bkz = comp3(B, r.kz), Ckz = comp3(C, r.kz);
+    const float Ax = comp3(A, r.kx) - r.Sx * Akz, Ay = comp3(A, r.ky) - r.Sy * Akz;
+    const float Bx = comp3(B, r.kx) - r.Sx * Bkz, By = comp3(B, r.ky) - r.Sy * Bkz;
+    const float Cx = comp3(C, r.kx) - r.Sx * Ckz, Cy = comp3(C, r.ky) - r.Sy * Ckz;
+    const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    const float det = U + V + W;
+    if (det == 0.f) return false;
+    const float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    if (det > 0.f ? T <= 0.f : T >= 0.f) return false;
+    t = T / det;
+    return true;
+}
+
+struct TraceCnt {
+    uint32_t nodes, tris;
+};
+
+// Closest hit with t in (0, tmax); ties in t go to the smaller original index.
+// Returns the leaf-order triangle index (or -1) and writes t and the original index.
+template <bool CNT>
+__device__ __forceinline__ int trace_closest(const DevScene &s, const RayT &r, float tmax, float &t_out,
+                                             int &orig_out, TraceCnt &cnt) {
+    float tbest = tmax;
+    int best_k = -1, best_id = 0x7fffffff;
+    uint32_t st_ref[MT_STACK];
+    float st_t[MT_STACK];
+    int sp = 0;
+    uint32_t ref = 0;
+    for (;;) {
+        if (!(ref & 0x80000000u)) {
+            const uint4 a = __ldg(&s.nodes[2 * ref]);
+            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            if (CNT) cnt.nodes++;
+            float tn0, tf0, tn1, tf1;
+            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tbest, tn0, tf0);
+            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tbest, tn1, tf1);
+            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
+            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            if (h0 && h1) {
+                const bool f0 = tn0 <= tn1;
+                if (sp < MT_STACK) {
+                    st_ref[sp] = f0 ? b.w : b.z;
+                    st_t[sp] = f0 ? tn1 : tn0;
+                    ++sp;
+                } else {
+                    raise_err(s, MT_EFLAG_STACK);
+                }
+                ref = f0 ? b.z : b.w;
+                continue;
+            }
+            if (h0) { ref = b.z; continue; }
+            if (h1) { ref = b.w; continue; }
+        } else {
+            const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
+            for (int k = first; k < first + n; ++k) {
+                const float4 p0 = __ldg(&s.tris[3 * k]);
+                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
+                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                if (CNT) cnt.tris++;
+                float t;
+                if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                    const int id = __float_as_int(p0.w);
+                    if (t < tbest || (t == tbest && id < best_id)) {
+                        tbest = t;
+                        best_k = k;
+                        best_id = id;
+                    }
+                }
+            }
+        }
+        // pop the next entry whose entry distance does not exceed the best hit
+        for (;;) {
+            if (sp == 0) {
+                t_out = tbest;
+                orig_out = best_id;
+                return best_k;
+            }
+            --sp;
+            if (st_t[sp] <= tbest) {
+                ref = st_ref[sp];
+                break;
+            }
+        }
+    }
+}
+
+// Any hit with t in (0, tmax).
+template <bool CNT>
+__device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, float tmax, TraceCnt &cnt) {
+    uint32_t st_ref[MT_STACK];
+    int sp = 0;
+    uint32_t ref = 0;
+    for (;;) {
+        if (!(ref & 0x80000000u)) {
+            const uint4 a = __ldg(&s.nodes[2 * ref]);
+            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            if (CNT) cnt.nodes++;
+            float tn0, tf0, tn1, tf1;
+            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tmax, tn0, tf0);
+            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tmax, tn1, tf1);
+            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
+            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            if (h0 && h1) {
+                const bool f0 = tn0 <= tn1;
+                if (sp < MT_STACK) st_ref[sp++] = f0 ? b.w : b.z;
+                else raise_err(s, MT_EFLAG_STACK);
+                ref = f0 ? b.z : b.w;
+                continue;
+            }
+            if (h0) { ref = b.z; continue; }
+            if (h1) { ref = b.w; continue; }
+        } else {
+            const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
+            for (int k = first; k < first + n; ++k) {
+                const float4 p0 = __ldg(&s.tris[3 * k]);
+                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
+                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                if (CNT) cnt.tris++;
+                float t;
+                if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) return true;
+            }
+        }
+        if (sp == 0) return false;
+        ref = st_ref[--sp];
+    }
+}

@@ -1,0 +1,47 @@
+"""Helpers for the GPU parity tests: load the CUDA path and compare it with the oracle."""
+import numpy as np
+
+
+def build_and_load():
+    from paper_2510_25660_gb300 import build as b
+    b.build()
+    from paper_2510_25660_gb300 import api
+    api.load()
+    return api
+
+
+def match_contribs(gpu, ora, rel=1e-4, opl_tol=1e-4):
+    """Match per-contribution records by (pixel, sample, depth, kind) and
+    compare values; records present on one side only count as divergent.
+    Returns (n_matched, n_divergent, worst relative error, bin mismatches away from edges)."""
+    def key(r):
+        return (r["pixel"].astype(np.int64) << 32) | (r["sample"].astype(np.int64) << 12) | \
+               (r["depth"].astype(np.int64) << 2) | r["kind"].astype(np.int64)
+
+    kg, ko = key(gpu), key(ora)
+    assert len(np.unique(kg)) == len(kg), "duplicate GPU records"
+    assert len(np.unique(ko)) == len(ko), "duplicate oracle records"
+    common, ig, io = np.intersect1d(kg, ko, return_indices=True)
+    div = len(kg) + len(ko) - 2 * len(common)
+    g, o = gpu[ig], ora[io]
+    same_tri = g["tri"] == o["tri"]
+    div += int((~same_tri).sum())
+    g, o = g[same_tri], o[same_tri]
+    cg = g["c"].astype(np.float64)
+    co = o["c"]
+    scale = np.maximum(np.abs(co).max(axis=1, keepdims=True), 1e-30)
+    err = np.abs(cg - co) / scale
+    worst = float(err.max()) if len(err) else 0.0
+    bad_val = int((err.max(axis=1) > rel).sum()) if len(err) else 0
+    # time bins must agree except where the OPL is within 1e-5 m of a bin edge
+    dopl = np.abs(g["opl"].astype(np.float64) - o["opl"])
+    bin_bad = int(((g["bin"] != o["bin"]) & (dopl < opl_tol)).sum())
+    return len(common), div, worst, bad_val, bin_bad, dopl
+
+
+def rel_l2(a, b, mask=None):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

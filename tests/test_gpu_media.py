@@ -1,0 +1,72 @@
+"""GPU parity of transient volumetric path tracing (Sec. 4.1): delta tracking
+with the optical path length accumulated through the medium, ratio-tracked
+next-event estimation, medium-albedo gradients, and the bounded tracking loop
+reporting MT_ERR_TIMEOUT instead of hanging."""
+import numpy as np
+import pytest
+
+from gpu_util import build_and_load, match_contribs, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def media(oracle_mod, scenes_mod):
+    api = build_and_load()
+    sc = scenes_mod.media_scene(res=32)
+    return api, sc, api.Scene(sc), oracle_mod.OracleScene(sc)
+
+
+def test_media_contributions_and_film(media):
+    api, sc, s, osc = media
+    H = W = 64
+    T, start, width = 1024, 3.5, 0.005
+    spp, seed, depth = 4, 25660, 8
+    film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=3_000_000)
+    crop = (24, 40, 24, 40)
+    ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=3_000_000)
+    px = rec["pixel"] % W
+    py = rec["pixel"] // W
+    sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"])
+    assert nm > 2000
+    assert div <= 5e-3 * nm, (div, nm)
+    assert bad <= 5e-3 * nm, (bad, worst)
+    f = film.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+    assert rel_l2(f.sum(2), ref["film"].sum(2)) < 0.01
+
+
+def test_medium_albedo_gradient(media):
+    import torch
+    api, sc, s, osc = media
+    H = W = 32
+    T, start, width = 64, 3.5, 0.05
+    spp, seed, depth = 4, 5, 6
+    rng = np.random.default_rng(3)
+    g = rng.uniform(-1, 1, (H, W, T, 3))
+    ga, gr, gm = api.render_backward(s, T, start, width, spp, seed, depth, torch.from_numpy(g.astype(np.float32)).cuda())
+    ref = osc.render_backward(H, W, T, start, width, spp, seed, depth, g)
+    assert abs(gm.item() - ref["medium_albedo"]) < 0.02 * abs(ref["medium_albedo"])
+    ra = ref["albedo"]
+    assert np.linalg.norm(ga.cpu().numpy() - ra) < 0.02 * np.linalg.norm(ra)
+
+
+def test_bounded_tracking_reports_timeout(api_free_scene=None):
+    """A medium whose majorant is far above its typical density makes the
+    free-flight loop exceed its step cap; the kernel drops those paths, sets the
+    error word, and mt_sync reports MT_ERR_TIMEOUT (no hang, no fault)."""
+    import torch
+    from paper_2510_25660_gb300 import scenes
+    api = build_and_load()
+    sc = scenes.cornell_box()
+    dens = np.zeros((8, 8, 8), np.float32)
+    dens[0, 0, 0] = 5000.0  # majorant 5000 /m, a 2 m segment takes ~10^4 null steps
+    sc.medium = dict(lo=(-1, -1, -1), hi=(1, 1, 1), density=dens, albedo=0.9, g=0.0)
+    s = api.Scene(sc)
+    api.render(s, 8, 8, 16, 3.5, 0.1, 1, 1, 2)
+    with pytest.raises(api.MtError) as e:
+        s.sync()
+    assert e.value.status == api.MT_ERR_TIMEOUT
+    # the context stays usable
+    api.render(s, 8, 8, 16, 3.5, 0.1, 1, 1, 1)
+    torch.cuda.synchronize()
