@@ -128,20 +128,19 @@ def cpu_baseline(sc, film_spec, spp, depth, budget_s=15.0):
     f = film_spec
     cx, cy = f.W // 2, f.H // 2
     total_v, total_t, px = 0, 0.0, 0
-    side = 1
-    while total_t < budget_s and side <= 16:
-        crop = (cx - (side + 1) // 2, cx - (side + 1) // 2 + side, cy + 8 * side, cy + 8 * side + side)
+    row = 0
+    while total_t < budget_s and row < f.H // 2:
+        # one row segment of 8 pixels per round, walking down from the centre
+        crop = (cx - 4, cx + 4, cy + row, cy + row + 1)
         t0 = time.perf_counter()
         r = osc.render(f.H, f.W, 16, f.start_opl, f.bin_width, spp, 25660, depth, crop=crop)
-        dt = time.perf_counter() - t0
+        total_t += time.perf_counter() - t0
         total_v += r["counters"]["vertices"]
-        total_t += dt
-        px += side * side
-        if dt < budget_s / 8:
-            side *= 2
+        px += 8
+        row += 1
     return {"value": total_v / total_t, "unit": "path vertices/s", "cores": 1, "kind": "oracle",
-            "sample": f"{px} pixels of the 512x512 frame (central crops) x {spp} spp, max_depth {depth}, "
-                      f"FP64 single-threaded, {total_t:.1f} s"}
+            "sample": f"{px} pixels of the 512x512 frame (8-pixel row segments below the centre) x {spp} spp, "
+                      f"max_depth {depth}, FP64 single-threaded, {total_t:.1f} s"}
 
 
 def run_reference(args):
@@ -185,9 +184,12 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", default="", help="small: a few launches of each kernel on reduced sizes (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return profile_case(args.profile)
 
     import numpy as np
     import torch
@@ -319,6 +321,40 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def profile_case(which):
+    """Reduced-size launches of the hot kernels for ncu captures: the large
+    scene (full geometry) at 128x128 px, 32 spp; the differentiable scene's
+    backward at 64x64; a 16x16 confocal NLOS grid."""
+    import torch
+    from paper_2510_25660_gb300 import api, scenes
+    from paper_2510_25660_gb300 import build as b
+    b.build()
+    api.load()
+    sc = scenes.large_scene()
+    f = scenes.LARGE_FILM
+    s = api.Scene(sc)
+    film, steady = api.new_film(128, 128, f.T)
+    for _ in range(3):
+        api.render(s, 128, 128, f.T, f.start_opl, f.bin_width, 32, 1, 8, out=(film, steady))
+    s.sync()
+    del s
+    sc = scenes.diff_scene()
+    f = scenes.DIFF_FILM
+    s = api.Scene(sc)
+    film, steady = api.render(s, 64, 64, f.T, f.start_opl, f.bin_width, 16, 1, 8)
+    for _ in range(2):
+        api.render_backward(s, f.T, f.start_opl, f.bin_width, 16, 1, 8, torch.randn_like(film))
+    s.sync()
+    del s
+    sc = scenes.nlos_scene()
+    s = api.Scene(sc)
+    lasers = torch.from_numpy(scenes.wall_grid(16, 16)).cuda()
+    for _ in range(2):
+        api.render_nlos(s, lasers, None, api.MT_CONFOCAL, scenes.NLOS_T, 0.0, scenes.NLOS_W, 1024, 1)
+    s.sync()
+    print("profile case done")
 
 
 def secondary(api, autotune, scenes):
