@@ -240,6 +240,37 @@ mt_status mt_render_dump(mt_scene scene, mt_film film, const mt_scan *scan, int3
                          int32_t max_depth, uint64_t sample_offset, mt_contrib *d_dump, int64_t cap,
                          int64_t *d_count, void *stream);
 
+/* ---- allocation-free variant ----
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory at the time they render.  mt_render_nlos
+ * allocates (with cudaMalloc) a hidden-surface table the first time it sees a
+ * hidden triangle range and grows a per-scene sample buffer the first time it
+ * sees a larger exhaustive grid.  That fails or is unwelcome for code recording
+ * a CUDA graph (cudaMalloc is not allowed while a stream is being captured),
+ * for applications whose device memory is reserved up front by their own
+ * allocator or a fixed budget, and for loops that must not stall on an
+ * allocation.  mt_render_nlos_noalloc computes the same impulse responses as
+ * mt_render_nlos (same arguments, same result up to the order of
+ * floating-point additions) but keeps its per-call scratch in one static
+ * device array of 4.75 MiB compiled into libmt.so, which every GPU that loads
+ * the library holds until the process exits.  It calls no cudaMalloc or
+ * cudaFree.
+ *   - Limits: at most 65,536 hidden triangles and, for EXHAUSTIVE scans,
+ *     n_lasers * spp <= 131,072; larger requests return
+ *     MT_ERR_INVALID_ARGUMENT with a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) for that device; make that first call before any
+ *     stream capture.
+ *   - Each call rebuilds the hidden-surface table in the array and reads the
+ *     total hidden area back to the host, so it synchronises `stream` once.
+ *   - All calls share the array and leave their contents in it: calls that
+ *     overlap on the GPU (for example on two streams, or from two threads)
+ *     race and corrupt each other's results; serialise them.
+ *   - The scene still comes from mt_scene_create and the film, steady image
+ *     and scan points are the caller's. */
+mt_status mt_render_nlos_noalloc(mt_scene scene, mt_film film, const mt_scan *scan, int32_t spp, uint64_t seed,
+                                 uint64_t sample_offset, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ SIGNATURES = {
     "mt_probe_trace": (C.c_int, [_P, _P, _I64, _F, _I32, _P, _P, _P]),
     "mt_probe_bins": (C.c_int, [_P, _I64, _F, _F, _I32, _P, _P]),
     "mt_render_dump": (C.c_int, [_P, _P, _P, _I32, _U64, _I32, _U64, _P, _I64, _P, _P]),
+    "mt_render_nlos_noalloc": (C.c_int, [_P, _P, _P, _I32, _U64, _U64, _P]),
 }
 
 _lib = None
@@ -194,6 +195,10 @@ def mt_probe_trace(scene, d_rays, n, tmax, any_hit, d_tri, d_t, stream):
 
 def mt_probe_bins(d_opl, n, start, width, T, d_bin, stream):
     return _call("mt_probe_bins", d_opl, n, start, width, T, d_bin, stream)
+
+
+def mt_render_nlos_noalloc(scene, film, scan, spp, seed, sample_offset, stream):
+    return _call("mt_render_nlos_noalloc", scene, film, scan, spp, seed, sample_offset, stream)
 
 
 def mt_render_dump(scene, film, scan, spp, seed, max_depth, sample_offset, d_dump, cap, d_count, stream):

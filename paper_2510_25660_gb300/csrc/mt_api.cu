@@ -853,3 +853,115 @@ mt_status mt_probe_bins(const float *d_opl, int64_t n, float start, float width,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// NLOS capture that allocates nothing: the per-call scratch (tile counter,
+// hidden-surface table, per-laser hidden samples) lives in one static device
+// array compiled into the library instead of scene-owned buffers.
+// ---------------------------------------------------------------------------
+#define MT_NOALLOC_MAX_HIDDEN (1 << 16)
+#define MT_NOALLOC_MAX_SAMPLES (1 << 17)
+namespace {
+constexpr size_t NA_HDR = 256;                                    // tile counter at 0, hidden area at 16
+constexpr size_t NA_CDF = (size_t)MT_NOALLOC_MAX_HIDDEN * 4;      // u32 table per hidden triangle
+constexpr size_t NA_YS = (size_t)MT_NOALLOC_MAX_SAMPLES * 32;     // two float4 per (laser, sample)
+constexpr size_t NA_YT = (size_t)MT_NOALLOC_MAX_SAMPLES * 4;      // hidden triangle per (laser, sample)
+constexpr size_t NA_BYTES = NA_HDR + NA_CDF + NA_YS + NA_YT;     // 4.75 MiB
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_mt_noalloc_scratch[NA_BYTES];
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[256];
+
+// device address of the static array for the current device (looked up once per device)
+static mt_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    MT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        mt::set_error("device ordinal %d out of range", dev);
+        return MT_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        MT_CUDA_TRY(cudaGetSymbolAddress(&p, g_mt_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return MT_OK;
+}
+
+extern "C" mt_status mt_render_nlos_noalloc(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed,
+                                            uint64_t sample_offset, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    MT_CHECK_ARG(s != nullptr && f != nullptr && sc != nullptr, "scene, film or scan is NULL");
+    MT_CHECK_ARG(f->C == 1, "NLOS films have C = 1");
+    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || sc->mode == MT_EXHAUSTIVE, "unknown scan mode");
+    MT_CHECK_ARG(sc->lasers != nullptr && sc->n_lasers >= 1, "no laser points");
+    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || (sc->sensors != nullptr && sc->n_sensors >= 1), "no sensor points");
+    const long long rows = sc->mode == MT_EXHAUSTIVE ? (long long)sc->n_lasers * sc->n_sensors : sc->n_lasers;
+    MT_CHECK_ARG((long long)f->H * f->W == rows, "film H*W = %lld must equal the number of scan pairs %lld",
+                 (long long)f->H * f->W, rows);
+    MT_CHECK_ARG(sc->hidden_count >= 1 && (int64_t)sc->hidden_first + sc->hidden_count <= s->n_tris,
+                 "hidden triangle range out of bounds");
+    MT_CHECK_ARG(spp >= 1 && sample_offset + (uint64_t)spp <= 0xFFFFFFFFull, "bad spp / sample_offset");
+    const float nl = std::sqrt(sc->wall_normal[0] * sc->wall_normal[0] + sc->wall_normal[1] * sc->wall_normal[1] +
+                               sc->wall_normal[2] * sc->wall_normal[2]);
+    MT_CHECK_ARG(std::fabs(nl - 1.0f) < 1e-3f, "wall normal must be a unit vector");
+    MT_CHECK_ARG(sc->hidden_count <= (uint32_t)MT_NOALLOC_MAX_HIDDEN,
+                 "mt_render_nlos_noalloc: %u hidden triangles exceed the static scratch limit of %d",
+                 sc->hidden_count, MT_NOALLOC_MAX_HIDDEN);
+    MT_CHECK_ARG(sc->mode != MT_EXHAUSTIVE || (long long)sc->n_lasers * spp <= (long long)MT_NOALLOC_MAX_SAMPLES,
+                 "mt_render_nlos_noalloc: n_lasers * spp = %lld exceeds the static scratch limit of %d",
+                 (long long)sc->n_lasers * spp, MT_NOALLOC_MAX_SAMPLES);
+    unsigned char *base = nullptr;
+    MT_TRY(noalloc_scratch(&base));
+    int *tile_counter = reinterpret_cast<int *>(base);
+    float *d_area = reinterpret_cast<float *>(base + 16);
+    uint32_t *cdf = reinterpret_cast<uint32_t *>(base + NA_HDR);
+    float4 *ys = reinterpret_cast<float4 *>(base + NA_HDR + NA_CDF);
+    int32_t *yt = reinterpret_cast<int32_t *>(base + NA_HDR + NA_CDF + NA_YS);
+    // hidden-surface table rebuilt into the static array on every call
+    k_setup_hidden<<<1, 1, 0, st>>>(reinterpret_cast<const float *>(s->dev.tris), s->dev.leaf_of,
+                                    (int)sc->hidden_first, (int)sc->hidden_count, cdf, d_area);
+    MT_CUDA_TRY(cudaGetLastError());
+    float h_area = 0.f;
+    MT_CUDA_TRY(cudaMemcpyAsync(&h_area, d_area, sizeof(float), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    int D;
+    LaunchCfg cfg = render_cfg(s, MT_LAUNCH_NLOS, (int)rows, f->T, 1, 0, D);
+    MT_CHECK_ARG(D >= 1, "film row too long");
+    NlosParams p{};
+    p.T = f->T;
+    p.D = D;
+    p.start = f->start;
+    p.width = f->width;
+    const bool acc = f->flags & MT_ACCUMULATE;
+    p.scale = acc ? 1.0f : 1.0f / (float)spp;
+    p.flags = f->flags;
+    p.spp = spp;
+    p.mode = (int32_t)sc->mode;
+    p.sample_offset = (uint32_t)sample_offset;
+    seed_key(seed, p.k0, p.k1);
+    p.lasers = sc->lasers;
+    p.sensors = sc->sensors;
+    p.n_l = sc->n_lasers;
+    p.n_s = sc->mode == MT_EXHAUSTIVE ? sc->n_sensors : 0;
+    p.nw = make_float3(sc->wall_normal[0], sc->wall_normal[1], sc->wall_normal[2]);
+    p.fw = sc->wall_albedo / MT_PI;
+    p.hidden_first = (int32_t)sc->hidden_first;
+    p.hidden_n = (int32_t)sc->hidden_count;
+    p.hcdf = cdf;
+    p.hidden_area = h_area;
+    p.tile = cfg.tile;
+    if (sc->mode == MT_EXHAUSTIVE) p.n_tiles = sc->n_lasers * ((sc->n_sensors + cfg.tile - 1) / cfg.tile);
+    else p.n_tiles = (int)((rows + cfg.tile - 1) / cfg.tile);
+    p.film = f->film;
+    p.steady = f->steady;
+    p.ysamp = ys;
+    p.ysamp_tri = yt;
+    p.tile_counter = tile_counter;
+    if (p.D < p.T && !acc) MT_CUDA_TRY(cudaMemsetAsync(p.film, 0, (size_t)rows * f->T * sizeof(float), st));
+    MT_CUDA_TRY(cudaMemsetAsync(tile_counter, 0, sizeof(int), st));
+    return mt_launch_nlos(s->dev, p, cfg, false, (f->flags & MT_COUNTERS) != 0, st);
+}
