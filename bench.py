@@ -185,11 +185,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile", default="", help="small: a few launches of each kernel on reduced sizes (for ncu)")
+    ap.add_argument("--compare", action="store_true",
+                    help="batched NLOS vs per-scan-point launches; adjoint vs finite differences")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return profile_case(args.profile)
+    if args.compare:
+        return compare()
 
     import numpy as np
     import torch
@@ -325,19 +329,22 @@ def main():
 
 def profile_case(which):
     """Reduced-size launches of the hot kernels for ncu captures: the large
-    scene (full geometry) at 128x128 px, 32 spp; the differentiable scene's
-    backward at 64x64; a 16x16 confocal NLOS grid."""
+    scene (full geometry) at 128x128 px, 256 spp with the launch configuration of
+    the benchmark; the differentiable scene's backward at 64x64; a 16x16
+    confocal NLOS grid."""
     import torch
     from paper_2510_25660_gb300 import api, scenes
     from paper_2510_25660_gb300 import build as b
     b.build()
     api.load()
+    from paper_2510_25660_gb300 import autotune
     sc = scenes.large_scene()
     f = scenes.LARGE_FILM
     s = api.Scene(sc)
+    autotune.apply(s, "render", sc, f, 256, 8)
     film, steady = api.new_film(128, 128, f.T)
     for _ in range(3):
-        api.render(s, 128, 128, f.T, f.start_opl, f.bin_width, 32, 1, 8, out=(film, steady))
+        api.render(s, 128, 128, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))
     s.sync()
     del s
     sc = scenes.diff_scene()
@@ -355,6 +362,120 @@ def profile_case(which):
         api.render_nlos(s, lasers, None, api.MT_CONFOCAL, scenes.NLOS_T, 0.0, scenes.NLOS_W, 1024, 1)
     s.sync()
     print("profile case done")
+
+
+def compare():
+    """(1) All 4096 confocal scan points in one graph launch against one launch
+    per scan point, at equal spp (equal film error: same estimator, same spp).
+    (2) Path-replay gradients of 32 albedo parameters against central finite
+    differences of forward renders (two launches per parameter), with the error
+    of each against the exact oracle-checked gradient on the same samples."""
+    import numpy as np
+    import torch
+    from paper_2510_25660_gb300 import api, autotune, scenes
+    from paper_2510_25660_gb300 import build as b
+    b.build()
+    api.load()
+    out = {}
+    sc = scenes.nlos_scene()
+    s = api.Scene(sc)
+    autotune.apply(s, "nlos", sc, None, 1024, 0)
+    pts = torch.from_numpy(scenes.wall_grid(64, 64)).cuda()
+    T, W0, spp = scenes.NLOS_T, scenes.NLOS_W, 1024
+    film = torch.empty((4096, T), device="cuda")
+    steady = torch.empty(4096, device="cuda")
+    for _ in range(2):
+        api.render_nlos(s, pts, None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=(film, steady))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.render_nlos(s, pts, None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=(film, steady))
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    # one plain launch per scan point through the same API (row views of the same film)
+    cfg = autotune.apply(s, "nlos", sc, None, 1024, 0) or {}
+    s.set_launch(api.MT_LAUNCH_NLOS, cfg.get("threads", 0), cfg.get("tile", 0), 0, cfg.get("priv", -1),
+                 cfg.get("options", 0) | api.MT_OPT_NO_GRAPH)
+    rows = [(film[i:i + 1], steady[i:i + 1]) for i in range(4096)]
+    pt_rows = [pts[i:i + 1].contiguous() for i in range(4096)]
+    for i in range(64):
+        api.render_nlos(s, pt_rows[i], None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=rows[i])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record()
+    for i in range(4096):
+        api.render_nlos(s, pt_rows[i], None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=rows[i])
+    e1.record()
+    torch.cuda.synchronize()
+    loop_wall_ms = 1000 * (time.perf_counter() - t0)
+    out["nlos_batched_vs_per_point"] = {
+        "workload": "64x64 confocal scan, 1024 spp, T=4096, 49.4k hidden triangles; per point: one direct "
+                    "launch per scan point, same kernel and launch configuration",
+        "batched_ms": batched_ms, "per_point_loop_gpu_ms": e0.elapsed_time(e1), "per_point_loop_wall_ms": loop_wall_ms,
+        "speedup": e0.elapsed_time(e1) / batched_ms}
+    del s
+    # adjoint vs finite differences on the differentiable scene, 32 parameters
+    sc = scenes.diff_scene()
+    f = scenes.DIFF_FILM
+    s = api.Scene(sc)
+    spp, depth = 64, 8
+    alb0 = torch.from_numpy(sc.albedo).cuda()
+    s.set_params(albedo=torch.from_numpy(scenes.perturbed_albedo(sc)).cuda())
+    target, _ = api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, spp, 7, depth)
+    target = target.clone()
+    s.set_params(albedo=alb0)
+    film, steady = api.new_film(f.H, f.W, f.T)
+
+    def loss():
+        api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, spp, 1, depth, out=(film, steady))
+        return float(((film.double() - target.double()) ** 2).sum())
+
+    L0 = loss()
+    g = (2 * (film - target)).contiguous()
+    outg = (torch.zeros((sc.n_tris, 3), device="cuda"), torch.zeros((len(sc.emitters), 3), device="cuda"),
+            torch.zeros(1, device="cuda"))
+    api.render_backward(s, f.T, f.start_opl, f.bin_width, spp, 1, depth, g, out=outg)
+    torch.cuda.synchronize()
+    outg[0].zero_()
+    e0.record()
+    api.render_backward(s, f.T, f.start_opl, f.bin_width, spp, 1, depth, g, out=outg)
+    e1.record()
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1)
+    ga = outg[0].cpu().numpy()
+    rng = np.random.default_rng(3)
+    # parameters the loss depends on noticeably
+    cand = np.argsort(-np.abs(ga).reshape(-1))[:2000]
+    pick = rng.choice(cand, 32, replace=False)
+    h = 1e-3
+    fd = []
+    t0 = time.perf_counter()
+    e0.record()
+    for k in pick:
+        t, c = divmod(int(k), 3)
+        vals = []
+        for sgn in (1, -1):
+            a = alb0.clone()
+            a[t, c] += sgn * h
+            s.set_params(albedo=a)
+            vals.append(loss())
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    e1.record()
+    torch.cuda.synchronize()
+    s.set_params(albedo=alb0)
+    fd_ms = e0.elapsed_time(e1)
+    adj = ga.reshape(-1)[pick]
+    fd = np.array(fd)
+    rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-30)
+    out["adjoint_vs_finite_differences"] = {
+        "workload": "97k-triangle scene, 256x256x512 film, 64 spp, depth 8, L2 loss vs a target with albedos x U[0.8,1.2]",
+        "adjoint_ms_all_params": adj_ms, "n_params_adjoint": int(sc.n_tris * 3),
+        "fd_ms_32_params": fd_ms, "fd_launches": 64, "loss": L0,
+        "adjoint_vs_fd_rel_err_median": float(np.median(rel)), "adjoint_vs_fd_rel_err_max": float(rel.max()),
+        "speedup_per_param": (fd_ms / 32) / (adj_ms / (sc.n_tris * 3)),
+        "speedup_for_32_params": fd_ms / adj_ms}
+    print(json.dumps(out), flush=True)
 
 
 def secondary(api, autotune, scenes):

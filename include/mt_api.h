@@ -196,10 +196,25 @@ mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *s
  * on the device, out[6] BVH build time in microseconds. */
 mt_status mt_scene_stats(mt_scene scene, int64_t *out);
 
-/* Launch configuration used by the next renders of this scene: threads per
- * CTA, pixels (or scan pairs) per tile, CTAs per SM (0 = occupancy maximum).
- * Set by the autotuner; 0 keeps a field at its default. */
-mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm);
+/* Launch configuration used by the next launches of this scene (set by the
+ * autotuner; 0 keeps a field at its default):
+ *   threads      threads per CTA (32..256, multiple of 32)
+ *   tile         RENDER/BACKWARD: pixels of one image row owned by one warp at
+ *                a time; NLOS: scan rows owned by one CTA at a time
+ *   ctas_per_sm  cap on resident CTAs per SM (0 = occupancy maximum)
+ *   priv_bins    time bins per pixel (scan row) accumulated in shared memory
+ *                before one write to HBM; later bins are added to the film in
+ *                global memory directly.  -1 = as many as fit (default),
+ *                0 = none.
+ *   options      MT_OPT_* bits (below). */
+mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm,
+                        int32_t priv_bins, uint32_t options);
+/* options: MT_OPT_AGGREGATE = lanes of a warp that add to the same film bin
+ * combine their values with warp shuffles first and issue one atomic.
+ * MT_OPT_NO_GRAPH (NLOS) = enqueue the kernels directly instead of replaying
+ * the cached CUDA graph. */
+#define MT_OPT_AGGREGATE 1u
+#define MT_OPT_NO_GRAPH 2u
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1
 #define MT_LAUNCH_NLOS 2

@@ -27,6 +27,7 @@ MT_EMITTER_AREA, MT_EMITTER_POINT = 0, 1
 MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
 MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
 MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
+MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH = 1, 2
 STATUS_NAMES = ["MT_OK", "MT_ERR_INVALID_ARGUMENT", "MT_ERR_OUT_OF_MEMORY", "MT_ERR_CUDA", "MT_ERR_TIMEOUT",
                 "MT_ERR_UNSUPPORTED", "MT_ERR_INTERNAL"]
 
@@ -76,7 +77,7 @@ SIGNATURES = {
     "mt_sync": (C.c_int, [_P, _P]),
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
-    "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _U32]),
     "mt_scene_destroy": (None, [_P]),
     "mt_film_destroy": (None, [_P]),
     "mt_probe_philox": (C.c_int, [_U64, _P, _I64, _P, _P]),
@@ -173,8 +174,8 @@ def mt_scene_stats(scene, out):
     return _call("mt_scene_stats", scene, out)
 
 
-def mt_set_launch(scene, kind, threads, tile, ctas_per_sm):
-    return _call("mt_set_launch", scene, kind, threads, tile, ctas_per_sm)
+def mt_set_launch(scene, kind, threads, tile, ctas_per_sm, priv_bins, options):
+    return _call("mt_set_launch", scene, kind, threads, tile, ctas_per_sm, priv_bins, options)
 
 
 def mt_scene_destroy(scene):
@@ -275,8 +276,8 @@ class Scene:
     def sync(self, stream=None):
         mt_sync(self.h, _stream(stream))
 
-    def set_launch(self, kind, threads=0, tile=0, ctas_per_sm=0):
-        mt_set_launch(self.h, kind, threads, tile, ctas_per_sm)
+    def set_launch(self, kind, threads=0, tile=0, ctas_per_sm=0, priv_bins=-1, options=0):
+        mt_set_launch(self.h, kind, threads, tile, ctas_per_sm, priv_bins, options)
 
 
 class Film:

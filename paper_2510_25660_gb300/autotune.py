@@ -15,6 +15,9 @@ import time
 KINDS = {"render": 0, "backward": 1, "nlos": 2}
 
 
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "launch_table.json")
+
+
 def cache_path() -> str:
     return os.environ.get("MT_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "mtr_autotune.json"))
 
@@ -45,29 +48,37 @@ def _store(d: dict) -> None:
 
 
 def apply(scene, kind, sc, film, spp, depth) -> dict | None:
-    """Apply a cached configuration, if any; returns it."""
-    cfg = _load().get(_key(kind, sc, film, spp, depth))
+    """Apply a cached configuration (user cache first, then the table shipped
+    with the package), if any; returns it."""
+    key = _key(kind, sc, film, spp, depth)
+    cfg = _load().get(key)
+    if cfg is None and os.path.exists(TABLE):
+        cfg = json.load(open(TABLE)).get(key)
     if cfg:
-        scene.set_launch(KINDS[kind], cfg["threads"], cfg["tile"], cfg["ctas_per_sm"])
+        scene.set_launch(KINDS[kind], cfg["threads"], cfg["tile"], cfg["ctas_per_sm"], cfg.get("priv", -1),
+                         cfg.get("options", 0))
     return cfg
 
 
 def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60.0) -> dict:
     """Time `run()` (one launch of the kernel) under each candidate
-    (threads, tile, ctas_per_sm); keep and cache the fastest."""
+    (threads, tile, ctas_per_sm, priv_bins); keep and cache the fastest."""
     import torch
     best = None
     t_end = time.time() + budget_s
     results = []
-    for threads, tile, cps in candidates:
+    for cand in candidates:
+        threads, tile, cps, priv = cand[:4]
+        opts = cand[4] if len(cand) > 4 else 0
         if time.time() > t_end:
             break
-        scene.set_launch(KINDS[kind], threads, tile, cps)
+        scene.set_launch(KINDS[kind], threads, tile, cps, priv, opts)
         try:
             run()
             torch.cuda.synchronize()
         except Exception as e:  # a configuration that does not fit is skipped
-            results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "error": str(e)[:80]})
+            results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts,
+                            "error": str(e)[:80]})
             continue
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -76,13 +87,80 @@ def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "ms": ms})
+        results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts, "ms": ms})
         if best is None or ms < best["ms"]:
-            best = {"threads": threads, "tile": tile, "ctas_per_sm": cps, "ms": ms}
+            best = {"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts, "ms": ms}
     if best is None:
         raise RuntimeError("no launch configuration ran")
-    scene.set_launch(KINDS[kind], best["threads"], best["tile"], best["ctas_per_sm"])
+    scene.set_launch(KINDS[kind], best["threads"], best["tile"], best["ctas_per_sm"], best["priv"], best["options"])
     d = _load()
     d[_key(kind, sc, film, spp, depth)] = dict(best, results=results)
     _store(d)
     return best
+
+
+def _candidates(kind, film_T):
+    out = []
+    if kind == "nlos":
+        for threads in (128, 256):
+            for tile in (1, 2, 4):
+                for priv in (-1, 0):
+                    for opt in (0, 1):
+                        out.append((threads, tile, 0, priv, opt))
+        return out
+    for threads in (128, 256):
+        for tile in (1, 2):
+            for priv in (-1, 0, film_T // 4, film_T // 2):
+                for opt in (0, 1):
+                    out.append((threads, tile, 0, priv, opt))
+    return out
+
+
+def main():
+    """Tune the benchmark workloads on this GPU and print the table entries."""
+    import sys
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2510_25660_gb300 import api, scenes
+    from paper_2510_25660_gb300 import build as b
+    b.build()
+    api.load()
+    found = {}
+    which = sys.argv[1:] or ["render", "backward", "nlos"]
+    if "render" in which:
+        sc = scenes.large_scene()
+        f = scenes.LARGE_FILM
+        s = api.Scene(sc)
+        film, steady = api.new_film(f.H, f.W, f.T)
+        run = lambda: api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))
+        best = tune(s, "render", sc, f, 256, 8, run, _candidates("render", f.T), reps=2, budget_s=120)
+        found[_key("render", sc, f, 256, 8)] = best
+        del s, film, steady
+    if "backward" in which:
+        sc = scenes.diff_scene()
+        f = scenes.DIFF_FILM
+        s = api.Scene(sc)
+        film, steady = api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8)
+        g = torch.randn_like(film)
+        out = (torch.zeros((sc.n_tris, 3), device="cuda"), torch.zeros((len(sc.emitters), 3), device="cuda"),
+               torch.zeros(1, device="cuda"))
+        run = lambda: api.render_backward(s, f.T, f.start_opl, f.bin_width, 64, 1, 8, g, out=out)
+        best = tune(s, "backward", sc, f, 64, 8, run, _candidates("backward", f.T), reps=2, budget_s=60)
+        found[_key("backward", sc, f, 64, 8)] = best
+        del s
+    if "nlos" in which:
+        sc = scenes.nlos_scene()
+        s = api.Scene(sc)
+        lasers = torch.from_numpy(scenes.wall_grid(64, 64)).cuda()
+        nf = [None]
+
+        def run():
+            nf[0] = api.render_nlos(s, lasers, None, api.MT_CONFOCAL, scenes.NLOS_T, scenes.NLOS_START,
+                                    scenes.NLOS_W, 1024, 1, out=nf[0])
+        best = tune(s, "nlos", sc, None, 1024, 0, run, _candidates("nlos", scenes.NLOS_T), reps=3, budget_s=60)
+        found[_key("nlos", sc, None, 1024, 0)] = best
+    print(json.dumps(found, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -426,7 +426,7 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
     D.tan_half = hcam.tan_half;
     D.err = sc->err;
     D.counters = sc->counters;
-    for (int k = 0; k < 3; ++k) sc->cfg[k] = LaunchCfg{256, 0, 0, sc->num_sms, 0};
+    for (int k = 0; k < 3; ++k) sc->cfg[k] = LaunchCfg{256, 0, 0, sc->num_sms, 0, -1, 0};
     return MT_OK;
 }
 
@@ -550,9 +550,38 @@ static LaunchCfg render_cfg(const mt_scene_s *s, int kind, int32_t W, int32_t T,
     size_t fixed = ((size_t)tile * (C == 3 ? 3 : 1) + extra_floats) * 4 + 64;
     size_t avail = budget > fixed ? budget - fixed : 0;
     D = (int)std::min<size_t>((size_t)T, avail / ((size_t)tile * C * 4));
+    if (c.priv >= 0) D = std::min(D, c.priv);
     if (D < 1) D = 0;
     c.tile = tile;
     c.smem_bytes = (((size_t)tile * D * C + (size_t)tile * (C == 3 ? 3 : 1) + extra_floats) * 4 + 15) & ~(size_t)15;
+    return c;
+}
+
+// warp-owned tiles of k_render: `tile` pixels per warp (default: enough pixels
+// for 64 paths), D = bins per pixel privatised in the warp's shared-memory
+// slice (priv < 0: as many as fit in ~100 KB per CTA; bins >= D go to global
+// memory with red.add)
+static LaunchCfg warp_tile_cfg(const mt_scene_s *s, int kind, int32_t W, int32_t T, int32_t spp, int extra_floats,
+                               int &D) {
+    LaunchCfg c = s->cfg[kind];
+    const int warps = c.threads / 32;
+    int tile = c.tile > 0 ? c.tile : std::max(1, (64 + spp - 1) / spp);
+    tile = std::max(1, std::min(tile, W));
+    const size_t cap = (size_t)std::min(s->smem_optin, 220 * 1024) - 1024;
+    const size_t budget = std::min(cap, (size_t)100 * 1024);
+    const size_t fixed = (size_t)extra_floats * 4 + 64;
+    const size_t per_warp = budget > fixed ? (budget - fixed) / warps : 0;
+    long long fit = ((long long)(per_warp / 4) - 3LL * tile) / (3LL * tile);
+    if (fit < 0) fit = 0;
+    long long d = c.priv < 0 ? std::min<long long>(T, fit) : std::min<long long>(std::min<long long>(c.priv, T), fit);
+    if (c.priv > 0 && d < c.priv) {  // an explicit depth may use the whole opt-in budget
+        const size_t per_warp_cap = cap > fixed ? (cap - fixed) / warps : 0;
+        const long long fit_cap = ((long long)(per_warp_cap / 4) - 3LL * tile) / (3LL * tile);
+        d = std::max<long long>(0, std::min<long long>(std::min<long long>(c.priv, T), fit_cap));
+    }
+    D = (int)d;
+    c.tile = tile;
+    c.smem_bytes = (((size_t)warps * tile * (3 * (size_t)D + 3) + extra_floats) * 4 + 15) & ~(size_t)15;
     return c;
 }
 
@@ -588,7 +617,7 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     const int kind = mode == 2 ? MT_LAUNCH_BACKWARD : MT_LAUNCH_RENDER;
     const int n_em_smem = (mode == 2 && s->n_em <= 64) ? s->n_em : 0;
     int D;
-    LaunchCfg cfg = render_cfg(s, kind, f->W, f->T, 3, n_em_smem * 3, D);
+    LaunchCfg cfg = warp_tile_cfg(s, kind, f->W, f->T, spp, n_em_smem * 3, D);
     RenderParams p{};
     p.H = f->H;
     p.W = f->W;
@@ -618,6 +647,7 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     p.dump_count = (unsigned long long *)dcount;
     p.tile_counter = s->tile_counter;
     p.n_em_smem = n_em_smem;
+    p.aggregate = (cfg.options & MT_OPT_AGGREGATE) ? 1 : 0;
     if (mode != 2 && D < f->T && !acc) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
@@ -684,7 +714,6 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
     }
     int D;
     cfg = render_cfg(s, MT_LAUNCH_NLOS, (int)rows, f->T, 1, 0, D);
-    MT_CHECK_ARG(D >= 1, "film row too long");
     p = NlosParams{};
     p.T = f->T;
     p.D = D;
@@ -715,6 +744,7 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
     p.ysamp = s->ysamp;
     p.ysamp_tri = s->ysamp_tri;
     p.tile_counter = s->tile_counter + 1;
+    p.aggregate = (cfg.options & MT_OPT_AGGREGATE) ? 1 : 0;
     return MT_OK;
 }
 
@@ -735,7 +765,7 @@ mt_status mt_render_nlos(mt_scene s, mt_film f, const mt_scan *scan, int32_t spp
     MT_TRY(nlos_prepare(s, f, scan, spp, seed, sample_offset, p, cfg, st));
     cudaStreamCaptureStatus cs;
     MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || (f->flags & MT_COUNTERS))
+    if (cs != cudaStreamCaptureStatusNone || (f->flags & MT_COUNTERS) || (cfg.options & MT_OPT_NO_GRAPH))
         return nlos_enqueue(s, f, p, cfg, false, st);
     // replay a cached graph of [zero counters, (sample pass,) connection pass];
     // re-capture when any launch parameter changed
@@ -810,15 +840,20 @@ mt_status mt_scene_stats(mt_scene s, int64_t *out) {
     return MT_OK;
 }
 
-mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm) {
+mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile, int32_t ctas_per_sm,
+                        int32_t priv_bins, uint32_t options) {
     MT_CHECK_ARG(s != nullptr, "scene is NULL");
     MT_CHECK_ARG(kind >= 0 && kind <= 2, "unknown launch kind");
     MT_CHECK_ARG(threads == 0 || (threads >= 32 && threads <= 256 && threads % 32 == 0), "threads must be 32..256, x32");
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
+    MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
+    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH)) == 0, "unknown launch options 0x%x", options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;
     c.tile = tile;
     c.ctas_per_sm = ctas_per_sm;
+    c.priv = priv_bins;
+    c.options = (int)options;
     return MT_OK;
 }
 

@@ -231,3 +231,33 @@ struct DevScene {
 };
 
 __device__ __forceinline__ void raise_err(const DevScene &s, uint32_t bit) { atomicOr(s.err, bit); }
+
+// Add v to addr[0..n) (shared or global memory).  With aggregate set, the
+// lanes of the warp that target the same address first sum their values with
+// shuffles and only the group's first lane issues the atomics.
+template <int N>
+__device__ __forceinline__ void splat_add(float *addr, const float *v, bool aggregate) {
+    if (aggregate) {
+        const unsigned active = __activemask();
+        const unsigned peers = __match_any_sync(active, (unsigned long long)addr);
+        if (peers != (1u << (threadIdx.x & 31))) {
+            float sum[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) sum[k] = 0.f;
+            unsigned m = peers;
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+#pragma unroll
+                for (int k = 0; k < N; ++k) sum[k] += __shfl_sync(peers, v[k], src);
+            }
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) atomicAdd(addr + k, sum[k]);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) atomicAdd(addr + k, v[k]);
+}

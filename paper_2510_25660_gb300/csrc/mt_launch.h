@@ -15,7 +15,7 @@ struct RenderParams {
     int32_t spp, max_depth;
     uint32_t sample_offset;
     uint32_t k0, k1;           // Philox key = seed
-    int32_t tile_px, n_tiles, tiles_per_row;
+    int32_t tile_px, n_tiles, tiles_per_row;  // tile = tile_px pixels of one row, owned by one warp
     float *film, *steady;
     const float *gfilm, *gsteady;
     float *galb, *grad, *gmed;
@@ -24,6 +24,7 @@ struct RenderParams {
     unsigned long long *dump_count;
     int *tile_counter;
     int32_t n_em_smem;         // emitters whose radiance gradients are summed in shared memory
+    int32_t aggregate;         // warp-aggregated splats
 };
 
 struct NlosParams {
@@ -47,11 +48,14 @@ struct NlosParams {
     long long dump_cap;
     unsigned long long *dump_count;
     int *tile_counter;
+    int32_t aggregate;         // warp-aggregated splats
 };
 
 struct LaunchCfg {
     int threads, tile, ctas_per_sm, num_sms;
     size_t smem_bytes;
+    int priv;  // bins per pixel (scan row) kept in shared memory: -1 = as many as fit, 0 = none
+    int options;  // MT_OPT_* bits
 };
 
 mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, int mode, bool counters,

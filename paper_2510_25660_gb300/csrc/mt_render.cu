@@ -27,6 +27,13 @@ namespace {
 
 constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2;
 
+// CTAs of 256 threads the register allocation must leave room for per SM: 4
+// (64 registers) measured fastest on GB300 for the large scene (205 ms against
+// 227 ms at 2), the extra warps hiding more gather latency than the spills cost
+#ifndef MT_RENDER_MINB
+#define MT_RENDER_MINB 4
+#endif
+
 struct VRec {
     int32_t tri;   // original triangle index, -1 for a medium vertex
     float3 r;      // d(factor)/factor of the continuation
@@ -148,17 +155,12 @@ struct Tracer {
         cnt.contribs++;
         if (MODE != MODE_BWD) {
             if (in) {
+                const float cv[3] = {c.x, c.y, c.z};
                 if (bin < p.D) {
-                    float *h = hist + ((size_t)ps.lp * p.D + bin) * 3;
-                    atomicAdd(h, c.x);
-                    atomicAdd(h + 1, c.y);
-                    atomicAdd(h + 2, c.z);
+                    splat_add<3>(hist + ((size_t)ps.lp * p.D + bin) * 3, cv, p.aggregate);
                     cnt.smem_splats++;
                 } else {
-                    float *h = p.film + ((size_t)ps.pix * p.T + bin) * 3;
-                    atomicAdd(h, c.x);
-                    atomicAdd(h + 1, c.y);
-                    atomicAdd(h + 2, c.z);
+                    splat_add<3>(p.film + ((size_t)ps.pix * p.T + bin) * 3, cv, p.aggregate);
                     cnt.gmem_splats++;
                 }
             }
@@ -431,30 +433,29 @@ struct Tracer {
 };
 
 template <int MODE, bool MEDIA, bool CNT>
-__global__ void __launch_bounds__(256) k_render(const DevScene s, const RenderParams p) {
+__global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s, const RenderParams p) {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
-    float *hist = smem;
-    float *steady_s = hist + (size_t)p.tile_px * p.D * 3;
-    float *em_acc = steady_s + p.tile_px * 3;
-    __shared__ int s_tile, s_next;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // each warp owns a slice: its tile's histograms (tile_px x D x 3) and steady sums (tile_px x 3)
+    const int slice = p.tile_px * (p.D * 3 + 3);
+    float *hist = smem + (size_t)warp * slice;
+    float *steady_s = hist + p.tile_px * p.D * 3;
+    float *em_acc = smem + (size_t)nwarps * slice;  // shared by the CTA (backward)
     __shared__ float s_med;
-    const int lane = threadIdx.x & 31;
     Counters cnt;
     VRec vrec[MODE == MODE_BWD ? MT_MAX_BWD_DEPTH + 1 : 1];
     if (MODE == MODE_BWD) {
         for (int i = threadIdx.x; i < p.n_em_smem * 3; i += blockDim.x) em_acc[i] = 0.f;
         if (threadIdx.x == 0) s_med = 0.f;
+        __syncthreads();
     }
     Tracer<MODE, MEDIA, CNT> tr{s, p, hist, steady_s, em_acc, s_med, cnt, vrec, Rng{p.k0, p.k1}};
-    const int hist_n = p.tile_px * p.D * 3;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = atomicAdd(p.tile_counter, 1);
-            s_next = 0;
-        }
-        __syncthreads();
-        const int tile = s_tile;
+        // the warp claims its next tile
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= p.n_tiles) break;
         const int ty = tile / p.tiles_per_row, tx = tile - ty * p.tiles_per_row;
         const int x0 = tx * p.tile_px;
@@ -462,36 +463,32 @@ __global__ void __launch_bounds__(256) k_render(const DevScene s, const RenderPa
         const int pix0 = ty * p.W + x0;
         // stage the tile: zero the histograms, or load dL/dfilm for replay
         if (MODE != MODE_BWD) {
-            for (int i = threadIdx.x; i < hist_n + p.tile_px * 3; i += blockDim.x) smem[i] = 0.f;
+            for (int i = lane; i < slice; i += 32) hist[i] = 0.f;
         } else {
-            for (int i = threadIdx.x; i < npx * p.D * 3; i += blockDim.x) {
+            for (int i = lane; i < npx * p.D * 3; i += 32) {
                 const int lp = i / (p.D * 3), r = i - lp * p.D * 3;
                 hist[i] = __ldg(&p.gfilm[((size_t)(pix0 + lp) * p.T) * 3 + r]);
             }
-            for (int i = threadIdx.x; i < p.tile_px * 3; i += blockDim.x)
+            for (int i = lane; i < p.tile_px * 3; i += 32)
                 steady_s[i] = (p.gsteady && i < npx * 3) ? __ldg(&p.gsteady[(size_t)pix0 * 3 + i]) : 0.f;
         }
-        __syncthreads();
+        __syncwarp();
+        // paths of the tile; a lane whose path ended takes the next one
         const int n_paths = npx * p.spp;
+        int next = 0;
         PathState ps;
-        bool active = false, exhausted = false;
+        bool active = false;
         for (;;) {
-            if (!exhausted) {
+            if (next < n_paths) {
                 const unsigned need = __ballot_sync(0xffffffffu, !active);
-                if (need) {
-                    const int leader = __ffs(need) - 1;
-                    int base = 0;
-                    if (lane == leader) base = atomicAdd(&s_next, __popc(need));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (base + __popc(need) >= n_paths) exhausted = true;
-                    if (!active) {
-                        const int j = base + __popc(need & ((1u << lane) - 1u));
-                        if (j < n_paths) {
-                            tr.begin(ps, j, pix0, x0, ty);
-                            active = true;
-                        }
+                if (!active) {
+                    const int j = next + __popc(need & ((1u << lane) - 1u));
+                    if (j < n_paths) {
+                        tr.begin(ps, j, pix0, x0, ty);
+                        active = true;
                     }
                 }
+                next += __popc(need);
             }
             if (!__any_sync(0xffffffffu, active)) break;
             if (active) {
@@ -501,17 +498,17 @@ __global__ void __launch_bounds__(256) k_render(const DevScene s, const RenderPa
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
         if (MODE != MODE_BWD) {
             // write the tile: bins < D of every pixel, then the steady image
             const bool acc = p.flags & MT_ACCUMULATE;
             if (p.D == p.T) {
                 const size_t n = (size_t)npx * p.T * 3;
                 float *dst = p.film + (size_t)pix0 * p.T * 3;
-                if (((n | (size_t)pix0 * p.T * 3) & 3) == 0 && (((uintptr_t)p.film) & 15) == 0) {
+                if (((n | (size_t)pix0 * p.T * 3 | (size_t)slice) & 3) == 0 && (((uintptr_t)p.film) & 15) == 0) {
                     float4 *d4 = reinterpret_cast<float4 *>(dst);
                     const float4 *s4 = reinterpret_cast<const float4 *>(hist);
-                    for (size_t i = threadIdx.x; i < n / 4; i += blockDim.x) {
+                    for (size_t i = lane; i < n / 4; i += 32) {
                         float4 v = s4[i];
                         if (acc) {
                             const float4 o = d4[i];
@@ -520,23 +517,23 @@ __global__ void __launch_bounds__(256) k_render(const DevScene s, const RenderPa
                         d4[i] = v;
                     }
                 } else {
-                    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = acc ? dst[i] + hist[i] : hist[i];
+                    for (size_t i = lane; i < n; i += 32) dst[i] = acc ? dst[i] + hist[i] : hist[i];
                 }
-            } else {
+            } else if (p.D > 0) {
                 const int row = p.D * 3;
-                for (int i = threadIdx.x; i < npx * row; i += blockDim.x) {
+                for (int i = lane; i < npx * row; i += 32) {
                     const int lp = i / row, r = i - lp * row;
                     float *d = p.film + (size_t)(pix0 + lp) * p.T * 3 + r;
                     *d = acc ? *d + hist[i] : hist[i];
                 }
             }
             if (p.steady)
-                for (int i = threadIdx.x; i < npx * 3; i += blockDim.x) {
+                for (int i = lane; i < npx * 3; i += 32) {
                     float *d = p.steady + (size_t)pix0 * 3 + i;
                     *d = acc ? *d + steady_s[i] : steady_s[i];
                 }
         }
-        __syncthreads();
+        __syncwarp();
     }
     if (MODE == MODE_BWD) {
         __syncthreads();
@@ -567,7 +564,8 @@ mt_status launch_one(const DevScene &s, const RenderParams &p, const LaunchCfg &
         return MT_ERR_UNSUPPORTED;
     }
     if (cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cfg.ctas_per_sm);
-    const int grid = std::max(1, std::min(p.n_tiles, per_sm * cfg.num_sms));
+    const int warps = cfg.threads / 32;
+    const int grid = std::max(1, std::min((p.n_tiles + warps - 1) / warps, per_sm * cfg.num_sms));
     kern<<<grid, cfg.threads, smem, st>>>(s, p);
     MT_CUDA_TRY(cudaGetLastError());
     return MT_OK;

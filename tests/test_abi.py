@@ -97,7 +97,7 @@ def test_invalid_arguments_without_gpu(lib):
     assert L.mt_render_backward(None, None, None, None, 1, 0, 1, 0, None, None, None, None) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_render_nlos(None, None, None, 1, 0, 0, None) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_sync(None, None) == api.MT_ERR_INVALID_ARGUMENT
-    assert L.mt_set_launch(None, 0, 0, 0, 0) == api.MT_ERR_INVALID_ARGUMENT
+    assert L.mt_set_launch(None, 0, 0, 0, 0, -1, 0) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_probe_bins(None, 4, 0.0, 1.0, 4, None, None) == api.MT_ERR_INVALID_ARGUMENT
 
 
