@@ -270,6 +270,17 @@ def main():
     achieved = alg_bytes / (mean_ms / 1000.0) / 1e9
     khash = _kernel_hash()
     traffic, _ = _traffic_from_profile(khash)
+    # measured rates of the render kernel's own access patterns on this GPU
+    aux = {}
+    try:
+        l2 = api.microbench(api.MT_MICRO_GATHER32, 64 << 20, 256)
+        aux = {"l2_gather32_gbs": l2, "frac_of_l2_gather": achieved / l2,
+               "red_global_gops": api.microbench(api.MT_MICRO_RED_GLOBAL, 1 << 30, 64),
+               "red_shared_gops": api.microbench(api.MT_MICRO_RED_SHARED, 1 << 20, 1024),
+               "note": "random 32-B loads from a 64 MB (L2-resident) buffer; red.add.f32 into 1 GB; "
+                       "shared-memory atomics into 48 KB per CTA"}
+    except Exception as e:  # reported, not fatal
+        aux = {"error": str(e)[:200]}
 
     # e2e: host arrays in, film out, through the public API (scene load + render + read-back)
     e2e = None
@@ -312,7 +323,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "per_vertex": "node visits x 32 B + triangle tests x 48 B + 32 B material/emitter per vertex "
                                    "+ film and steady image written once",
-                     "counts": cnt, "kernel_hash": khash},
+                     "counts": cnt, "kernel_hash": khash, "aux": aux},
         "clocks": clk,
         "gpu_launches": args.steps,
         "e2e": e2e,

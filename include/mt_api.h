@@ -212,9 +212,12 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
 /* options: MT_OPT_AGGREGATE = lanes of a warp that add to the same film bin
  * combine their values with warp shuffles first and issue one atomic.
  * MT_OPT_NO_GRAPH (NLOS) = enqueue the kernels directly instead of replaying
- * the cached CUDA graph. */
+ * the cached CUDA graph.  MT_OPT_REFILL(k) (RENDER/BACKWARD, k = 1..32) = a
+ * warp starts new paths only once at least k of its lanes are idle (default 1:
+ * every idle lane is refilled at once). */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
+#define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1
 #define MT_LAUNCH_NLOS 2
@@ -254,6 +257,21 @@ typedef struct {
 mt_status mt_render_dump(mt_scene scene, mt_film film, const mt_scan *scan, int32_t spp, uint64_t seed,
                          int32_t max_depth, uint64_t sample_offset, mt_contrib *d_dump, int64_t cap,
                          int64_t *d_count, void *stream);
+
+/* ---- microbenchmarks for the memory/atomic roofline ----
+ * Rates the tracer's access patterns can reach on this GPU, measured with CUDA
+ * events on `stream` (second of two runs):
+ *   MT_MICRO_GATHER32    random 32-byte loads from d_buf (bytes long; L2
+ *                        resident when smaller than L2), *out_rate in GB/s
+ *   MT_MICRO_RED_GLOBAL  red.global.add.f32 at random addresses of d_buf, Gop/s
+ *   MT_MICRO_RED_SHARED  shared-memory atomicAdd.f32 into a 48 KB histogram per
+ *                        CTA, Gop/s (d_buf is only a sink)
+ * iters = accesses per thread.  d_buf must be device memory of >= 4096 bytes;
+ * its contents are overwritten by MT_MICRO_RED_GLOBAL.  Synchronises. */
+#define MT_MICRO_GATHER32 0
+#define MT_MICRO_RED_GLOBAL 1
+#define MT_MICRO_RED_SHARED 2
+mt_status mt_microbench(int32_t kind, void *d_buf, int64_t bytes, int32_t iters, double *out_rate, void *stream);
 
 /* ---- allocation-free variant ----
  * The paper has no counterpart of this call; it exists for callers that

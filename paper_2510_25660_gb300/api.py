@@ -85,6 +85,7 @@ SIGNATURES = {
     "mt_probe_bins": (C.c_int, [_P, _I64, _F, _F, _I32, _P, _P]),
     "mt_render_dump": (C.c_int, [_P, _P, _P, _I32, _U64, _I32, _U64, _P, _I64, _P, _P]),
     "mt_render_nlos_noalloc": (C.c_int, [_P, _P, _P, _I32, _U64, _U64, _P]),
+    "mt_microbench": (C.c_int, [_I32, _P, _I64, _I32, _P, _P]),
 }
 
 _lib = None
@@ -381,6 +382,22 @@ def render_dump(scene: Scene, H, W, T, start, width, spp, seed, max_depth, cap, 
     n = int(cnt.item())
     rec = dump[:min(n, cap)].cpu().numpy().view(CONTRIB_DTYPE).reshape(-1)
     return film, steady, rec, n
+
+
+MT_MICRO_GATHER32, MT_MICRO_RED_GLOBAL, MT_MICRO_RED_SHARED = 0, 1, 2
+
+
+def mt_microbench(kind, d_buf, nbytes, iters, out_rate, stream):
+    return _call("mt_microbench", kind, d_buf, nbytes, iters, out_rate, stream)
+
+
+def microbench(kind, nbytes=64 << 20, iters=256):
+    """Measured rate of one access pattern (GB/s for gathers, Gop/s for atomics)."""
+    import torch
+    buf = torch.zeros(max(nbytes, 4096) // 4, dtype=torch.float32, device="cuda")
+    rate = C.c_double(0.0)
+    mt_microbench(kind, _ptr(buf), buf.numel() * 4, iters, C.byref(rate), _stream())
+    return rate.value
 
 
 def probe_philox(seed, counters):

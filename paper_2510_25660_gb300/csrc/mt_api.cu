@@ -648,6 +648,7 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     p.tile_counter = s->tile_counter;
     p.n_em_smem = n_em_smem;
     p.aggregate = (cfg.options & MT_OPT_AGGREGATE) ? 1 : 0;
+    p.refill_min = std::max(1, std::min(32, (cfg.options >> 8) & 0xFF));
     if (mode != 2 && D < f->T && !acc) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
@@ -847,7 +848,8 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     MT_CHECK_ARG(threads == 0 || (threads >= 32 && threads <= 256 && threads % 32 == 0), "threads must be 32..256, x32");
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
     MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
-    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH)) == 0, "unknown launch options 0x%x", options);
+    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | 0xFF00u)) == 0, "unknown launch options 0x%x",
+                 options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;
     c.tile = tile;

@@ -235,9 +235,9 @@ __device__ __forceinline__ void raise_err(const DevScene &s, uint32_t bit) { ato
 // Add v to addr[0..n) (shared or global memory).  With aggregate set, the
 // lanes of the warp that target the same address first sum their values with
 // shuffles and only the group's first lane issues the atomics.
-template <int N>
-__device__ __forceinline__ void splat_add(float *addr, const float *v, bool aggregate) {
-    if (aggregate) {
+template <int N, bool AGG>
+__device__ __forceinline__ void splat_add(float *addr, const float *v) {
+    if (AGG) {
         const unsigned active = __activemask();
         const unsigned peers = __match_any_sync(active, (unsigned long long)addr);
         if (peers != (1u << (threadIdx.x & 31))) {

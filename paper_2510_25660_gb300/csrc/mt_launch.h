@@ -25,6 +25,7 @@ struct RenderParams {
     int *tile_counter;
     int32_t n_em_smem;         // emitters whose radiance gradients are summed in shared memory
     int32_t aggregate;         // warp-aggregated splats
+    int32_t refill_min;        // idle lanes needed before a warp starts new paths (1..32)
 };
 
 struct NlosParams {

@@ -176,8 +176,13 @@ __global__ void __launch_bounds__(256) k_nlos(const DevScene s, const NlosParams
                 const int bin = in ? (int)x : -1;
                 const float v = H * p.scale;
                 if (in) {
-                    if (bin < p.D) splat_add<1>(&hist[r * p.D + bin], &v, p.aggregate);
-                    else splat_add<1>(&p.film[(size_t)(row0 + r) * p.T + bin], &v, p.aggregate);
+                    if (p.aggregate) {
+                        if (bin < p.D) splat_add<1, true>(&hist[r * p.D + bin], &v);
+                        else splat_add<1, true>(&p.film[(size_t)(row0 + r) * p.T + bin], &v);
+                    } else {
+                        if (bin < p.D) atomicAdd(&hist[r * p.D + bin], v);
+                        else atomicAdd(&p.film[(size_t)(row0 + r) * p.T + bin], v);
+                    }
                 }
                 atomicAdd(&steady_s[r], v);
                 if (DUMP) {

@@ -133,7 +133,7 @@ __device__ __forceinline__ int pick_unit(const DevScene &s, uint32_t u) {
     return lo;
 }
 
-template <int MODE, bool MEDIA, bool CNT>
+template <int MODE, bool MEDIA, bool CNT, bool AGG>
 struct Tracer {
     const DevScene &s;
     const RenderParams &p;
@@ -157,10 +157,10 @@ struct Tracer {
             if (in) {
                 const float cv[3] = {c.x, c.y, c.z};
                 if (bin < p.D) {
-                    splat_add<3>(hist + ((size_t)ps.lp * p.D + bin) * 3, cv, p.aggregate);
+                    splat_add<3, AGG>(hist + ((size_t)ps.lp * p.D + bin) * 3, cv);
                     cnt.smem_splats++;
                 } else {
-                    splat_add<3>(p.film + ((size_t)ps.pix * p.T + bin) * 3, cv, p.aggregate);
+                    splat_add<3, AGG>(p.film + ((size_t)ps.pix * p.T + bin) * 3, cv);
                     cnt.gmem_splats++;
                 }
             }
@@ -432,7 +432,7 @@ struct Tracer {
     }
 };
 
-template <int MODE, bool MEDIA, bool CNT>
+template <int MODE, bool MEDIA, bool CNT, bool AGG>
 __global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s, const RenderParams p) {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s
         if (threadIdx.x == 0) s_med = 0.f;
         __syncthreads();
     }
-    Tracer<MODE, MEDIA, CNT> tr{s, p, hist, steady_s, em_acc, s_med, cnt, vrec, Rng{p.k0, p.k1}};
+    Tracer<MODE, MEDIA, CNT, AGG> tr{s, p, hist, steady_s, em_acc, s_med, cnt, vrec, Rng{p.k0, p.k1}};
     for (;;) {
         // the warp claims its next tile
         int tile = 0;
@@ -481,14 +481,16 @@ __global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s
         for (;;) {
             if (next < n_paths) {
                 const unsigned need = __ballot_sync(0xffffffffu, !active);
-                if (!active) {
-                    const int j = next + __popc(need & ((1u << lane) - 1u));
-                    if (j < n_paths) {
-                        tr.begin(ps, j, pix0, x0, ty);
-                        active = true;
+                if (__popc(need) >= p.refill_min || need == 0xffffffffu) {
+                    if (!active) {
+                        const int j = next + __popc(need & ((1u << lane) - 1u));
+                        if (j < n_paths) {
+                            tr.begin(ps, j, pix0, x0, ty);
+                            active = true;
+                        }
                     }
+                    next += __popc(need);
                 }
-                next += __popc(need);
             }
             if (!__any_sync(0xffffffffu, active)) break;
             if (active) {
@@ -552,9 +554,9 @@ __global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s
     }
 }
 
-template <int MODE, bool MEDIA, bool CNT>
+template <int MODE, bool MEDIA, bool CNT, bool AGG>
 mt_status launch_one(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, cudaStream_t st) {
-    auto kern = k_render<MODE, MEDIA, CNT>;
+    auto kern = k_render<MODE, MEDIA, CNT, AGG>;
     const size_t smem = cfg.smem_bytes;
     MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -571,14 +573,21 @@ mt_status launch_one(const DevScene &s, const RenderParams &p, const LaunchCfg &
     return MT_OK;
 }
 
+template <int MODE, bool MEDIA, bool CNT>
+mt_status launch_agg(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, cudaStream_t st) {
+    // the backward pass splats nothing; only forward kernels get the aggregating variant
+    if (MODE != MODE_BWD && p.aggregate) return launch_one<MODE, MEDIA, CNT, true>(s, p, cfg, st);
+    return launch_one<MODE, MEDIA, CNT, false>(s, p, cfg, st);
+}
+
 }  // namespace
 
 mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const LaunchCfg &cfg, int mode, bool counters,
                            cudaStream_t st) {
     const bool media = s.has_medium;
 #define MT_DISPATCH(M)                                                                 \
-    if (media) return counters ? launch_one<M, true, true>(s, p, cfg, st) : launch_one<M, true, false>(s, p, cfg, st); \
-    return counters ? launch_one<M, false, true>(s, p, cfg, st) : launch_one<M, false, false>(s, p, cfg, st);
+    if (media) return counters ? launch_agg<M, true, true>(s, p, cfg, st) : launch_agg<M, true, false>(s, p, cfg, st); \
+    return counters ? launch_agg<M, false, true>(s, p, cfg, st) : launch_agg<M, false, false>(s, p, cfg, st);
     if (mode == 0) { MT_DISPATCH(MODE_FWD) }
     if (mode == 1) { MT_DISPATCH(MODE_DUMP) }
     MT_DISPATCH(MODE_BWD)

@@ -103,8 +103,8 @@ struct TraceCnt {
 // Closest hit with t in (0, tmax); ties in t go to the smaller original index.
 // Returns the leaf-order triangle index (or -1) and writes t and the original index.
 template <bool CNT>
-__device__ __forceinline__ int trace_closest(const DevScene &s, const RayT &r, float tmax, float &t_out,
-                                             int &orig_out, TraceCnt &cnt) {
+__device__ __forceinline__ int trace_closest_simple(const DevScene &s, const RayT &r, float tmax, float &t_out,
+                                                    int &orig_out, TraceCnt &cnt) {
     float tbest = tmax;
     int best_k = -1, best_id = 0x7fffffff;
     uint32_t st_ref[MT_STACK];
@@ -171,7 +171,7 @@ __device__ __forceinline__ int trace_closest(const DevScene &s, const RayT &r, f
 
 // Any hit with t in (0, tmax).
 template <bool CNT>
-__device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, float tmax, TraceCnt &cnt) {
+__device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &r, float tmax, TraceCnt &cnt) {
     uint32_t st_ref[MT_STACK];
     int sp = 0;
     uint32_t ref = 0;
@@ -208,4 +208,127 @@ __device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, floa
         if (sp == 0) return false;
         ref = st_ref[--sp];
     }
+}
+
+// ---------------------------------------------------------------------------
+// "While-while" traversal with speculative leaf postponing (Aila & Laine,
+// HPG 2009): a lane keeps descending internal nodes after it met a leaf, which
+// it postpones, until every lane of the warp holds a leaf; then the lanes test
+// their leaves' triangles together.  Only the visiting order changes: the
+// closest hit is still the smallest (t, original index).
+// ---------------------------------------------------------------------------
+#define MT_DONE 0xFFFFFFFEu
+#define MT_IS_LEAF(r) (((r) & 0x80000000u) != 0u)
+
+template <bool ANY, bool CNT>
+__device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float tmax, float &t_out, int &orig_out,
+                                        TraceCnt &cnt) {
+    float tbest = tmax;
+    int best_k = -1, best_id = 0x7fffffff;
+    uint32_t st_ref[MT_STACK];
+    float st_t[MT_STACK];
+    int sp = 0;
+    uint32_t ref = 0, leaf = MT_DONE;
+    auto pop = [&]() -> uint32_t {
+        while (sp > 0) {
+            --sp;
+            if (ANY || st_t[sp] <= tbest) return st_ref[sp];
+        }
+        return MT_DONE;
+    };
+    while (ref != MT_DONE) {
+        // internal nodes; the first leaf met is postponed
+        while (ref != MT_DONE && !MT_IS_LEAF(ref)) {
+            const uint4 a = __ldg(&s.nodes[2 * ref]);
+            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            if (CNT) cnt.nodes++;
+            float tn0, tf0, tn1, tf1;
+            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tbest, tn0, tf0);
+            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tbest, tn1, tf1);
+            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
+            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            if (h0 && h1) {
+                const bool f0 = tn0 <= tn1;
+                if (sp < MT_STACK) {
+                    st_ref[sp] = f0 ? b.w : b.z;
+                    st_t[sp] = f0 ? tn1 : tn0;
+                    ++sp;
+                } else {
+                    raise_err(s, MT_EFLAG_STACK);
+                }
+                ref = f0 ? b.z : b.w;
+            } else if (h0) {
+                ref = b.z;
+            } else if (h1) {
+                ref = b.w;
+            } else {
+                ref = pop();
+            }
+            if (ref != MT_DONE && MT_IS_LEAF(ref) && leaf == MT_DONE) {
+                leaf = ref;
+                ref = pop();
+            }
+            if (!__any_sync(__activemask(), leaf == MT_DONE)) break;
+        }
+        // leaves: the postponed one, then the current reference while it is a leaf
+        for (;;) {
+            if (leaf == MT_DONE) {
+                if (ref != MT_DONE && MT_IS_LEAF(ref)) {
+                    leaf = ref;
+                    ref = pop();
+                } else {
+                    break;
+                }
+            }
+            const int first = (int)(leaf & 0x1FFFFFFFu), n = (int)((leaf >> 29) & 3u) + 1;
+            leaf = MT_DONE;
+            for (int k = first; k < first + n; ++k) {
+                const float4 p0 = __ldg(&s.tris[3 * k]);
+                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
+                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                if (CNT) cnt.tris++;
+                float t;
+                if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                    if (ANY) return 1;
+                    const int id = __float_as_int(p0.w);
+                    if (t < tbest || (t == tbest && id < best_id)) {
+                        tbest = t;
+                        best_k = k;
+                        best_id = id;
+                    }
+                }
+            }
+        }
+    }
+    if (ANY) return 0;
+    t_out = tbest;
+    orig_out = best_id;
+    return best_k;
+}
+
+// while-while traversal measured slower than the single loop on GB300 for the
+// large scene (269 ms against 244 ms per render), so it is off by default
+#ifndef MT_TRAVERSAL_WW
+#define MT_TRAVERSAL_WW 0
+#endif
+
+template <bool CNT>
+__device__ __forceinline__ int trace_closest(const DevScene &s, const RayT &r, float tmax, float &t_out,
+                                             int &orig_out, TraceCnt &cnt) {
+#if MT_TRAVERSAL_WW
+    return trace_ww<false, CNT>(s, r, tmax, t_out, orig_out, cnt);
+#else
+    return trace_closest_simple<CNT>(s, r, tmax, t_out, orig_out, cnt);
+#endif
+}
+
+template <bool CNT>
+__device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, float tmax, TraceCnt &cnt) {
+#if MT_TRAVERSAL_WW
+    float t;
+    int id;
+    return trace_ww<true, CNT>(s, r, tmax, t, id, cnt) != 0;
+#else
+    return trace_any_simple<CNT>(s, r, tmax, cnt);
+#endif
 }
