@@ -214,9 +214,16 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * MT_OPT_NO_GRAPH (NLOS) = enqueue the kernels directly instead of replaying
  * the cached CUDA graph.  MT_OPT_REFILL(k) (RENDER/BACKWARD, k = 1..32) = a
  * warp starts new paths only once at least k of its lanes are idle (default 1:
- * every idle lane is refilled at once). */
+ * every idle lane is refilled at once).  MT_OPT_WAVEFRONT (RENDER, surfaces
+ * only) = render in wavefront form: a pool of up to 4M paths in device memory
+ * (about 150 B per path, allocated by the first such render of a scene) with
+ * separate kernels for camera rays, extension rays, shading and shadow rays,
+ * each warp claiming rays of one kind from a queue; films are zeroed and
+ * written with global atomics (tile, priv_bins and the refill option do not
+ * apply); the call synchronises `stream` every few iterations. */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
+#define MT_OPT_WAVEFRONT 4u
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1

@@ -90,6 +90,15 @@ struct mt_scene_s {
     long long ysamp_cap = 0;
     GraphCache nlos_graph;
     cudaStream_t cap_stream = nullptr;  // private stream the NLOS graph is captured on
+    // wavefront path pool
+    uint32_t wf_cap = 0;
+    float4 *wf_o = nullptr, *wf_d = nullptr, *wf_beta = nullptr, *wf_sh_o = nullptr, *wf_sh_d = nullptr,
+           *wf_sh_c = nullptr;
+    uint4 *wf_meta = nullptr, *wf_sh_m = nullptr;
+    int4 *wf_hit = nullptr;
+    uint32_t *wf_qa = nullptr, *wf_qb = nullptr, *wf_free = nullptr, *wf_counters = nullptr;
+    unsigned long long *wf_next = nullptr;
+    void *wf_iter = nullptr;
     size_t bytes = 0;
 };
 
@@ -600,6 +609,78 @@ static mt_status check_err_word(mt_scene s) {
     return MT_OK;
 }
 
+// forward render in wavefront form: a pool of paths in device memory
+static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp, const LaunchCfg &cfg, bool dump,
+                                  cudaStream_t st) {
+    const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
+    const uint32_t P = (uint32_t)std::min<unsigned long long>(total, 1ull << 22);
+    if (P > s->wf_cap) {
+        cudaStreamCaptureStatus cs;
+        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                     "the first wavefront render of this size must not be captured (it sizes the path pool)");
+        auto &al = s->al;
+        MT_TRY(al.alloc(&s->wf_o, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_d, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_beta, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_meta, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_hit, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_qa, P, "path queues"));
+        MT_TRY(al.alloc(&s->wf_qb, P, "path queues"));
+        MT_TRY(al.alloc(&s->wf_free, P, "path queues"));
+        MT_TRY(al.alloc(&s->wf_sh_o, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_d, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
+        if (!s->wf_counters) {
+            MT_TRY(al.alloc(&s->wf_counters, 8, "path queue counters"));
+            MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
+            MT_TRY(al.alloc((char **)&s->wf_iter, 64, "path queue counters"));
+        }
+        s->wf_cap = P;
+    }
+    WfParams w{};
+    w.H = rp.H;
+    w.W = rp.W;
+    w.T = rp.T;
+    w.start = rp.start;
+    w.width = rp.width;
+    w.scale = rp.scale;
+    w.flags = rp.flags;
+    w.spp = rp.spp;
+    w.max_depth = rp.max_depth;
+    w.sample_offset = rp.sample_offset;
+    w.k0 = rp.k0;
+    w.k1 = rp.k1;
+    w.total_paths = total;
+    w.P = P;
+    w.film = rp.film;
+    w.steady = rp.steady;
+    w.o = s->wf_o;
+    w.d = s->wf_d;
+    w.beta = s->wf_beta;
+    w.meta = s->wf_meta;
+    w.hit = s->wf_hit;
+    w.qa = s->wf_qa;
+    w.qb = s->wf_qb;
+    w.free_q = s->wf_free;
+    w.sh_o = s->wf_sh_o;
+    w.sh_d = s->wf_sh_d;
+    w.sh_c = s->wf_sh_c;
+    w.sh_m = s->wf_sh_m;
+    w.counters = s->wf_counters;
+    w.next_path = s->wf_next;
+    w.iter = (struct WfIter *)s->wf_iter;
+    w.dump = rp.dump;
+    w.dump_cap = rp.dump_cap;
+    w.dump_count = rp.dump_count;
+    if (!(rp.flags & MT_ACCUMULATE)) {
+        MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
+        if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
+    }
+    return mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st);
+}
+
 static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
                                uint64_t sample_offset, int mode, const float *gfilm, const float *gsteady,
                                float *galb, float *grad, float *gmed, mt_contrib *dump, int64_t cap,
@@ -653,6 +734,8 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
+    if (mode != 2 && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
+        return render_wavefront(s, f, p, cfg, mode == 1, st);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
     return mt_launch_render(s->dev, p, cfg, mode, (f->flags & MT_COUNTERS) != 0, st);
 }
@@ -848,8 +931,8 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     MT_CHECK_ARG(threads == 0 || (threads >= 32 && threads <= 256 && threads % 32 == 0), "threads must be 32..256, x32");
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
     MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
-    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | 0xFF00u)) == 0, "unknown launch options 0x%x",
-                 options);
+    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | MT_OPT_WAVEFRONT | 0xFF00u)) == 0,
+                 "unknown launch options 0x%x", options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;
     c.tile = tile;

@@ -544,13 +544,14 @@ __global__ void k_internal_flags(const BNode *nodes, int n, int *flags) {
         flags[i] = nodes[i].left >= 0 ? 1 : 0;
 }
 
+// planes rounded outward and padded by two quantisation steps
 __device__ __forceinline__ uint32_t qfloor(float v, double lo, double sc) {
-    double q = floor(((double)v - lo) / sc) - 1.0;
+    double q = floor(((double)v - lo) / sc) - 2.0;
     q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
     return (uint32_t)q;
 }
 __device__ __forceinline__ uint32_t qceil(float v, double lo, double sc) {
-    double q = ceil(((double)v - lo) / sc) + 1.0;
+    double q = ceil(((double)v - lo) / sc) + 2.0;
     q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
     return (uint32_t)q;
 }
@@ -579,8 +580,9 @@ __global__ void k_emit(const BNode *nodes, int n, const int *map, const int *fla
         quant_box(nodes[nd.left], qlo, qs, a);
         quant_box(nodes[nd.right], qlo, qs, b);
         const int m = map[i];
-        out[2 * m] = make_uint4(a[0] | (a[1] << 16), a[2] | (a[3] << 16), a[4] | (a[5] << 16), b[0] | (b[1] << 16));
-        out[2 * m + 1] = make_uint4(b[2] | (b[3] << 16), b[4] | (b[5] << 16), child_ref(nodes, map, nd.left),
+        // a[k] = lower plane, a[3 + k] = upper plane of axis k
+        out[2 * m] = make_uint4(a[0] | (a[3] << 16), a[1] | (a[4] << 16), a[2] | (a[5] << 16), b[0] | (b[3] << 16));
+        out[2 * m + 1] = make_uint4(b[1] | (b[4] << 16), b[2] | (b[5] << 16), child_ref(nodes, map, nd.left),
                                     child_ref(nodes, map, nd.right));
     }
 }
@@ -591,8 +593,9 @@ __global__ void k_emit_root_leaf(const BNode *nodes, uint4 *out, float qlx, floa
     uint32_t a[6];
     quant_box(nodes[0], qlo, qs, a);
     const uint32_t ref = 0x80000000u | ((uint32_t)(nodes[0].count - 1) << 29) | (uint32_t)nodes[0].first;
-    out[0] = make_uint4(a[0] | (a[1] << 16), a[2] | (a[3] << 16), a[4] | (a[5] << 16), 0xFFFFu);
-    out[1] = make_uint4(0u, 0u, ref, MT_EMPTY_REF);
+    // child 1 is empty: lower plane 65535 above upper plane 0 on every axis
+    out[0] = make_uint4(a[0] | (a[3] << 16), a[1] | (a[4] << 16), a[2] | (a[5] << 16), 0xFFFFu);
+    out[1] = make_uint4(0xFFFFu, 0xFFFFu, ref, MT_EMPTY_REF);
 }
 
 __global__ void k_reorder(const float *tris, const int *idx, int n, float4 *out) {
@@ -772,8 +775,8 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
         return MT_ERR_UNSUPPORTED;
     }
 
-    // quantisation frame: scene box mapped into [1, 65534] so that the
-    // outward-rounded planes never clamp
+    // quantisation frame: scene box mapped into [3, 65532] so that the
+    // outward-rounded, two-step padded planes never clamp
     double ext[3], mx = 0.0;
     for (int k = 0; k < 3; ++k) {
         ext[k] = (double)box[3 + k] - (double)box[k];
@@ -781,8 +784,8 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
     }
     for (int k = 0; k < 3; ++k) {
         const double e = std::max(std::max(ext[k], 1e-4 * mx), 1e-12) * (1.0 + 1.0 / 1024.0);
-        out->q_scale[k] = (float)(e / 65533.0);
-        out->q_lo[k] = (float)((double)box[k] - (double)out->q_scale[k]);
+        out->q_scale[k] = (float)(e / 65529.0);
+        out->q_lo[k] = (float)((double)box[k] - 3.0 * (double)out->q_scale[k]);
     }
 
     // internal nodes -> dense compact nodes

@@ -52,6 +52,29 @@ struct NlosParams {
     int32_t aggregate;         // warp-aggregated splats
 };
 
+struct WfParams {
+    int32_t H, W, T;
+    float start, width, scale;
+    uint32_t flags;
+    int32_t spp, max_depth;
+    uint32_t sample_offset, k0, k1;
+    unsigned long long total_paths;
+    uint32_t P;                    // paths in flight (pool size)
+    float *film, *steady;
+    float4 *o, *d, *beta;          // path state: origin + OPL, direction + pdf of the last BSDF sample, throughput
+    uint4 *meta;                   // pixel, sample index, depth
+    int4 *hit;                     // leaf-order triangle, original triangle, t bits
+    uint32_t *qa, *qb, *free_q;    // extension queues and the free-slot stack
+    float4 *sh_o, *sh_d, *sh_c;    // shadow rays: origin + tmax, direction + OPL, contribution + pixel
+    uint4 *sh_m;                   // shadow ray record: sample, depth, emitter triangle
+    uint32_t *counters;            // queue counts and cursors
+    unsigned long long *next_path;
+    struct WfIter *iter;
+    mt_contrib *dump;
+    long long dump_cap;
+    unsigned long long *dump_count;
+};
+
 struct LaunchCfg {
     int threads, tile, ctas_per_sm, num_sms;
     size_t smem_bytes;
@@ -63,3 +86,5 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
                            cudaStream_t st);
 mt_status mt_launch_nlos(const DevScene &s, const NlosParams &p, const LaunchCfg &cfg, bool dump, bool counters,
                          cudaStream_t st);
+mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p, int num_sms, bool dump, bool counters,
+                              cudaStream_t st);

@@ -3,11 +3,12 @@
 // Visibility V and segment lengths of the path integral (arXiv 2510.25660,
 // Sec. 3 Eqs. 3 and 8) come from these queries.
 //
-// Node layout (32 bytes = one L2 sector, fetched as two 16-byte loads):
-//   a.x = lo0.x | lo0.y<<16   a.y = lo0.z | hi0.x<<16   a.z = hi0.y | hi0.z<<16
-//   a.w = lo1.x | lo1.y<<16   b.x = lo1.z | hi1.x<<16   b.y = hi1.y | hi1.z<<16
-//   b.z = child 0 reference   b.w = child 1 reference
-// The twelve planes are 16-bit fixed point in the scene box, rounded outward
+// Node layout (32 bytes = one L2 sector, fetched as two 16-byte loads): one
+// 32-bit word per child and axis holds that axis' lower plane (low half) and
+// upper plane (high half):
+//   a.x = child 0 x   a.y = child 0 y   a.z = child 0 z   a.w = child 1 x
+//   b.x = child 1 y   b.y = child 1 z   b.z = child 0 reference   b.w = child 1 reference
+// Planes are 16-bit fixed point in the scene box, rounded outward by two steps
 // (plane = q_lo + q * q_scale), so boxes are conservative.  A reference with
 // bit 31 clear is an internal node index; with bit 31 set it is a leaf of
 // ((ref >> 29) & 3) + 1 triangles starting at (ref & 0x1FFFFFFF); 0xFFFFFFFF
@@ -20,7 +21,8 @@
 
 struct RayT {
     float3 o, d;
-    float3 sa, sb;   // slab parameter t = q * sa + sb for a quantised plane q
+    float3 sa, sb;   // slab: t = (2^23 + q) * sa + sb for a quantised plane q
+    uint32_t sel_n[3];  // byte-permute selector of the near plane per axis (far = near ^ 0x22)
     int kx, ky, kz;  // watertight test axes (Woop, Benthin, Wald, JCGT 2013)
     float Sx, Sy, Sz;
 };
@@ -37,7 +39,14 @@ __device__ __forceinline__ RayT make_ray(const DevScene &s, float3 o, float3 d) 
     const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
     const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
     r.sa = f3(s.q_scale.x * ix, s.q_scale.y * iy, s.q_scale.z * iz);
-    r.sb = f3((s.q_lo.x - o.x) * ix, (s.q_lo.y - o.y) * iy, (s.q_lo.z - o.z) * iz);
+    // the 2^23 offset of the exponent trick below is folded into sb; the two
+    // 2^23 * sa terms cancel exactly inside the FMA, leaving one rounding of sb
+    // (at most half a quantisation step, inside the two-step padding)
+    r.sb = f3((s.q_lo.x - o.x) * ix - 8388608.0f * r.sa.x, (s.q_lo.y - o.y) * iy - 8388608.0f * r.sa.y,
+              (s.q_lo.z - o.z) * iz - 8388608.0f * r.sa.z);
+    const float dd[3] = {dx, dy, dz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.sel_n[k] = dd[k] >= 0.0f ? 0x7610u : 0x7632u;  // low half = lower plane
     const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -57,21 +66,23 @@ __device__ __forceinline__ RayT make_ray(const DevScene &s, float3 o, float3 d) 
     return r;
 }
 
-// 16-bit fixed point -> exact float via the 2^23 magic exponent
-__device__ __forceinline__ float q_lo16(uint32_t x) {
-    return __int_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8388608.0f;
-}
-__device__ __forceinline__ float q_hi16(uint32_t x) {
-    return __int_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8388608.0f;
+// 16-bit fixed point q -> the float 2^23 + q (exact) by writing q under the
+// exponent of 2^23 with one byte permute
+__device__ __forceinline__ float q_plane(uint32_t word, uint32_t sel) {
+    return __int_as_float(__byte_perm(word, 0x4B000000u, sel));
 }
 
-__device__ __forceinline__ void slab(const RayT &r, float lx, float ly, float lz, float hx, float hy, float hz,
-                                     float tmax, float &tn, float &tf) {
-    const float x0 = fmaf(lx, r.sa.x, r.sb.x), x1 = fmaf(hx, r.sa.x, r.sb.x);
-    const float y0 = fmaf(ly, r.sa.y, r.sb.y), y1 = fmaf(hy, r.sa.y, r.sb.y);
-    const float z0 = fmaf(lz, r.sa.z, r.sb.z), z1 = fmaf(hz, r.sa.z, r.sb.z);
-    tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
-    tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+// entry / exit distance of one child box; wx, wy, wz are its three axis words
+__device__ __forceinline__ void slab(const RayT &r, uint32_t wx, uint32_t wy, uint32_t wz, float tmax, float &tn,
+                                     float &tf) {
+    const float nx = fmaf(q_plane(wx, r.sel_n[0]), r.sa.x, r.sb.x);
+    const float fx = fmaf(q_plane(wx, r.sel_n[0] ^ 0x22u), r.sa.x, r.sb.x);
+    const float ny = fmaf(q_plane(wy, r.sel_n[1]), r.sa.y, r.sb.y);
+    const float fy = fmaf(q_plane(wy, r.sel_n[1] ^ 0x22u), r.sa.y, r.sb.y);
+    const float nz = fmaf(q_plane(wz, r.sel_n[2]), r.sa.z, r.sb.z);
+    const float fz = fmaf(q_plane(wz, r.sel_n[2] ^ 0x22u), r.sa.z, r.sb.z);
+    tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
+    tf = fminf(fminf(fx, fy), fminf(fz, tmax));
 }
 
 // Watertight ray/triangle test.  The edge functions are evaluated without
@@ -107,8 +118,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
                                                     int &orig_out, TraceCnt &cnt) {
     float tbest = tmax;
     int best_k = -1, best_id = 0x7fffffff;
-    uint32_t st_ref[MT_STACK];
-    float st_t[MT_STACK];
+    uint2 st[MT_STACK];  // (reference, entry distance bits)
     int sp = 0;
     uint32_t ref = 0;
     for (;;) {
@@ -117,15 +127,14 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes++;
             float tn0, tf0, tn1, tf1;
-            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tbest, tn0, tf0);
-            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tbest, tn1, tf1);
+            slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
+            slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
             const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
             const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
                 if (sp < MT_STACK) {
-                    st_ref[sp] = f0 ? b.w : b.z;
-                    st_t[sp] = f0 ? tn1 : tn0;
+                    st[sp] = make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0));
                     ++sp;
                 } else {
                     raise_err(s, MT_EFLAG_STACK);
@@ -161,8 +170,9 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
                 return best_k;
             }
             --sp;
-            if (st_t[sp] <= tbest) {
-                ref = st_ref[sp];
+            const uint2 e = st[sp];
+            if (__uint_as_float(e.y) <= tbest) {
+                ref = e.x;
                 break;
             }
         }
@@ -181,8 +191,8 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes++;
             float tn0, tf0, tn1, tf1;
-            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tmax, tn0, tf0);
-            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tmax, tn1, tf1);
+            slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
+            slab(r, a.w, b.x, b.y, tmax, tn1, tf1);
             const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
             const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
             if (h0 && h1) {
@@ -243,8 +253,8 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes++;
             float tn0, tf0, tn1, tf1;
-            slab(r, q_lo16(a.x), q_hi16(a.x), q_lo16(a.y), q_hi16(a.y), q_lo16(a.z), q_hi16(a.z), tbest, tn0, tf0);
-            slab(r, q_lo16(a.w), q_hi16(a.w), q_lo16(b.x), q_hi16(b.x), q_lo16(b.y), q_hi16(b.y), tbest, tn1, tf1);
+            slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
+            slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
             const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
             const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
             if (h0 && h1) {

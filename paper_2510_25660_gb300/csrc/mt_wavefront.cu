@@ -1,0 +1,406 @@
+// mt_wavefront.cu -- wavefront form of the forward transient path tracer.
+//
+// The same estimator as k_render (arXiv 2510.25660 Sec. 3: paths, optical
+// path length, next-event estimation with power-heuristic MIS, path reuse into
+// time bins), reorganised so that every traversal kernel sees only one kind of
+// ray: a pool of P paths lives in device memory and each iteration runs
+//   k_wf_setup     bookkeeping of queue counts, how many new paths to start
+//   k_wf_generate  camera rays for new paths in free pool slots
+//   k_wf_extend    closest hits of all queued extension rays
+//   k_wf_shade     emission found by the path, next-event sample (a shadow ray
+//                  carrying its contribution), BSDF sample, continuation
+//   k_wf_shadow    any-hit test of the shadow rays, splat of unoccluded ones
+// Warps claim rays 32 at a time from a queue cursor, so lanes stay busy until
+// the queue drains; appends to the queues are warp-aggregated.  New paths get
+// consecutive ids (pixel-major), so camera rays of a warp share a pixel.
+// Contributions go to the film with global atomics (no per-tile ownership).
+#include "mt_common.cuh"
+#include "mt_internal.h"
+#include "mt_launch.h"
+#include "mt_trace.cuh"
+
+struct WfIter {
+    uint32_t cont, n_new, free_before;
+    unsigned long long base;
+};
+
+namespace {
+
+// counters[] layout
+enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_PAD = 7 };
+
+__device__ __forceinline__ float mis2w(float a, float b) { return a * a / (a * a + b * b); }
+
+__device__ __forceinline__ int pick_unit_wf(const DevScene &s, uint32_t u) {
+    int lo = 0, hi = s.n_units - 1;
+    const uint32_t key = u >> 8;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key < __ldg(&s.unit_cdf[mid])) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// warp-aggregated append of one entry per participating lane; returns the slot
+__device__ __forceinline__ uint32_t wf_append(uint32_t *count, bool want) {
+    // every lane of the warp calls this together (shade loops in whole warps)
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (!want) return 0;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void wf_splat(const WfParams &p, uint32_t pix, float opl, float3 c) {
+    const float x = (opl - p.start) / p.width;
+    if (x >= 0.f && x < (float)p.T) {
+        float *h = p.film + ((size_t)pix * p.T + (int)x) * 3;
+        atomicAdd(h, c.x);
+        atomicAdd(h + 1, c.y);
+        atomicAdd(h + 2, c.z);
+    }
+    if (p.steady) {
+        float *g = p.steady + (size_t)pix * 3;
+        atomicAdd(g, c.x);
+        atomicAdd(g + 1, c.y);
+        atomicAdd(g + 2, c.z);
+    }
+}
+
+__device__ __forceinline__ void wf_dump(const WfParams &p, uint32_t pix, uint32_t smp, int depth, int kind, int tri,
+                                        float opl, float3 c) {
+    const unsigned long long slot = atomicAdd(p.dump_count, 1ull);
+    if ((long long)slot < p.dump_cap) {
+        const float x = (opl - p.start) / p.width;
+        mt_contrib r;
+        r.pixel = (int32_t)pix;
+        r.sample = (int32_t)smp;
+        r.depth = depth;
+        r.kind = kind;
+        r.tri = tri;
+        r.bin = (x >= 0.f && x < (float)p.T) ? (int)x : (int)floorf(x);
+        r.opl = opl;
+        r.c[0] = c.x / p.scale;
+        r.c[1] = c.y / p.scale;
+        r.c[2] = c.z / p.scale;
+        p.dump[slot] = r;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_count(unsigned long long *dst, T v) {
+    unsigned long long x = v;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(dst, x);
+}
+
+__global__ void k_wf_setup(WfParams p, WfIter *it) {
+    uint32_t *c = p.counters;
+    const uint32_t cont = c[C_NEXT], freec = c[C_FREE];
+    const unsigned long long base = *p.next_path;
+    const unsigned long long remain = base < p.total_paths ? p.total_paths - base : 0ull;
+    const uint32_t n_new = (uint32_t)min((unsigned long long)freec, remain);
+    it->cont = cont;
+    it->n_new = n_new;
+    it->free_before = freec;
+    it->base = base;
+    c[C_CUR] = cont + n_new;
+    c[C_NEXT] = 0;
+    c[C_SHADOW] = 0;
+    c[C_FREE] = freec - n_new;
+    c[C_EXT_CUR] = 0;
+    c[C_SH_CUR] = 0;
+    c[C_DONE] = (cont + n_new == 0) ? 1u : 0u;
+    *p.next_path = base + n_new;
+}
+
+__global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfParams p, const WfIter *itp,
+                                                     uint32_t *qcur) {
+    const WfIter it = *itp;
+    uint32_t paths = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < it.n_new; i += gridDim.x * blockDim.x) {
+        const uint32_t slot = p.free_q[it.free_before - 1 - i];
+        const unsigned long long j = it.base + i;
+        const uint32_t pix = (uint32_t)(j / p.spp);
+        const uint32_t smp = p.sample_offset + (uint32_t)(j - (unsigned long long)pix * p.spp);
+        const uint4 R = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.k0, p.k1);
+        const bool center = p.flags & MT_PIXEL_CENTER;
+        const float jx = center ? 0.5f : u24(R.x), jy = center ? 0.5f : u24(R.y);
+        const uint32_t py = pix / (uint32_t)p.W, px = pix - py * (uint32_t)p.W;
+        const float sx = (2.0f * ((float)px + jx) / (float)p.W - 1.0f) * s.tan_half;
+        const float sy = (1.0f - 2.0f * ((float)py + jy) / (float)p.H) * s.tan_half * ((float)p.H / (float)p.W);
+        const float3 d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
+        p.o[slot] = make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f);
+        p.d[slot] = make_float4(d.x, d.y, d.z, 0.f);
+        p.beta[slot] = make_float4(1.f, 1.f, 1.f, 0.f);
+        p.meta[slot] = make_uint4(pix, smp, 1u, 0u);
+        qcur[it.cont + i] = slot;
+        paths++;
+    }
+    warp_count(&s.counters[1], paths);
+}
+
+template <bool CNT>
+__global__ void __launch_bounds__(256) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
+    const uint32_t n = p.counters[C_CUR];
+    const int lane = threadIdx.x & 31;
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&p.counters[C_EXT_CUR], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i < n) {
+            const uint32_t slot = qcur[i];
+            const float4 o = p.o[slot], d = p.d[slot];
+            const RayT r = make_ray(s, xyz(o), xyz(d));
+            float t;
+            int orig;
+            const int k = trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
+            p.hit[slot] = make_int4(k, orig, __float_as_int(t), 0);
+            rays++;
+        }
+    }
+    warp_count(&s.counters[3], rays);
+    if (CNT) {
+        warp_count(&s.counters[4], tc.nodes);
+        warp_count(&s.counters[5], tc.tris);
+    }
+}
+
+template <bool DUMP>
+__global__ void __launch_bounds__(256) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
+                                                  uint32_t *qnext) {
+    const uint32_t n = p.counters[C_CUR];
+    uint32_t verts = 0, contribs = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (warp-level appends)
+    const uint32_t n_round = ((n + 31u) / 32u) * 32u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        bool valid = i < n;
+        const uint32_t slot = valid ? qcur[i] : 0u;
+        bool cont = false, shadow = false, done = false;
+        float4 sh_o = make_float4(0, 0, 0, 0), sh_d = sh_o, sh_c = sh_o;
+        uint4 sh_m = make_uint4(0, 0, 0, 0);
+        float4 o4 = sh_o, d4 = sh_o, b4 = sh_o;
+        uint4 m = sh_m;
+        if (valid) {
+            o4 = p.o[slot];
+            d4 = p.d[slot];
+            b4 = p.beta[slot];
+            m = p.meta[slot];
+            const int4 h = p.hit[slot];
+            const uint32_t pix = m.x, smp = m.y;
+            const int depth = (int)m.z;
+            float opl = o4.w;
+            float3 beta = xyz(b4);
+            const float3 dir = xyz(d4);
+            if (h.x < 0) {
+                done = true;
+            } else {
+                verts++;
+                const int k = h.x, orig = h.y;
+                const float th = __int_as_float(h.z);
+                const float3 x = xyz(o4) + dir * th;
+                if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
+                const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
+                const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+                const float3 wo = -dir;
+                const float cwo = dot(ng, wo);
+                const int unit = __ldg(&s.tri_unit[orig]);
+                if (unit >= 0 && cwo > 0.f) {
+                    const LightUnit U = s.units[unit];
+                    float w = 1.0f;
+                    if (depth > 1) w = mis2w(d4.w, (U.v1.w / U.v0.w) * th * th / cwo);
+                    const int em = __float_as_int(U.v2.w);
+                    const float3 c = mul(beta * w, xyz(s.em_rad[em])) * p.scale;
+                    wf_splat(p, pix, opl, c);
+                    contribs++;
+                    if (DUMP) wf_dump(p, pix, smp, depth, 0, orig, opl, c);
+                }
+                if (depth == p.max_depth) {
+                    done = true;
+                } else {
+                    const float3 nn = cwo >= 0.f ? ng : -ng;
+                    float3 tb, bb;
+                    onb(nn, tb, bb);
+                    const float3 wol = to_local(wo, tb, bb, nn);
+                    const float4 mm = __ldg(&s.mats[orig]);
+                    const Mat mat{xyz(mm), mm.w};
+                    // next-event estimate: a shadow ray carrying its contribution
+                    if (s.n_units > 0) {
+                        const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_NEE), p.k0, p.k1);
+                        const int un = pick_unit_wf(s, R.x);
+                        const LightUnit U = s.units[un];
+                        const int em = __float_as_int(U.v2.w);
+                        const bool is_pt = __float_as_int(U.n.w) < 0;
+                        const float3 y = is_pt ? xyz(U.v0)
+                                               : tri_point(xyz(U.v0), xyz(U.v1), xyz(U.v2), u24(R.y), u24(R.z));
+                        const float3 xo = x + nn * eps_of(x);
+                        const float3 dl = y - xo;
+                        const float dist = sqrtf(dot(dl, dl));
+                        const float3 wi = dl * (1.0f / dist);
+                        const float cx = dot(nn, wi);
+                        const float cy = is_pt ? 1.0f : -dot(xyz(U.n), wi);
+                        if (cx > 0.f && cy > 0.f && dist > 0.f) {
+                            float3 f;
+                            float pb;
+                            bsdf_eval(mat, wol, to_local(wi, tb, bb, nn), f, pb);
+                            const float pick = U.v1.w;
+                            float geo, w = 1.0f;
+                            if (is_pt) geo = 1.0f / (dist * dist) / pick;
+                            else {
+                                const float pA = pick / U.v0.w;
+                                geo = cy / (dist * dist) / pA;
+                                w = mis2w(pA * dist * dist / cy, pb);
+                            }
+                            const float3 c = mul(mul(beta, f) * (cx * geo * w), xyz(s.em_rad[em])) * p.scale;
+                            if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
+                                shadow = true;
+                                sh_o = make_float4(xo.x, xo.y, xo.z, dist - (is_pt ? 0.0f : eps_of(y)));
+                                sh_d = make_float4(wi.x, wi.y, wi.z, opl + dist);
+                                sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
+                                sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                            }
+                        }
+                    }
+                    // continue by sampling the BSDF
+                    const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_SCATTER), p.k0, p.k1);
+                    float3 wil;
+                    if (bsdf_sample(mat, wol, u24(R.x), u24(R.y), wil)) {
+                        float3 f;
+                        float pb;
+                        bsdf_eval(mat, wol, wil, f, pb);
+                        if (pb > 0.f) {
+                            beta = mul(beta, f) * (wil.z / pb);
+                            const float3 no = x + nn * eps_of(x);
+                            const float3 nd = to_world(wil, tb, bb, nn);
+                            p.o[slot] = make_float4(no.x, no.y, no.z, opl);
+                            p.d[slot] = make_float4(nd.x, nd.y, nd.z, pb);
+                            p.beta[slot] = make_float4(beta.x, beta.y, beta.z, 0.f);
+                            p.meta[slot] = make_uint4(pix, smp, (uint32_t)(depth + 1), 0u);
+                            cont = true;
+                        }
+                    }
+                    if (!cont) done = true;
+                }
+            }
+        }
+        const uint32_t qs = wf_append(&p.counters[C_NEXT], cont);
+        if (cont) qnext[qs] = slot;
+        const uint32_t fs = wf_append(&p.counters[C_FREE], done);
+        if (done) p.free_q[fs] = slot;
+        const uint32_t ss = wf_append(&p.counters[C_SHADOW], shadow);
+        if (shadow) {
+            p.sh_o[ss] = sh_o;
+            p.sh_d[ss] = sh_d;
+            p.sh_c[ss] = sh_c;
+            p.sh_m[ss] = sh_m;
+        }
+        (void)valid;
+    }
+    warp_count(&s.counters[0], verts);
+    warp_count(&s.counters[2], contribs);
+}
+
+template <bool DUMP, bool CNT>
+__global__ void __launch_bounds__(256) k_wf_shadow(const DevScene s, const WfParams p) {
+    const uint32_t n = p.counters[C_SHADOW];
+    const int lane = threadIdx.x & 31;
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0, contribs = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&p.counters[C_SH_CUR], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i < n) {
+            const float4 o = p.sh_o[i], d = p.sh_d[i];
+            const RayT r = make_ray(s, xyz(o), xyz(d));
+            rays++;
+            if (!trace_any<CNT>(s, r, o.w, tc)) {
+                const float4 c = p.sh_c[i];
+                const uint32_t pix = (uint32_t)__float_as_int(c.w);
+                wf_splat(p, pix, d.w, xyz(c));
+                contribs++;
+                if (DUMP) {
+                    const uint4 m = p.sh_m[i];
+                    wf_dump(p, pix, m.x, (int)m.y, 1, (int)m.z, d.w, xyz(c));
+                }
+            }
+        }
+    }
+    warp_count(&s.counters[3], rays);
+    warp_count(&s.counters[2], contribs);
+    if (CNT) {
+        warp_count(&s.counters[4], tc.nodes);
+        warp_count(&s.counters[5], tc.tris);
+    }
+}
+
+__global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsigned long long *next_path) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) free_q[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < 8; ++k) counters[k] = 0;
+        counters[C_FREE] = P;
+        *next_path = 0ull;
+    }
+}
+
+}  // namespace
+
+mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms, bool dump, bool counters,
+                              cudaStream_t st) {
+    WfParams p = p0;
+    const int grid = num_sms * 8;
+    k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.free_q, p.P, p.counters,
+                                                                                    p.next_path);
+    MT_CUDA_TRY(cudaGetLastError());
+    uint32_t *qa = p.qa, *qb = p.qb;
+    // an upper bound on iterations: every path needs at most max_depth extension rays
+    const unsigned long long bound =
+        (p.total_paths + p.P - 1) / p.P * (unsigned long long)(p.max_depth + 1) + (unsigned long long)p.max_depth + 2;
+    for (unsigned long long iter = 0; iter < bound; ++iter) {
+        k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
+        k_wf_generate<<<grid, 256, 0, st>>>(s, p, p.iter, qa);
+        if (counters) k_wf_extend<true><<<grid, 256, 0, st>>>(s, p, qa);
+        else k_wf_extend<false><<<grid, 256, 0, st>>>(s, p, qa);
+        if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (dump) {
+            if (counters) k_wf_shadow<true, true><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<true, false><<<grid, 256, 0, st>>>(s, p);
+        } else {
+            if (counters) k_wf_shadow<false, true><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<false, false><<<grid, 256, 0, st>>>(s, p);
+        }
+        MT_CUDA_TRY(cudaGetLastError());
+        uint32_t *t = qa;
+        qa = qb;
+        qb = t;
+        // check for completion every few iterations (one small read-back)
+        if ((iter & 3) == 3 || iter + 1 == bound) {
+            uint32_t done = 0;
+            MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            MT_CUDA_TRY(cudaStreamSynchronize(st));
+            if (done) return MT_OK;
+        }
+    }
+    // one more setup decides whether anything is left
+    k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
+    uint32_t done = 0;
+    MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!done) {
+        mt::set_error("wavefront render did not drain its queues within the iteration bound");
+        return MT_ERR_INTERNAL;
+    }
+    return MT_OK;
+}

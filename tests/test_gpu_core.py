@@ -254,3 +254,44 @@ def test_invalid_arguments_give_status(api, cornell):
     with pytest.raises(api.MtError) as e:
         api.render(s, 64, 64, 256, 3.5, 0.01, 1, 1, 65)
     assert e.value.status == api.MT_ERR_INVALID_ARGUMENT
+
+
+@pytest.mark.parametrize("opts", ["wavefront", "megakernel_refill16"])
+def test_forward_forms_per_path_parity(api, cornell, opts):
+    """The wavefront form and the megakernel with deferred refill compute the
+    same contributions as the oracle on the same Philox stream."""
+    sc, s, osc = cornell
+    H = W = 64
+    T, start, width = 256, 3.5, 0.01
+    spp, seed, depth = 4, 77, 4
+    opt = api.MT_OPT_WAVEFRONT if opts == "wavefront" else api.MT_OPT_REFILL(16)
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, opt)
+    try:
+        film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=2_000_000)
+        f2, s2 = api.render(s, H, W, T, start, width, spp, seed, depth)
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
+    crop = (16, 48, 16, 48)
+    ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=2_000_000)
+    px, py = rec["pixel"] % W, rec["pixel"] // W
+    sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"])
+    assert nm > 3000 and div <= 1e-3 * nm and bad <= 1e-3 * nm and bin_bad == 0, (nm, div, bad, bin_bad)
+    g = f2.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+    assert rel_l2(g, ref["film"]) < 0.01
+    assert rel_l2(s2.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]], ref["steady"]) < 0.01
+    # the default form on the same samples gives the same film
+    f3, s3 = api.render(s, H, W, T, start, width, spp, seed, depth)
+    assert rel_l2(f2.cpu().numpy(), f3.cpu().numpy()) < 1e-4
+
+
+def test_wavefront_large_scene_matches_megakernel(api, scenes_mod):
+    sc = scenes_mod.diff_scene()
+    s = api.Scene(sc)
+    f = scenes_mod.DIFF_FILM
+    a, sa = api.render(s, 64, 64, f.T, f.start_opl, f.bin_width, 16, 3, 8)
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    b, sb = api.render(s, 64, 64, f.T, f.start_opl, f.bin_width, 16, 3, 8)
+    s.sync()
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-4
+    assert rel_l2(sb.cpu().numpy(), sa.cpu().numpy()) < 1e-4
