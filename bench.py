@@ -119,6 +119,20 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def aggregate_ranks(seconds, vertices, world_size, device):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    the path vertices all ranks traced (replicas: no data exchange)."""
+    if world_size <= 1:
+        return seconds, vertices
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([vertices], dtype=torch.float64, device=device)
+    dist.all_reduce(v)
+    return float(t.item()), float(v.item())
+
+
 def cpu_baseline(sc, film_spec, spp, depth, budget_s=15.0):
     """The oracle as it stands, single-threaded on this host, on a centred pixel
     crop of the same workload at full spp and depth (bounded to ~budget_s)."""
@@ -238,6 +252,7 @@ def main():
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     s.read_counters(reset=True)
+    launches0 = s.stats()["launches"]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -253,17 +268,9 @@ def main():
     clk = clocks.stop()
     s.sync()
     run_cnt = s.read_counters(reset=True)
+    launches = s.stats()["launches"] - launches0
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
-    total_s = sum(step_ms) / 1000.0
-    if ws > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        vt = torch.tensor([float(run_cnt["vertices"])], device="cuda")
-        torch.distributed.all_reduce(vt)
-        total_vertices = float(vt.item())
-    else:
-        total_vertices = float(run_cnt["vertices"])
+    total_s, total_vertices = aggregate_ranks(sum(step_ms) / 1000.0, float(run_cnt["vertices"]), ws, "cuda")
     value = total_vertices / total_s
     mean_ms = 1000.0 * total_s / args.steps
     peak, peak_kind = _peaks()
@@ -325,7 +332,7 @@ def main():
                                    "+ film and steady image written once",
                      "counts": cnt, "kernel_hash": khash, "aux": aux},
         "clocks": clk,
-        "gpu_launches": args.steps,
+        "gpu_launches": launches,
         "e2e": e2e,
         "step_ms": step_ms,
     }
@@ -546,6 +553,23 @@ def secondary(api, autotune, scenes):
     out["nlos"] = {"confocal_connections_per_s": 4096 * 1024 / (ms / 1000.0), "ms_per_capture": ms,
                    "workload": "64x64 confocal grid x 1024 spp, T=4096 x 0.003 m, 49.4k hidden triangles, "
                                "one graph launch"}
+    del nf
+    # exhaustive grid: 16x16 lasers x 64x64 sensors, 1024 hidden samples per laser shared by its sensors
+    las = torch.from_numpy(scenes.wall_grid(16, 16)).cuda()
+    sen = torch.from_numpy(scenes.wall_grid(64, 64)).cuda()
+    ef = (torch.empty((256 * 4096, scenes.NLOS_T), device="cuda"), torch.empty(256 * 4096, device="cuda"))
+    api.render_nlos(s, las, sen, api.MT_EXHAUSTIVE, scenes.NLOS_T, scenes.NLOS_START, scenes.NLOS_W, 1024, 1, out=ef)
+    s.sync()
+    e0.record()
+    api.render_nlos(s, las, sen, api.MT_EXHAUSTIVE, scenes.NLOS_T, scenes.NLOS_START, scenes.NLOS_W, 1024, 1, out=ef)
+    e1.record()
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    out["nlos"]["exhaustive_connections_per_s"] = 256 * 4096 * 1024 / (ms / 1000.0)
+    out["nlos"]["exhaustive_ms"] = ms
+    out["nlos"]["exhaustive_workload"] = ("16x16 lasers x 64x64 sensors x 1024 shared hidden samples per laser, "
+                                          "film 1,048,576 x 4096 (17.2 GB)")
+    del ef
     return out
 
 

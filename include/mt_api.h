@@ -168,6 +168,17 @@ mt_status mt_render(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, in
 mt_status mt_render_nlos(mt_scene scene, mt_film film, const mt_scan *scan, int32_t spp, uint64_t seed,
                          uint64_t sample_offset, void *stream);
 
+/* Frequency-space rendering (Sec. 4.3, Eq. 12): the paths of mt_render, each
+ * contribution C adding C * exp(-i * 2 pi * opl / lambda_k) for the K
+ * wavelengths d_lambdas (device float32 [K], metres; opl is the optical path
+ * length, so 1/lambda is the modulation frequency in 1/m).  The film must have
+ * T = 2K and C = 3 and is laid out [H][W][K][2][3]: the real RGB then the
+ * imaginary RGB per wavelength, times 1/spp (unnormalised with MT_ACCUMULATE);
+ * the film's start and width are ignored; the steady image is the usual one.
+ * Asynchronous; allocates nothing. */
+mt_status mt_render_phasor(mt_scene scene, mt_film film, const float *d_lambdas, int32_t K, int32_t spp,
+                           uint64_t seed, int32_t max_depth, uint64_t sample_offset, void *stream);
+
 /* Backward mode by path replay (Sec. 4.4, Eqs. 13-15): regenerate every path of
  * mt_render(scene, film, spp, seed, max_depth, sample_offset) from its Philox
  * key and add dL/dalbedo (device [n_tris][3]), dL/dradiance (device
@@ -190,10 +201,11 @@ mt_status mt_sync(mt_scene scene, void *stream);
  * Synchronises `stream`; reset != 0 zeroes them afterwards. */
 mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *stream);
 
-/* Scene statistics: out[0] n_tris, out[1] BVH internal nodes, out[2] BVH
- * depth, out[3] SAH cost x 1000 (sum of node areas / root area, with unit
- * traversal and intersection costs), out[4] light units, out[5] scene bytes
- * on the device, out[6] BVH build time in microseconds. */
+/* Scene statistics (out has 8 entries): out[0] n_tris, out[1] BVH internal
+ * nodes, out[2] BVH depth, out[3] SAH cost x 1000 (sum of node areas / root
+ * area, with unit traversal and intersection costs), out[4] light units,
+ * out[5] scene bytes on the device, out[6] BVH build time in microseconds,
+ * out[7] kernels launched by render calls on this scene so far. */
 mt_status mt_scene_stats(mt_scene scene, int64_t *out);
 
 /* Launch configuration used by the next launches of this scene (set by the

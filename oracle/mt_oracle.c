@@ -629,6 +629,7 @@ typedef struct {
     int backward;
     /* forward outputs (crop-relative) */
     double *film, *steady, *dropped;
+    double *phasor; const double *lambdas; int32_t K; /* frequency-space film (Sec. 4.3) */
     mo_contrib *dump; int64_t dump_cap, n_dump;
     /* backward inputs/outputs */
     const double *gfilm, *gsteady;
@@ -656,6 +657,15 @@ static void deposit(ctx_t *cx, int32_t pix_full, int32_t lp, int32_t sample, int
     int in = bin >= 0 && bin < a->T;
     cx->cnt[2]++;
     if (!cx->backward) {
+        /* frequency space (Sec. 4.3, Eq. 12): C * exp(-i * 2 pi * tof / lambda) per wavelength */
+        for (int32_t q = 0; q < cx->K; q++) {
+            double ph = 2.0 * PI_D * opl / cx->lambdas[q];
+            double cr = cos(ph), si = sin(ph);
+            for (int k = 0; k < 3; k++) {
+                cx->phasor[(((int64_t)lp * cx->K + q) * 2 + 0) * 3 + k] += c[k] * cr;
+                cx->phasor[(((int64_t)lp * cx->K + q) * 2 + 1) * 3 + k] -= c[k] * si;
+            }
+        }
         for (int k = 0; k < 3; k++) {
             if (in) cx->film[((int64_t)lp * a->T + bin) * 3 + k] += c[k];
             else if (cx->dropped) cx->dropped[(int64_t)lp * 3 + k] += c[k];
@@ -960,6 +970,36 @@ int mo_render(const mo_scene *s, const mo_args *a, double *film, double *steady,
     }
     if (n_dump) *n_dump = cx.n_dump;
     if (counters) for (int k = 0; k < 4; k++) counters[k] += cx.cnt[k];
+    return 0;
+}
+
+/* Frequency-space rendering (Sec. 4.3, Eq. 12): the same paths, each
+ * contribution adding C * exp(-i * 2 pi * tof / lambda_k) for K wavelengths
+ * (lambda in metres, tof as optical path length).  phasor is [px][K][2][3]
+ * (real RGB, imaginary RGB), normalised by 1/spp unless MO_ACCUMULATE. */
+int mo_render_phasor(const mo_scene *s, const mo_args *a0, const double *lambdas, int32_t K, double *phasor,
+                     double *steady) {
+    mo_args a = *a0;
+    a.T = 0; /* no time bins: every contribution goes to the phasors and the steady image */
+    ctx_t cx;
+    memset(&cx, 0, sizeof(cx));
+    double dummy = 0.0;
+    cx.s = s; cx.a = &a; cx.film = &dummy; cx.steady = steady;
+    cx.phasor = phasor; cx.lambdas = lambdas; cx.K = K;
+    int64_t npx = (int64_t)(a.x1 - a.x0) * (a.y1 - a.y0);
+    if (K < 1) return 1;
+    for (int32_t q = 0; q < K; q++) if (!(lambdas[q] > 0.0)) return 1;
+    if (!(a.flags & MO_ACCUMULATE)) {
+        memset(phasor, 0, sizeof(double) * (size_t)(npx * K * 6));
+        if (steady) memset(steady, 0, sizeof(double) * (size_t)(npx * 3));
+    }
+    int rc = run(&cx);
+    if (rc) return rc;
+    if (!(a.flags & MO_ACCUMULATE) && a.spp > 0) {
+        double inv = 1.0 / a.spp;
+        for (int64_t i = 0; i < npx * K * 6; i++) phasor[i] *= inv;
+        if (steady) for (int64_t i = 0; i < npx * 3; i++) steady[i] *= inv;
+    }
     return 0;
 }
 

@@ -20,6 +20,7 @@
  *   - transient volumetric path tracing with tof inside media (Sec. 4.1)
  *   - backward-mode gradients of a scalar loss (Sec. 4.4, Eqs. 13-15)
  *   - relay-wall NLOS impulse responses H(x_l, x_s, t) (Sec. 4.5)
+ *   - frequency-space (phasor) rendering, C * exp(-i 2 pi tof / lambda) (Sec. 4.3)
  * Where the paper is silent (estimator details, sampling maps, RNG layout)
  * the oracle follows the readings listed in the project's design notes; each
  * function below states the one it uses.
@@ -100,6 +101,8 @@ double mo_track(const mo_scene *s, const double *o, const double *d, double dist
 
 int mo_render(const mo_scene *s, const mo_args *a, double *film, double *steady, double *dropped,
               mo_contrib *dump, int64_t dump_cap, int64_t *n_dump, uint64_t *counters);
+int mo_render_phasor(const mo_scene *s, const mo_args *a, const double *lambdas, int32_t K, double *phasor,
+                     double *steady);
 int mo_render_backward(const mo_scene *s, const mo_args *a, const double *grad_film,
                        const double *grad_steady, double *grad_albedo, double *grad_radiance,
                        double *grad_medium_albedo);

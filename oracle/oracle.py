@@ -89,6 +89,8 @@ def lib():
         _lib.mo_track.argtypes = [P, P, P, C.c_double, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int]
         _lib.mo_render.restype = C.c_int
         _lib.mo_render.argtypes = [P, P, P, P, P, P, C.c_int64, P, P]
+        _lib.mo_render_phasor.restype = C.c_int
+        _lib.mo_render_phasor.argtypes = [P, P, P, C.c_int32, P, P]
         _lib.mo_render_backward.restype = C.c_int
         _lib.mo_render_backward.argtypes = [P, P, P, P, P, P, P]
         _lib.mo_render_nlos.restype = C.c_int
@@ -221,6 +223,19 @@ class OracleScene:
             out["n_dump"] = nd.value
         del npx
         return out
+
+    def render_phasor(self, H, W, lambdas, spp, seed, max_depth, flags=0, sample_offset=0, crop=None):
+        """Frequency-space film [h, w, K, 2 (re, im), 3] (Sec. 4.3) and the steady image."""
+        x0, x1, y0, y1 = crop if crop is not None else (0, W, 0, H)
+        lam = np.ascontiguousarray(lambdas, np.float64)
+        K = lam.shape[0]
+        ph = np.zeros((y1 - y0, x1 - x0, K, 2, 3), np.float64)
+        steady = np.zeros((y1 - y0, x1 - x0, 3), np.float64)
+        a = Args(H, W, 0, 0.0, 1.0, flags, spp, seed, max_depth, sample_offset, x0, x1, y0, y1, STRAT_MIS)
+        rc = lib().mo_render_phasor(self.h, C.byref(a), _p(lam), K, _p(ph), _p(steady))
+        if rc:
+            raise ValueError("oracle phasor: invalid arguments")
+        return dict(phasor=ph, steady=steady)
 
     def render_backward(self, H, W, T, start, width, spp, seed, max_depth, grad_film, grad_steady=None,
                         flags=0, sample_offset=0, crop=None):

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mt_render_dump": (C.c_int, [_P, _P, _P, _I32, _U64, _I32, _U64, _P, _I64, _P, _P]),
     "mt_render_nlos_noalloc": (C.c_int, [_P, _P, _P, _I32, _U64, _U64, _P]),
     "mt_microbench": (C.c_int, [_I32, _P, _I64, _I32, _P, _P]),
+    "mt_render_phasor": (C.c_int, [_P, _P, _P, _I32, _I32, _U64, _I32, _U64, _P]),
 }
 
 _lib = None
@@ -269,7 +270,8 @@ class Scene:
     def stats(self) -> dict:
         out = (C.c_int64 * 8)()
         mt_scene_stats(self.h, out)
-        keys = ["n_tris", "bvh_nodes", "bvh_depth", "sah_x1000", "light_units", "device_bytes", "build_us"]
+        keys = ["n_tris", "bvh_nodes", "bvh_depth", "sah_x1000", "light_units", "device_bytes", "build_us",
+                "launches"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def read_counters(self, reset=True, stream=None) -> dict:
@@ -317,6 +319,22 @@ def render(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_off
     f = Film(film, steady, start, width, flags)
     mt_render(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
     return film, steady
+
+
+def mt_render_phasor(scene, film, d_lambdas, K, spp, seed, max_depth, sample_offset, stream):
+    return _call("mt_render_phasor", scene, film, d_lambdas, K, spp, seed, max_depth, sample_offset, stream)
+
+
+def render_phasor(scene: Scene, H, W, lambdas, spp, seed, max_depth, sample_offset=0, flags=0, stream=None):
+    """Frequency-space film [H, W, K, 2 (re, im), 3] and the steady image [H, W, 3]."""
+    import torch
+    lam = torch.as_tensor(lambdas, dtype=torch.float32, device="cuda").contiguous()
+    K = lam.shape[0]
+    film = torch.empty((H, W, 2 * K, 3), dtype=torch.float32, device="cuda")
+    steady = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    f = Film(film, steady, 0.0, 1.0, flags)
+    mt_render_phasor(scene.h, f.h, _ptr(lam), K, spp, seed, max_depth, sample_offset, _stream(stream))
+    return film.view(H, W, K, 2, 3), steady
 
 
 def render_backward(scene: Scene, T, start, width, spp, seed, max_depth, grad_film, grad_steady=None,

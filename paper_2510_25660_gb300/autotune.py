@@ -111,8 +111,10 @@ def _candidates(kind, film_T):
     for threads in (128, 256):
         for tile in (1, 2):
             for priv in (-1, 0, film_T // 4, film_T // 2):
-                for opt in (0, 1):
+                for opt in (0, 1, 16 << 8):
                     out.append((threads, tile, 0, priv, opt))
+    if kind == "render":
+        out.append((256, 1, 0, 0, 4))  # wavefront form
     return out
 
 

@@ -91,6 +91,7 @@ struct mt_scene_s {
     GraphCache nlos_graph;
     cudaStream_t cap_stream = nullptr;  // private stream the NLOS graph is captured on
     // wavefront path pool
+    long long launches = 0;  // kernels launched by this scene's render calls
     uint32_t wf_cap = 0;
     float4 *wf_o = nullptr, *wf_d = nullptr, *wf_beta = nullptr, *wf_sh_o = nullptr, *wf_sh_d = nullptr,
            *wf_sh_c = nullptr;
@@ -678,13 +679,16 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
     }
-    return mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st);
+    long long n = 0;
+    const mt_status r = mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n);
+    s->launches += n + 1;
+    return r;
 }
 
 static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
                                uint64_t sample_offset, int mode, const float *gfilm, const float *gsteady,
                                float *galb, float *grad, float *gmed, mt_contrib *dump, int64_t cap,
-                               int64_t *dcount, cudaStream_t st) {
+                               int64_t *dcount, cudaStream_t st, const float *lambdas = nullptr, int32_t K = 0) {
     MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
     MT_CHECK_ARG(f->C == 3, "path-traced films have C = 3");
     MT_CHECK_ARG(spp >= 1, "spp must be >= 1");
@@ -730,13 +734,16 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     p.n_em_smem = n_em_smem;
     p.aggregate = (cfg.options & MT_OPT_AGGREGATE) ? 1 : 0;
     p.refill_min = std::max(1, std::min(32, (cfg.options >> 8) & 0xFF));
+    p.lambdas = lambdas;
+    p.K = K;
     if (mode != 2 && D < f->T && !acc) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
-    if (mode != 2 && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
+    if ((mode == 0 || mode == 1) && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
         return render_wavefront(s, f, p, cfg, mode == 1, st);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
+    s->launches += 1;
     return mt_launch_render(s->dev, p, cfg, mode, (f->flags & MT_COUNTERS) != 0, st);
 }
 
@@ -744,6 +751,15 @@ mt_status mt_render(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t m
                     void *stream) {
     return render_common(s, f, spp, seed, max_depth, sample_offset, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+mt_status mt_render_phasor(mt_scene s, mt_film f, const float *d_lambdas, int32_t K, int32_t spp, uint64_t seed,
+                           int32_t max_depth, uint64_t sample_offset, void *stream) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
+    MT_CHECK_ARG(d_lambdas != nullptr && K >= 1, "need K >= 1 wavelengths");
+    MT_CHECK_ARG(f->T == 2 * K && f->C == 3, "phasor films have T = 2K (real, imaginary) and C = 3");
+    return render_common(s, f, spp, seed, max_depth, sample_offset, 3, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, 0, nullptr, (cudaStream_t)stream, d_lambdas, K);
 }
 
 mt_status mt_render_backward(mt_scene s, mt_film f, const float *d_grad_film, const float *d_grad_steady, int32_t spp,
@@ -838,6 +854,7 @@ static mt_status nlos_enqueue(mt_scene s, mt_film f, const NlosParams &p, const 
         MT_CUDA_TRY(cudaMemsetAsync(p.film, 0, (size_t)f->H * f->W * f->T * sizeof(float), st));
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(p.dump_count, 0, sizeof(int64_t), st));
     MT_CUDA_TRY(cudaMemsetAsync(p.tile_counter, 0, sizeof(int), st));
+    s->launches += p.mode == MT_EXHAUSTIVE ? 2 : 1;
     return mt_launch_nlos(s->dev, p, cfg, dump, (f->flags & MT_COUNTERS) != 0, st);
 }
 
@@ -877,6 +894,7 @@ mt_status mt_render_nlos(mt_scene s, mt_film f, const mt_scan *scan, int32_t spp
         gc.key = key;
     }
     MT_CUDA_TRY(cudaGraphLaunch(gc.exec, st));
+    s->launches += scan->mode == MT_EXHAUSTIVE ? 2 : 1;
     return MT_OK;
 }
 
@@ -921,6 +939,7 @@ mt_status mt_scene_stats(mt_scene s, int64_t *out) {
     out[4] = s->dev.n_units;
     out[5] = (int64_t)s->bvh.n_nodes * 32 + s->n_tris * 48 + s->n_tris * 24;
     out[6] = (int64_t)llround(s->bvh.build_us);
+    out[7] = s->launches;
     return MT_OK;
 }
 

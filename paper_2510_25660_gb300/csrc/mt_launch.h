@@ -26,6 +26,8 @@ struct RenderParams {
     int32_t n_em_smem;         // emitters whose radiance gradients are summed in shared memory
     int32_t aggregate;         // warp-aggregated splats
     int32_t refill_min;        // idle lanes needed before a warp starts new paths (1..32)
+    const float *lambdas;      // frequency-space film: K wavelengths (m); the film has T = 2K
+    int32_t K;
 };
 
 struct NlosParams {
@@ -87,4 +89,4 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
 mt_status mt_launch_nlos(const DevScene &s, const NlosParams &p, const LaunchCfg &cfg, bool dump, bool counters,
                          cudaStream_t st);
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p, int num_sms, bool dump, bool counters,
-                              cudaStream_t st);
+                              cudaStream_t st, long long *launches);

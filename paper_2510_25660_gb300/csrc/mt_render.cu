@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2;
+constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2, MODE_PHASOR = 3;
 
 // CTAs of 256 threads the register allocation must leave room for per SM: 4
 // (64 registers) measured fastest on GB300 for the large scene (205 ms against
@@ -153,7 +153,26 @@ struct Tracer {
         c = c * p.scale;
         cb = cb * p.scale;
         cnt.contribs++;
-        if (MODE != MODE_BWD) {
+        if (MODE == MODE_PHASOR) {
+            // frequency space (Sec. 4.3, Eq. 12): C exp(-i 2 pi opl / lambda) per wavelength;
+            // "bin" 2q holds the real part, 2q + 1 the imaginary part
+            for (int q = 0; q < p.K; ++q) {
+                float sn, cs;
+                sincospif(2.0f * opl / __ldg(&p.lambdas[q]), &sn, &cs);
+                const float re[3] = {c.x * cs, c.y * cs, c.z * cs};
+                const float im[3] = {-c.x * sn, -c.y * sn, -c.z * sn};
+                if (2 * q + 1 < p.D) {
+                    splat_add<3, AGG>(hist + ((size_t)ps.lp * p.D + 2 * q) * 3, re);
+                    splat_add<3, AGG>(hist + ((size_t)ps.lp * p.D + 2 * q + 1) * 3, im);
+                } else {
+                    splat_add<3, AGG>(p.film + ((size_t)ps.pix * p.T + 2 * q) * 3, re);
+                    splat_add<3, AGG>(p.film + ((size_t)ps.pix * p.T + 2 * q + 1) * 3, im);
+                }
+            }
+            ps.acc = ps.acc + c;
+            (void)in;
+            (void)bin;
+        } else if (MODE != MODE_BWD) {
             if (in) {
                 const float cv[3] = {c.x, c.y, c.z};
                 if (bin < p.D) {
@@ -590,6 +609,7 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
     return counters ? launch_agg<M, false, true>(s, p, cfg, st) : launch_agg<M, false, false>(s, p, cfg, st);
     if (mode == 0) { MT_DISPATCH(MODE_FWD) }
     if (mode == 1) { MT_DISPATCH(MODE_DUMP) }
+    if (mode == 3) { MT_DISPATCH(MODE_PHASOR) }
     MT_DISPATCH(MODE_BWD)
 #undef MT_DISPATCH
 }

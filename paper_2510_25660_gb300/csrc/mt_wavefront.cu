@@ -357,7 +357,7 @@ __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsi
 }  // namespace
 
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms, bool dump, bool counters,
-                              cudaStream_t st) {
+                              cudaStream_t st, long long *launches) {
     WfParams p = p0;
     const int grid = num_sms * 8;
     k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.free_q, p.P, p.counters,
@@ -382,6 +382,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_shadow<false, false><<<grid, 256, 0, st>>>(s, p);
         }
         MT_CUDA_TRY(cudaGetLastError());
+        *launches += 5;
         uint32_t *t = qa;
         qa = qb;
         qb = t;
@@ -395,6 +396,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
     }
     // one more setup decides whether anything is left
     k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
+    *launches += 1;
     uint32_t done = 0;
     MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     MT_CUDA_TRY(cudaStreamSynchronize(st));

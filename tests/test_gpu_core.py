@@ -170,7 +170,7 @@ def test_cornell_per_path_contributions(api, cornell):
     px = rec["pixel"] % W
     py = rec["pixel"] // W
     sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
-    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"], start=start, width=width)
     assert nm > 3000
     assert div <= 1e-3 * nm, (div, nm)
     assert bad <= 1e-3 * nm, (bad, worst)
@@ -275,7 +275,7 @@ def test_forward_forms_per_path_parity(api, cornell, opts):
     ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=2_000_000)
     px, py = rec["pixel"] % W, rec["pixel"] // W
     sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
-    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"], start=start, width=width)
     assert nm > 3000 and div <= 1e-3 * nm and bad <= 1e-3 * nm and bin_bad == 0, (nm, div, bad, bin_bad)
     g = f2.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
     assert rel_l2(g, ref["film"]) < 0.01

@@ -28,7 +28,7 @@ def test_media_contributions_and_film(media):
     px = rec["pixel"] % W
     py = rec["pixel"] // W
     sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
-    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"], start=start, width=width)
     assert nm > 2000
     assert div <= 5e-3 * nm, (div, nm)
     assert bad <= 5e-3 * nm, (bad, worst)

@@ -39,7 +39,7 @@ def test_nlos_contributions_and_film(nlos, scenes_mod, mode):
     film, steady, rec, n = api.render_dump(s, 0, 0, T, start, width, spp, seed, 2, cap=4_000_000,
                                            scan_args=(L, S, m))
     ref = osc.render_nlos(lasers, sensors, m == api.MT_EXHAUSTIVE, T, start, width, spp, seed, dump_cap=4_000_000)
-    nm, div, worst, bad, bin_bad, _ = match_contribs(rec, ref["dump"])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec, ref["dump"], start=start, width=width)
     assert nm > 1000
     assert div <= 2e-3 * nm, (div, nm)
     assert bad <= 1e-3 * nm, (bad, worst)
