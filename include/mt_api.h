@@ -232,10 +232,14 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * separate kernels for camera rays, extension rays, shading and shadow rays,
  * each warp claiming rays of one kind from a queue; films are zeroed and
  * written with global atomics (tile, priv_bins and the refill option do not
- * apply); the call synchronises `stream` every few iterations. */
+ * apply); the call synchronises `stream` every few iterations.
+ * MT_OPT_DYNAMIC_FETCH (with MT_OPT_WAVEFRONT) = traversal lanes whose ray is
+ * done take the next queued ray instead of waiting for their warp, as soon as
+ * MT_OPT_REFILL(k) lanes of the warp are idle (k = 0: 8; k > 32: 32). */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
 #define MT_OPT_WAVEFRONT 4u
+#define MT_OPT_DYNAMIC_FETCH 8u
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1

@@ -27,7 +27,7 @@ MT_EMITTER_AREA, MT_EMITTER_POINT = 0, 1
 MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
 MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
 MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
-MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT = 1, 2, 4
+MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH = 1, 2, 4, 8
 
 
 def MT_OPT_REFILL(k):

@@ -75,6 +75,7 @@ struct WfParams {
     mt_contrib *dump;
     long long dump_cap;
     unsigned long long *dump_count;
+    int32_t dynamic_fetch;         // 0: off; else idle lanes of a warp that trigger a fetch (1..32)
 };
 
 struct LaunchCfg {

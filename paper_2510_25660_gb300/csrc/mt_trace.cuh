@@ -342,3 +342,89 @@ __device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, floa
     return trace_any_simple<CNT>(s, r, tmax, cnt);
 #endif
 }
+
+// ---------------------------------------------------------------------------
+// Traversal as a per-lane state machine, one node or leaf per call, for
+// kernels whose lanes fetch a new ray as soon as their current one is done
+// (persistent threads with dynamic ray fetch, Aila & Laine, HPG 2009).
+// ---------------------------------------------------------------------------
+struct TravState {
+    uint32_t ref;
+    int sp;
+    float tbest;
+    int best_k, best_id;
+};
+
+__device__ __forceinline__ void trav_init(TravState &ts, float tmax) {
+    ts.ref = 0;
+    ts.sp = 0;
+    ts.tbest = tmax;
+    ts.best_k = -1;
+    ts.best_id = 0x7fffffff;
+}
+
+// Advance by one node or one leaf; returns true when the traversal is over
+// (for ANY: also when a hit is found, signalled by best_k = 1).
+template <bool ANY, bool CNT>
+__device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, float tmax, TravState &ts, uint2 *st,
+                                          TraceCnt &cnt) {
+    if (!(ts.ref & 0x80000000u)) {
+        const uint4 a = __ldg(&s.nodes[2 * ts.ref]);
+        const uint4 b = __ldg(&s.nodes[2 * ts.ref + 1]);
+        if (CNT) cnt.nodes++;
+        float tn0, tf0, tn1, tf1;
+        slab(r, a.x, a.y, a.z, ts.tbest, tn0, tf0);
+        slab(r, a.w, b.x, b.y, ts.tbest, tn1, tf1);
+        const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
+        const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+        if (h0 && h1) {
+            const bool f0 = tn0 <= tn1;
+            if (ts.sp < MT_STACK) {
+                st[ts.sp] = make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0));
+                ++ts.sp;
+            } else {
+                raise_err(s, MT_EFLAG_STACK);
+            }
+            ts.ref = f0 ? b.z : b.w;
+            return false;
+        }
+        if (h0) {
+            ts.ref = b.z;
+            return false;
+        }
+        if (h1) {
+            ts.ref = b.w;
+            return false;
+        }
+    } else {
+        const int first = (int)(ts.ref & 0x1FFFFFFFu), n = (int)((ts.ref >> 29) & 3u) + 1;
+        for (int k = first; k < first + n; ++k) {
+            const float4 p0 = __ldg(&s.tris[3 * k]);
+            const float4 p1 = __ldg(&s.tris[3 * k + 1]);
+            const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+            if (CNT) cnt.tris++;
+            float t;
+            if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                if (ANY) {
+                    ts.best_k = 1;
+                    return true;
+                }
+                const int id = __float_as_int(p0.w);
+                if (t < ts.tbest || (t == ts.tbest && id < ts.best_id)) {
+                    ts.tbest = t;
+                    ts.best_k = k;
+                    ts.best_id = id;
+                }
+            }
+        }
+    }
+    while (ts.sp > 0) {
+        --ts.sp;
+        const uint2 e = st[ts.sp];
+        if (ANY || __uint_as_float(e.y) <= ts.tbest) {
+            ts.ref = e.x;
+            return false;
+        }
+    }
+    return true;
+}

@@ -174,6 +174,87 @@ __global__ void __launch_bounds__(256) k_wf_extend(const DevScene s, const WfPar
     }
 }
 
+// Extension and shadow rays with dynamic fetch: a lane whose ray is done
+// takes the next queue entry as soon as at least p.dynamic_fetch lanes of its
+// warp are idle, so a warp does not wait for its longest ray.  Between two
+// fetch decisions every busy lane advances MT_WF_STEPS nodes or leaves.
+#define MT_WF_STEPS 8
+
+template <bool SHADOW, bool CNT>
+__global__ void __launch_bounds__(256) k_wf_trace_dyn(const DevScene s, const WfParams p, const uint32_t *qcur) {
+    const uint32_t n = p.counters[SHADOW ? C_SHADOW : C_CUR];
+    uint32_t *cursor = &p.counters[SHADOW ? C_SH_CUR : C_EXT_CUR];
+    const int lane = threadIdx.x & 31;
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0, contribs = 0;
+    uint2 st[MT_STACK];
+    TravState ts;
+    RayT r;
+    float tmax = INFINITY;
+    uint32_t item = 0;
+    bool active = false, exhausted = false;
+    for (;;) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !active);
+        if (!exhausted && idle && (__popc(idle) >= p.dynamic_fetch || idle == 0xffffffffu)) {
+            const int leader = __ffs(idle) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(cursor, (uint32_t)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (base + __popc(idle) >= n) exhausted = true;
+            if (!active) {
+                const uint32_t i = base + __popc(idle & ((1u << lane) - 1u));
+                if (i < n) {
+                    item = SHADOW ? i : qcur[i];
+                    float4 o, d;
+                    if (SHADOW) {
+                        o = p.sh_o[i];
+                        d = p.sh_d[i];
+                        tmax = o.w;
+                    } else {
+                        o = p.o[item];
+                        d = p.d[item];
+                        tmax = INFINITY;
+                    }
+                    r = make_ray(s, xyz(o), xyz(d));
+                    trav_init(ts, tmax);
+                    active = true;
+                    rays++;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (active) {
+            for (int k = 0; k < MT_WF_STEPS; ++k) {
+                if (trav_step<SHADOW, CNT>(s, r, tmax, ts, st, tc)) {
+                    active = false;
+                    break;
+                }
+            }
+            if (!active) {
+                if (SHADOW) {
+                    if (ts.best_k < 0) {  // unoccluded: splat the carried contribution
+                        const float4 c = p.sh_c[item];
+                        const float4 d = p.sh_d[item];
+                        wf_splat(p, (uint32_t)__float_as_int(c.w), d.w, xyz(c));
+                        contribs++;
+                    }
+                } else {
+                    p.hit[item] = make_int4(ts.best_k, ts.best_id, __float_as_int(ts.tbest), 0);
+                }
+            }
+        }
+    }
+    warp_count(&s.counters[3], rays);
+    if (SHADOW) warp_count(&s.counters[2], contribs);
+    if (CNT) {
+        warp_count(&s.counters[4], tc.nodes);
+        warp_count(&s.counters[5], tc.tris);
+    }
+}
+
 template <bool DUMP>
 __global__ void __launch_bounds__(256) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
                                                   uint32_t *qnext) {
@@ -370,11 +451,20 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
     for (unsigned long long iter = 0; iter < bound; ++iter) {
         k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
         k_wf_generate<<<grid, 256, 0, st>>>(s, p, p.iter, qa);
-        if (counters) k_wf_extend<true><<<grid, 256, 0, st>>>(s, p, qa);
-        else k_wf_extend<false><<<grid, 256, 0, st>>>(s, p, qa);
+        const bool dyn = p.dynamic_fetch && !dump;
+        if (dyn) {
+            if (counters) k_wf_trace_dyn<false, true><<<grid, 256, 0, st>>>(s, p, qa);
+            else k_wf_trace_dyn<false, false><<<grid, 256, 0, st>>>(s, p, qa);
+        } else {
+            if (counters) k_wf_extend<true><<<grid, 256, 0, st>>>(s, p, qa);
+            else k_wf_extend<false><<<grid, 256, 0, st>>>(s, p, qa);
+        }
         if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
         else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
-        if (dump) {
+        if (dyn) {
+            if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
+            else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
+        } else if (dump) {
             if (counters) k_wf_shadow<true, true><<<grid, 256, 0, st>>>(s, p);
             else k_wf_shadow<true, false><<<grid, 256, 0, st>>>(s, p);
         } else {

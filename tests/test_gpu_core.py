@@ -256,15 +256,22 @@ def test_invalid_arguments_give_status(api, cornell):
     assert e.value.status == api.MT_ERR_INVALID_ARGUMENT
 
 
-@pytest.mark.parametrize("opts", ["wavefront", "megakernel_refill16"])
+def _form_options(api, opts):
+    return {"wavefront": api.MT_OPT_WAVEFRONT,
+            "wavefront_dynamic_fetch": api.MT_OPT_WAVEFRONT | api.MT_OPT_DYNAMIC_FETCH,
+            "megakernel_refill16": api.MT_OPT_REFILL(16)}[opts]
+
+
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_dynamic_fetch", "megakernel_refill16"])
 def test_forward_forms_per_path_parity(api, cornell, opts):
-    """The wavefront form and the megakernel with deferred refill compute the
-    same contributions as the oracle on the same Philox stream."""
+    """The wavefront form (with or without dynamic ray fetch in its traversal
+    kernels) and the megakernel with deferred refill compute the same
+    contributions as the oracle on the same Philox stream."""
     sc, s, osc = cornell
     H = W = 64
     T, start, width = 256, 3.5, 0.01
     spp, seed, depth = 4, 77, 4
-    opt = api.MT_OPT_WAVEFRONT if opts == "wavefront" else api.MT_OPT_REFILL(16)
+    opt = _form_options(api, opts)
     s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, opt)
     try:
         film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=2_000_000)
@@ -285,12 +292,13 @@ def test_forward_forms_per_path_parity(api, cornell, opts):
     assert rel_l2(f2.cpu().numpy(), f3.cpu().numpy()) < 1e-4
 
 
-def test_wavefront_large_scene_matches_megakernel(api, scenes_mod):
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_dynamic_fetch"])
+def test_wavefront_large_scene_matches_megakernel(api, scenes_mod, opts):
     sc = scenes_mod.diff_scene()
     s = api.Scene(sc)
     f = scenes_mod.DIFF_FILM
     a, sa = api.render(s, 64, 64, f.T, f.start_opl, f.bin_width, 16, 3, 8)
-    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, _form_options(api, opts))
     b, sb = api.render(s, 64, 64, f.T, f.start_opl, f.bin_width, 16, 3, 8)
     s.sync()
     assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-4
