@@ -247,7 +247,7 @@ def main():
     cnt = s.read_counters(reset=True)
     s.sync()
     film_bytes = film.numel() * 4 + steady.numel() * 4
-    alg_bytes = cnt["node_visits"] * 32 + cnt["tri_tests"] * 48 + cnt["vertices"] * 32 + film_bytes
+    alg_bytes = cnt["node_bytes"] + cnt["tri_tests"] * 48 + cnt["vertices"] * 32 + film_bytes
     # timed region
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]

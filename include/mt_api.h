@@ -196,7 +196,7 @@ mt_status mt_sync(mt_scene scene, void *stream);
 
 /* Counters accumulated by launches on this scene since the last reset:
  * out[0] path vertices, out[1] paths, out[2] contributions, out[3] rays,
- * out[4] node visits*, out[5] triangle tests*, out[6] splats into shared
+ * out[4] bytes of BVH nodes fetched*, out[5] triangle tests*, out[6] splats into shared
  * memory, out[7] splats into global memory (* only with MT_COUNTERS).
  * Synchronises `stream`; reset != 0 zeroes them afterwards. */
 mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *stream);
@@ -235,11 +235,15 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * apply); the call synchronises `stream` every few iterations.
  * MT_OPT_DYNAMIC_FETCH (with MT_OPT_WAVEFRONT) = traversal lanes whose ray is
  * done take the next queued ray instead of waiting for their warp, as soon as
- * MT_OPT_REFILL(k) lanes of the warp are idle (k = 0: 8; k > 32: 32). */
+ * MT_OPT_REFILL(k) lanes of the warp are idle (k = 0: 8; k > 32: 32).
+ * MT_OPT_WIDE_BVH (with MT_OPT_WAVEFRONT) = extension and shadow rays traverse
+ * the scene's 8-wide BVH (80-byte nodes, 8-bit child planes in a per-node
+ * frame) instead of the binary one; hits are the same. */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
 #define MT_OPT_WAVEFRONT 4u
 #define MT_OPT_DYNAMIC_FETCH 8u
+#define MT_OPT_WIDE_BVH 16u
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1
@@ -256,8 +260,9 @@ mt_status mt_probe_philox(uint64_t seed, const uint32_t *d_counters, int64_t n, 
 
 /* Closest hits of n rays (device float32 [n][6] = origin, unit direction) with
  * t in (0, tmax): device int32 [n] triangle index (-1 = miss, ties to the
- * smaller index) and device float32 [n] distance.  any_hit != 0 instead writes
- * 1/0 occlusion into d_tri. */
+ * smaller index) and device float32 [n] distance.  Bit 0 of any_hit set
+ * instead writes 1/0 occlusion into d_tri; bit 1 set traverses the 8-wide BVH
+ * (MT_OPT_WIDE_BVH) instead of the binary one; other bits are invalid. */
 mt_status mt_probe_trace(mt_scene scene, const float *d_rays, int64_t n, float tmax, int32_t any_hit,
                          int32_t *d_tri, float *d_t, void *stream);
 

@@ -27,7 +27,7 @@ MT_EMITTER_AREA, MT_EMITTER_POINT = 0, 1
 MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
 MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
 MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
-MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH = 1, 2, 4, 8
+MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH, MT_OPT_WIDE_BVH = 1, 2, 4, 8, 16
 
 
 def MT_OPT_REFILL(k):
@@ -277,7 +277,7 @@ class Scene:
     def read_counters(self, reset=True, stream=None) -> dict:
         out = (C.c_uint64 * 8)()
         mt_read_counters(self.h, out, int(reset), _stream(stream))
-        keys = ["vertices", "paths", "contributions", "rays", "node_visits", "tri_tests", "smem_splats", "gmem_splats"]
+        keys = ["vertices", "paths", "contributions", "rays", "node_bytes", "tri_tests", "smem_splats", "gmem_splats"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def sync(self, stream=None):
@@ -429,12 +429,14 @@ def probe_philox(seed, counters):
     return out
 
 
-def probe_trace(scene: Scene, rays, tmax=float("inf"), any_hit=False):
+def probe_trace(scene: Scene, rays, tmax=float("inf"), any_hit=False, wide=False):
+    """Closest (or any) hits of rays [n][6]; wide=True traverses the 8-wide BVH."""
     import torch
     n = rays.shape[0]
     tri = torch.empty(n, dtype=torch.int32, device="cuda")
     t = torch.empty(n, dtype=torch.float32, device="cuda")
-    mt_probe_trace(scene.h, _ptr(rays), n, float(tmax), int(any_hit), _ptr(tri), _ptr(t), _stream())
+    mode = (1 if any_hit else 0) | (2 if wide else 0)
+    mt_probe_trace(scene.h, _ptr(rays), n, float(tmax), mode, _ptr(tri), _ptr(t), _stream())
     return tri, t
 
 

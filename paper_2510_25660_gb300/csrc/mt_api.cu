@@ -262,12 +262,16 @@ __global__ void k_probe_trace(const DevScene s, const float *rays, long long n, 
         const float *r = rays + 6 * i;
         const RayT ray = make_ray(s, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]));
         TraceCnt c{0, 0};
-        if (any) {
-            tri[i] = trace_any<false>(s, ray, tmax, c) ? 1 : 0;
+        const bool wide = any & 2;
+        float t;
+        int orig;
+        if (any & 1) {
+            tri[i] = (wide ? trace_wide<true, false>(s, ray, tmax, t, orig, c) >= 0 : trace_any<false>(s, ray, tmax, c))
+                         ? 1
+                         : 0;
         } else {
-            float t;
-            int orig;
-            const int k = trace_closest<false>(s, ray, tmax, t, orig, c);
+            const int k = wide ? trace_wide<false, false>(s, ray, tmax, t, orig, c)
+                               : trace_closest<false>(s, ray, tmax, t, orig, c);
             tri[i] = k >= 0 ? orig : -1;
             if (tt) tt[i] = k >= 0 ? t : INFINITY;
         }
@@ -324,6 +328,7 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
     MT_TRY(mt_build_bvh(d_tris, (int32_t)n, st, al, &sc->bvh));
     DevScene &D = sc->dev;
     D.nodes = sc->bvh.nodes;
+    D.wnodes = sc->bvh.wnodes;
     D.tris = sc->bvh.tris;
     D.n_tris = (int32_t)n;
     D.n_em = n_em;
@@ -678,6 +683,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     // the refill field of the options word doubles as the fetch threshold
     const int fetch_k = (int)((cfg.options >> 8) & 0xFFu);
     w.dynamic_fetch = (cfg.options & MT_OPT_DYNAMIC_FETCH) ? (fetch_k ? std::min(fetch_k, 32) : 8) : 0;
+    w.wide = (cfg.options & MT_OPT_WIDE_BVH) ? 1 : 0;
     if (!(rp.flags & MT_ACCUMULATE)) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
@@ -940,7 +946,7 @@ mt_status mt_scene_stats(mt_scene s, int64_t *out) {
     out[2] = s->bvh.depth;
     out[3] = (int64_t)llround(s->bvh.sah * 1000.0);
     out[4] = s->dev.n_units;
-    out[5] = (int64_t)s->bvh.n_nodes * 32 + s->n_tris * 48 + s->n_tris * 24;
+    out[5] = (int64_t)s->bvh.n_nodes * 32 + (int64_t)s->bvh.n_wnodes * 80 + s->n_tris * 48 + s->n_tris * 24;
     out[6] = (int64_t)llround(s->bvh.build_us);
     out[7] = s->launches;
     return MT_OK;
@@ -953,7 +959,8 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     MT_CHECK_ARG(threads == 0 || (threads >= 32 && threads <= 256 && threads % 32 == 0), "threads must be 32..256, x32");
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
     MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
-    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | MT_OPT_WAVEFRONT | MT_OPT_DYNAMIC_FETCH | 0xFF00u)) == 0,
+    MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | MT_OPT_WAVEFRONT | MT_OPT_DYNAMIC_FETCH |
+                              MT_OPT_WIDE_BVH | 0xFF00u)) == 0,
                  "unknown launch options 0x%x", options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;
@@ -977,7 +984,8 @@ mt_status mt_probe_philox(uint64_t seed, const uint32_t *d_counters, int64_t n, 
 
 mt_status mt_probe_trace(mt_scene s, const float *d_rays, int64_t n, float tmax, int32_t any_hit, int32_t *d_tri,
                          float *d_t, void *stream) {
-    MT_CHECK_ARG(s != nullptr && d_rays != nullptr && d_tri != nullptr && n >= 0, "bad arguments");
+    MT_CHECK_ARG(s != nullptr && d_rays != nullptr && d_tri != nullptr && n >= 0 && (any_hit & ~3) == 0,
+                 "bad arguments");
     if (n == 0) return MT_OK;
     k_probe_trace<<<grid_for(n, 128, s->num_sms), 128, 0, (cudaStream_t)stream>>>(s->dev, d_rays, n, tmax, any_hit,
                                                                                  d_tri, d_t);

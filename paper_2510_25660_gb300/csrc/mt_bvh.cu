@@ -7,9 +7,14 @@
 // warp per node and partitioning stably per chunk.  Smaller nodes are built
 // completely by one CTA each with an explicit stack.  Leaves hold at most four
 // triangles; a node of two to four triangles becomes a leaf when that is
-// cheaper under the SAH.  The binary tree is then written as 32-byte nodes
-// holding both children's boxes as outward-rounded 16-bit planes, and the
-// triangles are reordered into leaf order as 48-byte records.
+// cheaper under the SAH.  The binary tree is then collapsed into an 8-wide
+// tree (each wide node takes a binary node's two children and keeps replacing
+// the internal child of largest surface area by its two children while it has
+// fewer than eight), the triangles are reordered so that the leaf children of
+// every wide node are contiguous, and both trees are written: binary nodes of
+// 32 bytes holding both children's boxes as outward-rounded 16-bit planes in
+// the scene box, wide nodes of 80 bytes with 8-bit planes in a per-node frame,
+// and 48-byte triangle records shared by the two.
 #include <cub/cub.cuh>
 
 #include <chrono>
@@ -598,6 +603,154 @@ __global__ void k_emit_root_leaf(const BNode *nodes, uint4 *out, float qlx, floa
     out[1] = make_uint4(0xFFFFu, 0xFFFFu, ref, MT_EMPTY_REF);
 }
 
+// One thread per wide node of the current level: collapse the binary subtree
+// below binary node wsrc[w] into up to eight children, give the children
+// slots by position, quantise their boxes, allocate the internal children
+// (wsrc of the next level) and the leaf triangles, record the new triangle
+// order in perm and point the binary leaves at it.
+__global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end, int *wsrc, uint4 *wnodes,
+                                int *wcount, int *perm, int e_min) {
+    for (int w = begin + blockIdx.x * blockDim.x + threadIdx.x; w < end; w += gridDim.x * blockDim.x) {
+        const int b = wsrc[w];
+        int ch[8];
+        int n = 0;
+        if (nodes[b].left < 0) {
+            ch[n++] = b;  // the root is a leaf
+        } else {
+            ch[n++] = nodes[b].left;
+            ch[n++] = nodes[b].right;
+        }
+        while (n < 8) {
+            int best = -1;
+            float ba = -1.0f;
+            for (int i = 0; i < n; ++i) {
+                const BNode &c = nodes[ch[i]];
+                if (c.left < 0) continue;
+                const float a = area_of(c.lo, c.hi);
+                if (a > ba) {
+                    ba = a;
+                    best = i;
+                }
+            }
+            if (best < 0) break;
+            const int c = ch[best];
+            ch[best] = nodes[c].left;
+            ch[n++] = nodes[c].right;
+        }
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double cc[8][3];
+        for (int i = 0; i < n; ++i) {
+            const BNode &c = nodes[ch[i]];
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fmin(lo[k], (double)c.lo[k]);
+                hi[k] = fmax(hi[k], (double)c.hi[k]);
+                cc[i][k] = 0.5 * ((double)c.lo[k] + (double)c.hi[k]);
+            }
+        }
+        // per-axis step 2^e >= extent / 250 (and >= 2^e_min); origin two steps below
+        int e[3];
+        double step[3];
+        float p[3];
+        for (int k = 0; k < 3; ++k) {
+            int ek = e_min;
+            while (ek < 127 && ldexp(250.0, ek) < hi[k] - lo[k]) ++ek;
+            e[k] = ek;
+            step[k] = ldexp(1.0, ek);
+            p[k] = (float)(lo[k] - 2.0 * step[k]);
+        }
+        // slots: greedily pair the child and corner whose centroid offset
+        // points most toward that corner
+        int slot_child[8];
+        for (int q = 0; q < 8; ++q) slot_child[q] = -1;
+        bool used[8] = {false, false, false, false, false, false, false, false};
+        for (int round = 0; round < n; ++round) {
+            double bestc = INFINITY;
+            int bi = -1, bq = -1;
+            for (int i = 0; i < n; ++i) {
+                if (used[i]) continue;
+                for (int q = 0; q < 8; ++q) {
+                    if (slot_child[q] >= 0) continue;
+                    double c = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double off = cc[i][k] - 0.5 * (lo[k] + hi[k]);
+                        c -= ((q >> k) & 1) ? off : -off;
+                    }
+                    if (c < bestc) {
+                        bestc = c;
+                        bi = i;
+                        bq = q;
+                    }
+                }
+            }
+            used[bi] = true;
+            slot_child[bq] = bi;
+        }
+        int n_int = 0, n_leaf_tris = 0;
+        for (int i = 0; i < n; ++i) {
+            if (nodes[ch[i]].left >= 0) ++n_int;
+            else n_leaf_tris += max(0, nodes[ch[i]].count);
+        }
+        const int base = n_int ? atomicAdd(&wcount[0], n_int) : 0;
+        const int tbase = n_leaf_tris ? atomicAdd(&wcount[1], n_leaf_tris) : 0;
+        uint32_t imask = 0, meta[2] = {0, 0}, ql[3][2] = {{0, 0}, {0, 0}, {0, 0}}, qh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        int r_int = 0, off = 0;
+        for (int q = 0; q < 8; ++q) {
+            const int sh = 8 * (q & 3), h = q >> 2;
+            if (slot_child[q] < 0) {
+                for (int k = 0; k < 3; ++k) ql[k][h] |= 255u << sh;
+                continue;
+            }
+            const int c = ch[slot_child[q]];
+            BNode &cn = nodes[c];
+            if (cn.left < 0 && cn.count <= 0) {  // an empty leaf stays an empty slot
+                for (int k = 0; k < 3; ++k) ql[k][h] |= 255u << sh;
+                continue;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double a = floor(((double)cn.lo[k] - (double)p[k]) / step[k]) - 2.0;
+                double z = ceil(((double)cn.hi[k] - (double)p[k]) / step[k]) + 2.0;
+                a = a < 0.0 ? 0.0 : a;
+                z = z > 255.0 ? 255.0 : z;  // unreachable: extent / step <= 250
+                ql[k][h] |= (uint32_t)a << sh;
+                qh[k][h] |= (uint32_t)z << sh;
+            }
+            if (cn.left >= 0) {
+                imask |= 1u << q;
+                wsrc[base + r_int++] = c;
+            } else {
+                meta[h] |= (0x80u | ((uint32_t)(cn.count - 1) << 5) | (uint32_t)off) << sh;
+                for (int j = 0; j < cn.count; ++j) perm[tbase + off + j] = idx[cn.first + j];
+                cn.first = tbase + off;
+                off += cn.count;
+            }
+        }
+        uint4 *o = wnodes + MT_WIDE_WORDS * (size_t)w;
+        o[0] = make_uint4(__float_as_uint(p[0]), __float_as_uint(p[1]), __float_as_uint(p[2]),
+                          (uint32_t)(e[0] + 127) | ((uint32_t)(e[1] + 127) << 8) | ((uint32_t)(e[2] + 127) << 16) |
+                              (imask << 24));
+        o[1] = make_uint4((uint32_t)base, (uint32_t)tbase, meta[0], meta[1]);
+        o[2] = make_uint4(ql[0][0], ql[0][1], ql[1][0], ql[1][1]);
+        o[3] = make_uint4(ql[2][0], ql[2][1], qh[0][0], qh[0][1]);
+        o[4] = make_uint4(qh[1][0], qh[1][1], qh[2][0], qh[2][1]);
+    }
+}
+
+// every internal child index in range, leaf triangles inside [0, n)
+__global__ void k_wide_validate(const uint4 *w, int nw, int n, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
+        const uint4 a = w[MT_WIDE_WORDS * (size_t)i], b = w[MT_WIDE_WORDS * (size_t)i + 1];
+        const uint32_t imask = a.w >> 24;
+        if (imask && ((uint64_t)b.x + __popc(imask) > (uint64_t)nw || b.x == 0u)) atomicOr(bad, 4);
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t m = ((q < 4 ? b.z : b.w) >> (8 * (q & 3))) & 0xFFu;
+            if (!(imask >> q & 1u) && (m & 0x80u)) {
+                const uint64_t last = (uint64_t)b.y + (m & 31u) + ((m >> 5) & 3u);
+                if (last >= (uint64_t)n) atomicOr(bad, 8);
+            }
+        }
+    }
+}
+
 __global__ void k_reorder(const float *tris, const int *idx, int n, float4 *out) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int p = idx[k];
@@ -786,6 +939,61 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
         const double e = std::max(std::max(ext[k], 1e-4 * mx), 1e-12) * (1.0 + 1.0 / 1024.0);
         out->q_scale[k] = (float)(e / 65529.0);
         out->q_lo[k] = (float)((double)box[k] - 3.0 * (double)out->q_scale[k]);
+    }
+
+    // 8-wide tree, level by level; the leaves' triangle ranges move to the
+    // wide order (perm) before the binary nodes are written
+    {
+        int *wsrc, *wcount, *perm, *dbad;
+        uint4 *wtmp;
+        const int max_w = std::max(1, n_build);
+        MT_TRY(tmpal.alloc(&wsrc, max_w, "wide bvh sources"));
+        MT_TRY(tmpal.alloc(&wtmp, (size_t)MT_WIDE_WORDS * max_w, "wide bvh nodes"));
+        MT_TRY(tmpal.alloc(&wcount, 2, "wide bvh counters"));
+        MT_TRY(tmpal.alloc(&perm, n, "wide bvh order"));
+        MT_TRY(tmpal.alloc(&dbad, 1, "wide bvh check"));
+        const int hw[2] = {1, 0}, zero = 0;
+        MT_CUDA_TRY(cudaMemcpyAsync(wcount, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(wsrc, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        // smallest step: 2^-16 of the largest scene extent, far above the
+        // rounding of the slab distances
+        double mxe = 0.0;
+        for (int k = 0; k < 3; ++k) mxe = std::max(mxe, (double)box[3 + k] - (double)box[k]);
+        int e_min = -126;
+        if (mxe > 0.0) e_min = std::max(-126, (int)std::ceil(std::log2(mxe)) - 16);
+        int begin = 0, end = 1, levels = 0, hcount[2] = {1, 0};
+        while (begin < end) {
+            const int nl = end - begin;
+            k_wide_collapse<<<std::min(4096, (nl + 127) / 128), 128, 0, st>>>(nodes, idx, begin, end, wsrc, wtmp,
+                                                                              wcount, perm, e_min);
+            MT_CUDA_TRY(cudaGetLastError());
+            MT_CUDA_TRY(cudaMemcpyAsync(hcount, wcount, sizeof(hcount), cudaMemcpyDeviceToHost, st));
+            MT_CUDA_TRY(cudaStreamSynchronize(st));
+            begin = end;
+            end = hcount[0];
+            if (++levels > MT_STACK || end > max_w) {
+                mt::set_error("wide BVH collapse did not terminate (%d levels, %d nodes)", levels, end);
+                return MT_ERR_INTERNAL;
+            }
+        }
+        if (hcount[1] != n) {
+            mt::set_error("wide BVH holds %d of %d triangles", hcount[1], n);
+            return MT_ERR_INTERNAL;
+        }
+        out->n_wnodes = end;
+        MT_TRY(al.alloc(&out->wnodes, (size_t)MT_WIDE_WORDS * end, "wide bvh nodes"));
+        MT_CUDA_TRY(cudaMemcpyAsync(out->wnodes, wtmp, (size_t)MT_WIDE_WORDS * end * sizeof(uint4),
+                                    cudaMemcpyDeviceToDevice, st));
+        MT_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), st));
+        k_wide_validate<<<std::min(1024, (end + 255) / 256), 256, 0, st>>>(out->wnodes, end, n, dbad);
+        int hbad = 0;
+        MT_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad) {
+            mt::set_error("wide BVH validation failed (flags %d)", hbad);
+            return MT_ERR_INTERNAL;
+        }
+        std::swap(idx, perm);  // perm is freed with the other temporaries
     }
 
     // internal nodes -> dense compact nodes

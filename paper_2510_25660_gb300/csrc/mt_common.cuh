@@ -206,6 +206,7 @@ struct LightUnit {
 
 struct DevScene {
     const uint4 *nodes;    // 2 x uint4 per internal node
+    const uint4 *wnodes;   // 5 x uint4 per 8-wide node (root = node 0)
     const float4 *tris;    // 3 x float4 per leaf-ordered triangle, v0.w = original index
     const float4 *mats;    // per original triangle: albedo, w = GGX roughness or -1 (Lambert)
     const int32_t *tri_unit; // per original triangle: light unit or -1

@@ -61,6 +61,8 @@ struct AllocList {
 // BVH build products (device pointers owned by the caller's AllocList)
 struct BvhResult {
     uint4 *nodes = nullptr;     // 2 per internal node
+    uint4 *wnodes = nullptr;    // 5 per 8-wide node
+    int32_t n_wnodes = 0;
     float4 *tris = nullptr;     // 3 per triangle, leaf order
     int32_t n_nodes = 0;
     int32_t depth = 0;

@@ -76,6 +76,7 @@ struct WfParams {
     long long dump_cap;
     unsigned long long *dump_count;
     int32_t dynamic_fetch;         // 0: off; else idle lanes of a warp that trigger a fetch (1..32)
+    int32_t wide;                  // traverse the 8-wide BVH
 };
 
 struct LaunchCfg {

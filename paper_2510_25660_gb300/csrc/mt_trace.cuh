@@ -22,6 +22,8 @@
 struct RayT {
     float3 o, d;
     float3 sa, sb;   // slab: t = (2^23 + q) * sa + sb for a quantised plane q
+    float3 inv;      // 1 / direction (zero components replaced by +-1e-20)
+    uint32_t oct;    // bit k set: direction component k is negative
     uint32_t sel_n[3];  // byte-permute selector of the near plane per axis (far = near ^ 0x22)
     int kx, ky, kz;  // watertight test axes (Woop, Benthin, Wald, JCGT 2013)
     float Sx, Sy, Sz;
@@ -38,6 +40,8 @@ __device__ __forceinline__ RayT make_ray(const DevScene &s, float3 o, float3 d) 
     const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
     const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
     const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
+    r.inv = f3(ix, iy, iz);
+    r.oct = (dx < 0.0f ? 1u : 0u) | (dy < 0.0f ? 2u : 0u) | (dz < 0.0f ? 4u : 0u);
     r.sa = f3(s.q_scale.x * ix, s.q_scale.y * iy, s.q_scale.z * iz);
     // the 2^23 offset of the exponent trick below is folded into sb; the two
     // 2^23 * sa terms cancel exactly inside the FMA, leaving one rounding of sb
@@ -108,7 +112,7 @@ __device__ __forceinline__ bool tri_hit(const RayT &r, float3 v0, float3 v1, flo
 }
 
 struct TraceCnt {
-    uint32_t nodes, tris;
+    uint32_t nodes, tris;  // bytes of BVH nodes fetched, triangle records tested
 };
 
 // Closest hit with t in (0, tmax); ties in t go to the smaller original index.
@@ -125,7 +129,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
         if (!(ref & 0x80000000u)) {
             const uint4 a = __ldg(&s.nodes[2 * ref]);
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
-            if (CNT) cnt.nodes++;
+            if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
             slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
@@ -189,7 +193,7 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
         if (!(ref & 0x80000000u)) {
             const uint4 a = __ldg(&s.nodes[2 * ref]);
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
-            if (CNT) cnt.nodes++;
+            if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
             slab(r, a.w, b.x, b.y, tmax, tn1, tf1);
@@ -251,7 +255,7 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
         while (ref != MT_DONE && !MT_IS_LEAF(ref)) {
             const uint4 a = __ldg(&s.nodes[2 * ref]);
             const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
-            if (CNT) cnt.nodes++;
+            if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
             slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
@@ -371,7 +375,7 @@ __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, floa
     if (!(ts.ref & 0x80000000u)) {
         const uint4 a = __ldg(&s.nodes[2 * ts.ref]);
         const uint4 b = __ldg(&s.nodes[2 * ts.ref + 1]);
-        if (CNT) cnt.nodes++;
+        if (CNT) cnt.nodes += 32;
         float tn0, tf0, tn1, tf1;
         slab(r, a.x, a.y, a.z, ts.tbest, tn0, tf0);
         slab(r, a.w, b.x, b.y, ts.tbest, tn1, tf1);
@@ -427,4 +431,137 @@ __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, floa
         }
     }
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// 8-wide BVH with compressed child boxes (after Ylitie, Karras and Laine,
+// "Efficient incoherent ray traversal on GPUs through compressed wide BVHs",
+// HPG 2017; the node layout below is this library's own).
+//
+// Node = 80 bytes = five uint4:
+//   w0.xyz  frame origin p (float), w0.w = ex | ey << 8 | ez << 16 | imask << 24
+//           (biased float exponents of the per-axis step 2^e; imask bit i set:
+//           child slot i is an internal node)
+//   w1.x    index of the first internal child; the internal child in slot i
+//           is w1.x + popc(imask & ((1 << i) - 1))
+//   w1.y    first triangle of this node's leaf children
+//   w1.z/w  one meta byte per slot (slots 0-3 / 4-7): a leaf child has
+//           0x80 | (count - 1) << 5 | offset, triangles w1.y + offset ...
+//   w2.xy qlo_x[8]  w2.zw qlo_y[8]  w3.xy qlo_z[8]  w3.zw qhi_x[8]
+//   w4.xy qhi_y[8]  w4.zw qhi_z[8]   (one byte per slot, little-endian)
+// A plane is p + q * 2^e, rounded outward by two steps; an empty slot has
+// lower planes 255 and upper planes 0 and is never hit.  Slot bit k of a child
+// says it lies on the upper side of the node along axis k, so visiting slots
+// in increasing order of slot ^ oct(ray) is roughly front to back.
+// ---------------------------------------------------------------------------
+#define MT_WIDE_WORDS 5
+
+// reorder the bits of an 8-bit mask so that bit k holds bit (k ^ m)
+__device__ __forceinline__ uint32_t perm_xor8(uint32_t x, uint32_t m) {
+    if (m & 1u) x = ((x & 0x55u) << 1) | ((x >> 1) & 0x55u);
+    if (m & 2u) x = ((x & 0x33u) << 2) | ((x >> 2) & 0x33u);
+    if (m & 4u) x = ((x & 0x0Fu) << 4) | ((x >> 4) & 0x0Fu);
+    return x;
+}
+
+// byte i of the 8-byte pair (lo, hi) as the float 2^23 + q
+__device__ __forceinline__ float q8(uint32_t lo, uint32_t hi, int i) {
+    return __int_as_float(__byte_perm(i < 4 ? lo : hi, 0x4B000000u, 0x7440u | (uint32_t)(i & 3)));
+}
+
+// Hit mask of the eight child boxes of node w0..w4 against (0, tmax].
+__device__ __forceinline__ uint32_t wide_hits(const RayT &r, const uint4 &w0, const uint4 &w2, const uint4 &w3,
+                                              const uint4 &w4, float tmax) {
+    // per-axis frame: t = (2^23 + q) * a + b with the 2^23 offset folded into b
+    const float ax = __int_as_float((int)((w0.w & 0xFFu) << 23)) * r.inv.x;
+    const float ay = __int_as_float((int)(((w0.w >> 8) & 0xFFu) << 23)) * r.inv.y;
+    const float az = __int_as_float((int)(((w0.w >> 16) & 0xFFu) << 23)) * r.inv.z;
+    const float bx = fmaf(-8388608.0f, ax, (__uint_as_float(w0.x) - r.o.x) * r.inv.x);
+    const float by = fmaf(-8388608.0f, ay, (__uint_as_float(w0.y) - r.o.y) * r.inv.y);
+    const float bz = fmaf(-8388608.0f, az, (__uint_as_float(w0.z) - r.o.z) * r.inv.z);
+    // near planes: the lower ones for a positive direction component
+    const bool nx = r.oct & 1u, ny = r.oct & 2u, nz = r.oct & 4u;
+    const uint32_t nx0 = nx ? w3.z : w2.x, nx1 = nx ? w3.w : w2.y, fx0 = nx ? w2.x : w3.z, fx1 = nx ? w2.y : w3.w;
+    const uint32_t ny0 = ny ? w4.x : w2.z, ny1 = ny ? w4.y : w2.w, fy0 = ny ? w2.z : w4.x, fy1 = ny ? w2.w : w4.y;
+    const uint32_t nz0 = nz ? w4.z : w3.x, nz1 = nz ? w4.w : w3.y, fz0 = nz ? w3.x : w4.z, fz1 = nz ? w3.y : w4.w;
+    uint32_t hits = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float tnx = fmaf(q8(nx0, nx1, i), ax, bx), tfx = fmaf(q8(fx0, fx1, i), ax, bx);
+        const float tny = fmaf(q8(ny0, ny1, i), ay, by), tfy = fmaf(q8(fy0, fy1, i), ay, by);
+        const float tnz = fmaf(q8(nz0, nz1, i), az, bz), tfz = fmaf(q8(fz0, fz1, i), az, bz);
+        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
+        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+        hits |= (tn <= tf ? 1u : 0u) << i;
+    }
+    return hits;
+}
+
+// Closest hit (ANY = false: returns the triangle index or -1, writes t and the
+// original index; ties in t go to the smaller original index) or any hit
+// (ANY = true: returns 1 on a hit, else -1) with t in (0, tmax).
+template <bool ANY, bool CNT>
+__device__ __forceinline__ int trace_wide(const DevScene &s, const RayT &r, float tmax, float &t_out, int &orig_out,
+                                          TraceCnt &cnt) {
+    float tbest = tmax;
+    int best_k = -1, best_id = 0x7fffffff;
+    uint2 st[MT_STACK];  // (first internal child, imask << 8 | remaining visit-order mask)
+    int sp = 0;
+    uint32_t node = 0;
+    for (;;) {
+        const uint4 *np = s.wnodes + MT_WIDE_WORDS * (size_t)node;
+        const uint4 w0 = __ldg(np), w1 = __ldg(np + 1), w2 = __ldg(np + 2), w3 = __ldg(np + 3), w4 = __ldg(np + 4);
+        if (CNT) cnt.nodes += 80;
+        const uint32_t hits = wide_hits(r, w0, w2, w3, w4, tbest);
+        const uint32_t imask = w0.w >> 24;
+        uint32_t leaves = hits & ~imask;
+        while (leaves) {
+            const int slot = __ffs(leaves) - 1;
+            leaves &= leaves - 1u;
+            const uint32_t meta = ((slot < 4 ? w1.z : w1.w) >> (8 * (slot & 3))) & 0xFFu;
+            const int first = (int)w1.y + (int)(meta & 31u), last = first + (int)((meta >> 5) & 3u);
+            for (int k = first; k <= last; ++k) {
+                const float4 p0 = __ldg(&s.tris[3 * k]);
+                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
+                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                if (CNT) cnt.tris++;
+                float t;
+                if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                    if (ANY) return 1;
+                    const int id = __float_as_int(p0.w);
+                    if (t < tbest || (t == tbest && id < best_id)) {
+                        tbest = t;
+                        best_k = k;
+                        best_id = id;
+                    }
+                }
+            }
+        }
+        uint32_t order = perm_xor8(hits & imask, r.oct);
+        uint32_t base = w1.x, im = imask;
+        if (!order) {
+            // pop the next group that still has children to visit
+            if (sp == 0) break;
+            const uint2 g = st[sp - 1];
+            base = g.x;
+            im = g.y >> 8;
+            order = g.y & 0xFFu;
+            --sp;
+        }
+        const int k = __ffs(order) - 1;
+        order &= order - 1u;
+        const uint32_t slot = (uint32_t)k ^ r.oct;
+        node = base + __popc(im & ((1u << slot) - 1u));
+        if (order) {
+            if (sp < MT_STACK) {
+                st[sp] = make_uint2(base, (im << 8) | order);
+                ++sp;
+            } else {
+                raise_err(s, MT_EFLAG_STACK);
+            }
+        }
+    }
+    t_out = tbest;
+    orig_out = best_id;
+    return best_k;
 }

@@ -144,8 +144,16 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
     warp_count(&s.counters[1], paths);
 }
 
-template <bool CNT>
-__global__ void __launch_bounds__(256) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
+// Resident CTAs per SM the traversal stages are compiled for (6 x 256 threads
+// caps them at 40 registers; the few spilled values cost less than the
+// occupancy they buy: measured 98 ms against 107 ms at 53 registers and 4 CTAs
+// per SM for the 512x512x256-spp forward render of the 1.16M-triangle scene).
+#ifndef MT_WF_TRACE_MINB
+#define MT_WF_TRACE_MINB 6
+#endif
+
+template <bool WIDE, bool CNT>
+__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
     const uint32_t n = p.counters[C_CUR];
     const int lane = threadIdx.x & 31;
     TraceCnt tc{0, 0};
@@ -162,7 +170,8 @@ __global__ void __launch_bounds__(256) k_wf_extend(const DevScene s, const WfPar
             const RayT r = make_ray(s, xyz(o), xyz(d));
             float t;
             int orig;
-            const int k = trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
+            const int k = WIDE ? trace_wide<false, CNT>(s, r, INFINITY, t, orig, tc)
+                               : trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
             p.hit[slot] = make_int4(k, orig, __float_as_int(t), 0);
             rays++;
         }
@@ -255,8 +264,13 @@ __global__ void __launch_bounds__(256) k_wf_trace_dyn(const DevScene s, const Wf
     }
 }
 
+// the shading stage at 3 CTAs per SM (80 registers, no spills)
+#ifndef MT_WF_SHADE_MINB
+#define MT_WF_SHADE_MINB 3
+#endif
+
 template <bool DUMP>
-__global__ void __launch_bounds__(256) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
+__global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
                                                   uint32_t *qnext) {
     const uint32_t n = p.counters[C_CUR];
     uint32_t verts = 0, contribs = 0;
@@ -390,8 +404,8 @@ __global__ void __launch_bounds__(256) k_wf_shade(const DevScene s, const WfPara
     warp_count(&s.counters[2], contribs);
 }
 
-template <bool DUMP, bool CNT>
-__global__ void __launch_bounds__(256) k_wf_shadow(const DevScene s, const WfParams p) {
+template <bool DUMP, bool CNT, bool WIDE>
+__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevScene s, const WfParams p) {
     const uint32_t n = p.counters[C_SHADOW];
     const int lane = threadIdx.x & 31;
     TraceCnt tc{0, 0};
@@ -406,7 +420,11 @@ __global__ void __launch_bounds__(256) k_wf_shadow(const DevScene s, const WfPar
             const float4 o = p.sh_o[i], d = p.sh_d[i];
             const RayT r = make_ray(s, xyz(o), xyz(d));
             rays++;
-            if (!trace_any<CNT>(s, r, o.w, tc)) {
+            float t_unused;
+            int id_unused;
+            const bool occluded = WIDE ? trace_wide<true, CNT>(s, r, o.w, t_unused, id_unused, tc) >= 0
+                                       : trace_any<CNT>(s, r, o.w, tc);
+            if (!occluded) {
                 const float4 c = p.sh_c[i];
                 const uint32_t pix = (uint32_t)__float_as_int(c.w);
                 wf_splat(p, pix, d.w, xyz(c));
@@ -455,21 +473,32 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (dyn) {
             if (counters) k_wf_trace_dyn<false, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<false, false><<<grid, 256, 0, st>>>(s, p, qa);
+        } else if (p.wide) {
+            if (counters) k_wf_extend<true, true><<<grid, 256, 0, st>>>(s, p, qa);
+            else k_wf_extend<true, false><<<grid, 256, 0, st>>>(s, p, qa);
         } else {
-            if (counters) k_wf_extend<true><<<grid, 256, 0, st>>>(s, p, qa);
-            else k_wf_extend<false><<<grid, 256, 0, st>>>(s, p, qa);
+            if (counters) k_wf_extend<false, true><<<grid, 256, 0, st>>>(s, p, qa);
+            else k_wf_extend<false, false><<<grid, 256, 0, st>>>(s, p, qa);
         }
         if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
         else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
+        } else if (p.wide) {
+            if (dump) {
+                if (counters) k_wf_shadow<true, true, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<true, false, true><<<grid, 256, 0, st>>>(s, p);
+            } else {
+                if (counters) k_wf_shadow<false, true, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, true><<<grid, 256, 0, st>>>(s, p);
+            }
         } else if (dump) {
-            if (counters) k_wf_shadow<true, true><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<true, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<true, true, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<true, false, false><<<grid, 256, 0, st>>>(s, p);
         } else {
-            if (counters) k_wf_shadow<false, true><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<false, true, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<false, false, false><<<grid, 256, 0, st>>>(s, p);
         }
         MT_CUDA_TRY(cudaGetLastError());
         *launches += 5;

@@ -68,8 +68,9 @@ def _exact_hits(tris, o, d):
     return np.where(hit, t, np.inf), bmin, t
 
 
+@pytest.mark.parametrize("wide", [False, True], ids=["binary", "wide"])
 @pytest.mark.parametrize("seed,n_tris", [(1, 7), (2, 64), (3, 200), (4, 1500)])
-def test_closest_hit_ids_bit_exact(api, scenes_mod, seed, n_tris):
+def test_closest_hit_ids_bit_exact(api, scenes_mod, seed, n_tris, wide):
     import torch
     tris = scenes_mod.random_mesh(seed, n_tris)
     sc = scenes_mod.Scene(tris, np.full((n_tris, 3), 0.5, np.float32), np.zeros(n_tris, np.float32),
@@ -77,8 +78,8 @@ def test_closest_hit_ids_bit_exact(api, scenes_mod, seed, n_tris):
     s = api.Scene(sc)
     o, d = scenes_mod.random_rays(seed + 100, 4000)
     rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
-    tri, t = api.probe_trace(s, rays)
-    occ, _ = api.probe_trace(s, rays, tmax=1.5, any_hit=True)
+    tri, t = api.probe_trace(s, rays, wide=wide)
+    occ, _ = api.probe_trace(s, rays, tmax=1.5, any_hit=True, wide=wide)
     tri, t, occ = tri.cpu().numpy(), t.cpu().numpy(), occ.cpu().numpy()
     T, bmin, traw = _exact_hits(tris, o, d)
     best = T.argmin(1)
@@ -99,6 +100,37 @@ def test_closest_hit_ids_bit_exact(api, scenes_mod, seed, n_tris):
     clear_occ = (~near_edge) & (np.abs(T - 1.5) > 1e-4).all(1)
     ref_occ = (T < 1.5).any(1)
     assert np.array_equal(occ[clear_occ].astype(bool), ref_occ[clear_occ])
+
+
+@pytest.mark.parametrize("which", ["cornell_box", "diff_scene", "large_scene"])
+def test_wide_bvh_hits_equal_binary(api, scenes_mod, which):
+    """Both trees cull conservatively and share the triangle test and the tie
+    rule, so closest hits (index and t) and occlusion agree bit for bit."""
+    import torch
+    sc = getattr(scenes_mod, which)()
+    s = api.Scene(sc)
+    rng = np.random.default_rng(17)
+    n = 200_000
+    lo, hi = sc.tris.reshape(-1, 3).min(0), sc.tris.reshape(-1, 3).max(0)
+    # origins inside the scene box and on scene triangles (bounce-like rays)
+    o1 = rng.uniform(lo, hi, (n // 2, 3))
+    k = rng.integers(0, sc.n_tris, n - n // 2)
+    b = rng.dirichlet([1, 1, 1], n - n // 2)
+    o2 = np.einsum("nk,nkc->nc", b, sc.tris[k].astype(np.float64))
+    o = np.concatenate([o1, o2]).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    o = o + 1e-4 * d * (np.abs(o).max(1, keepdims=True) + 1)
+    rays = torch.from_numpy(np.concatenate([o, d], 1).astype(np.float32)).cuda()
+    ta, da = api.probe_trace(s, rays)
+    tb, db = api.probe_trace(s, rays, wide=True)
+    oa, _ = api.probe_trace(s, rays, tmax=0.7, any_hit=True)
+    ob, _ = api.probe_trace(s, rays, tmax=0.7, any_hit=True, wide=True)
+    s.sync()
+    assert (ta >= 0).float().mean().item() > 0.3
+    assert torch.equal(ta, tb)
+    assert torch.equal(da, db)
+    assert torch.equal(oa, ob)
 
 
 def test_closest_hit_large_scene_vs_oracle(api, oracle_mod, scenes_mod):
@@ -239,7 +271,7 @@ def test_counters_and_stats(api, cornell):
     api.render(s, 64, 64, 256, 3.5, 0.01, 2, 1, 4, flags=api.MT_COUNTERS)
     c = s.read_counters(reset=True)
     assert c["paths"] == 64 * 64 * 2
-    assert c["vertices"] > c["paths"] and c["node_visits"] > 0 and c["tri_tests"] > 0
+    assert c["vertices"] > c["paths"] and c["node_bytes"] > 0 and c["tri_tests"] > 0
     ref = osc.render(64, 64, 256, 3.5, 0.01, 2, 1, 4)
     assert abs(c["vertices"] - ref["counters"]["vertices"]) <= 1e-3 * ref["counters"]["vertices"]
     st = s.stats()
@@ -258,11 +290,12 @@ def test_invalid_arguments_give_status(api, cornell):
 
 def _form_options(api, opts):
     return {"wavefront": api.MT_OPT_WAVEFRONT,
+            "wavefront_wide_bvh": api.MT_OPT_WAVEFRONT | api.MT_OPT_WIDE_BVH,
             "wavefront_dynamic_fetch": api.MT_OPT_WAVEFRONT | api.MT_OPT_DYNAMIC_FETCH,
             "megakernel_refill16": api.MT_OPT_REFILL(16)}[opts]
 
 
-@pytest.mark.parametrize("opts", ["wavefront", "wavefront_dynamic_fetch", "megakernel_refill16"])
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_dynamic_fetch", "megakernel_refill16"])
 def test_forward_forms_per_path_parity(api, cornell, opts):
     """The wavefront form (with or without dynamic ray fetch in its traversal
     kernels) and the megakernel with deferred refill compute the same
@@ -292,7 +325,7 @@ def test_forward_forms_per_path_parity(api, cornell, opts):
     assert rel_l2(f2.cpu().numpy(), f3.cpu().numpy()) < 1e-4
 
 
-@pytest.mark.parametrize("opts", ["wavefront", "wavefront_dynamic_fetch"])
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_dynamic_fetch"])
 def test_wavefront_large_scene_matches_megakernel(api, scenes_mod, opts):
     sc = scenes_mod.diff_scene()
     s = api.Scene(sc)
