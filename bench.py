@@ -99,16 +99,17 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile(kernel_hash):
-    """dram bytes per launch of the render kernel from the committed ncu summary,
-    or None if the kernel sources changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "k_render_large_scene.json")
+def _traffic_from_profile(kernel_hash, name):
+    """DRAM bytes per render of the dominant kernel(s) from the committed ncu
+    summary profiles/<name>.json, or None if the kernel sources changed since it
+    was captured."""
+    p = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(p):
         return None, None
     d = json.load(open(p))
     if d.get("kernel_hash") != kernel_hash:
         return None, d.get("kernel_hash")
-    return d.get("dram_bytes_per_launch"), d.get("kernel_hash")
+    return d.get("dram_bytes_per_render"), d.get("kernel_hash")
 
 
 def _peaks():
@@ -229,7 +230,12 @@ def main():
     f = scenes.LARGE_FILM
     spp, depth, seed = 256, 8, scenes.RENDER_SEED
     s = api.Scene(sc)
-    autotune.apply(s, "render", sc, f, spp, depth)
+    cfg = autotune.apply(s, "render", sc, f, spp, depth)
+    wavefront = bool(cfg and cfg.get("options", 0) & api.MT_OPT_WAVEFRONT)
+    if wavefront:
+        # CUDA events at the stage boundaries time the traversal kernels inside the timed region
+        s.set_launch(api.MT_LAUNCH_RENDER, cfg["threads"], cfg["tile"], cfg["ctas_per_sm"], cfg.get("priv", -1),
+                     cfg["options"] | api.MT_OPT_STAGE_TIMING)
     film, steady = api.new_film(f.H, f.W, f.T)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -247,11 +253,13 @@ def main():
     cnt = s.read_counters(reset=True)
     s.sync()
     film_bytes = film.numel() * 4 + steady.numel() * 4
-    alg_bytes = cnt["node_bytes"] + cnt["tri_tests"] * 48 + cnt["vertices"] * 32 + film_bytes
+    trav_bytes = cnt["node_bytes"] + cnt["tri_tests"] * 48
+    alg_bytes = trav_bytes + cnt["vertices"] * 32 + film_bytes
     # timed region
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     s.read_counters(reset=True)
+    s.stage_times(reset=True)
     launches0 = s.stats()["launches"]
     if ws > 1:
         torch.distributed.barrier()
@@ -268,15 +276,32 @@ def main():
     clk = clocks.stop()
     s.sync()
     run_cnt = s.read_counters(reset=True)
+    stages = s.stage_times(reset=True)
     launches = s.stats()["launches"] - launches0
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
     total_s, total_vertices = aggregate_ranks(sum(step_ms) / 1000.0, float(run_cnt["vertices"]), ws, "cuda")
     value = total_vertices / total_s
     mean_ms = 1000.0 * total_s / args.steps
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / (mean_ms / 1000.0) / 1e9
+    render_achieved = alg_bytes / (mean_ms / 1000.0) / 1e9
     khash = _kernel_hash()
-    traffic, _ = _traffic_from_profile(khash)
+    traffic, _ = _traffic_from_profile(khash, "k_wf_traversal_large_scene" if wavefront else "k_render_large_scene")
+    if wavefront:
+        # dominant kernel: the BVH traversal (k_wf_extend + k_wf_shadow), timed by its own events
+        trav_ms = (stages["extend_ms"] + stages["shadow_ms"]) / args.steps
+        achieved = trav_bytes / (trav_ms / 1000.0) / 1e9
+        kernel_name = "k_wf_extend + k_wf_shadow (BVH traversal of extension and shadow rays)"
+        kernel_bytes = trav_bytes
+        per_unit = "per ray: BVH node bytes fetched (32 B per node) + 48 B per triangle tested"
+        stage_ms = {k: v / args.steps for k, v in stages.items() if k.endswith("_ms")}
+        stage_ms["share_of_step"] = {k: v / mean_ms for k, v in stage_ms.items()}
+    else:
+        achieved = render_achieved
+        kernel_name = "k_render (forward megakernel)"
+        kernel_bytes = alg_bytes
+        per_unit = ("node bytes fetched + triangle tests x 48 B + 32 B material/emitter per vertex "
+                    "+ film and steady image written once")
+        stage_ms = None
     # measured rates of the render kernel's own access patterns on this GPU
     aux = {}
     try:
@@ -326,10 +351,11 @@ def main():
                          f"{film_bytes / 1e9:.2f} GB per step",
                    "bvh": s.stats()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "per_vertex": "node visits x 32 B + triangle tests x 48 B + 32 B material/emitter per vertex "
-                                   "+ film and steady image written once",
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
+                     "algorithmic_bytes_per_launch": kernel_bytes, "per_unit": per_unit,
+                     "stage_ms_per_step": stage_ms,
+                     "whole_render": {"algorithmic_bytes": alg_bytes, "achieved_gbs": render_achieved,
+                                      "frac": render_achieved / peak},
                      "counts": cnt, "kernel_hash": khash, "aux": aux},
         "clocks": clk,
         "gpu_launches": launches,
@@ -346,10 +372,12 @@ def main():
 
 
 def profile_case(which):
-    """Reduced-size launches of the hot kernels for ncu captures: the large
-    scene (full geometry) at 128x128 px, 256 spp with the launch configuration of
-    the benchmark; the differentiable scene's backward at 64x64; a 16x16
-    confocal NLOS grid."""
+    """Launches of the hot kernels for ncu captures.  small: the large scene
+    (full geometry) at 128x128 px, 256 spp with the launch configuration of the
+    benchmark, the differentiable scene's backward at 64x64, a 16x16 confocal
+    NLOS grid.  traversal: one full-size render of the benchmark (512x512 px,
+    256 spp) with the benchmark's launch configuration, for single-pass
+    counters of every traversal launch of one render."""
     import torch
     from paper_2510_25660_gb300 import api, scenes
     from paper_2510_25660_gb300 import build as b
@@ -360,6 +388,12 @@ def profile_case(which):
     f = scenes.LARGE_FILM
     s = api.Scene(sc)
     autotune.apply(s, "render", sc, f, 256, 8)
+    if which == "traversal":
+        film, steady = api.new_film(f.H, f.W, f.T)
+        api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 256, scenes.RENDER_SEED, 8, out=(film, steady))
+        s.sync()
+        print("profile case done")
+        return
     film, steady = api.new_film(128, 128, f.T)
     for _ in range(3):
         api.render(s, 128, 128, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))

@@ -201,6 +201,15 @@ mt_status mt_sync(mt_scene scene, void *stream);
  * Synchronises `stream`; reset != 0 zeroes them afterwards. */
 mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *stream);
 
+/* Device time of the wavefront stages of renders launched with
+ * MT_OPT_STAGE_TIMING since the last reset (out has 5 entries): out[0] ms in
+ * queue setup, camera-ray generation (and ray sorting), out[1] ms in
+ * extension-ray traversal (k_wf_extend), out[2] ms in shading (k_wf_shade),
+ * out[3] ms in shadow-ray traversal (k_wf_shadow), out[4] iterations.  The
+ * values are complete when the renders have returned (they synchronise their
+ * stream).  reset != 0 zeroes them afterwards. */
+mt_status mt_stage_times(mt_scene scene, double *out, int32_t reset);
+
 /* Scene statistics (out has 8 entries): out[0] n_tris, out[1] BVH internal
  * nodes, out[2] BVH depth, out[3] SAH cost x 1000 (sum of node areas / root
  * area, with unit traversal and intersection costs), out[4] light units,
@@ -238,12 +247,19 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * MT_OPT_REFILL(k) lanes of the warp are idle (k = 0: 8; k > 32: 32).
  * MT_OPT_WIDE_BVH (with MT_OPT_WAVEFRONT) = extension and shadow rays traverse
  * the scene's 8-wide BVH (80-byte nodes, 8-bit child planes in a per-node
- * frame) instead of the binary one; hits are the same. */
+ * frame) instead of the binary one; hits are the same.
+ * MT_OPT_SORT_RAYS (with MT_OPT_WAVEFRONT) = before each extension pass the
+ * queued rays are sorted by direction octant and the Morton code of their
+ * origin, so that a warp traces similar rays (the film is the same).
+ * MT_OPT_STAGE_TIMING (with MT_OPT_WAVEFRONT) = CUDA events on the render
+ * stream at every stage boundary; read the totals with mt_stage_times. */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
 #define MT_OPT_WAVEFRONT 4u
 #define MT_OPT_DYNAMIC_FETCH 8u
 #define MT_OPT_WIDE_BVH 16u
+#define MT_OPT_SORT_RAYS 32u
+#define MT_OPT_STAGE_TIMING 64u
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1

@@ -28,6 +28,7 @@ MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
 MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
 MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
 MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH, MT_OPT_WIDE_BVH = 1, 2, 4, 8, 16
+MT_OPT_SORT_RAYS, MT_OPT_STAGE_TIMING = 32, 64
 
 
 def MT_OPT_REFILL(k):
@@ -80,6 +81,7 @@ SIGNATURES = {
     "mt_render_backward": (C.c_int, [_P, _P, _P, _P, _I32, _U64, _I32, _U64, _P, _P, _P, _P]),
     "mt_sync": (C.c_int, [_P, _P]),
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
+    "mt_stage_times": (C.c_int, [_P, _P, _I32]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
     "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _U32]),
     "mt_scene_destroy": (None, [_P]),
@@ -174,6 +176,10 @@ def mt_sync(scene, stream):
 
 def mt_read_counters(scene, out, reset, stream):
     return _call("mt_read_counters", scene, out, reset, stream)
+
+
+def mt_stage_times(scene, out, reset):
+    return _call("mt_stage_times", scene, out, reset)
 
 
 def mt_scene_stats(scene, out):
@@ -273,6 +279,13 @@ class Scene:
         keys = ["n_tris", "bvh_nodes", "bvh_depth", "sah_x1000", "light_units", "device_bytes", "build_us",
                 "launches"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def stage_times(self, reset=True) -> dict:
+        """Milliseconds per wavefront stage of renders run with MT_OPT_STAGE_TIMING."""
+        out = (C.c_double * 5)()
+        mt_stage_times(self.h, out, int(reset))
+        keys = ["generate_ms", "extend_ms", "shade_ms", "shadow_ms", "iterations"]
+        return {k: float(out[i]) for i, k in enumerate(keys)}
 
     def read_counters(self, reset=True, stream=None) -> dict:
         out = (C.c_uint64 * 8)()

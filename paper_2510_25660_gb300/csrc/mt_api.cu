@@ -98,6 +98,11 @@ struct mt_scene_s {
     uint4 *wf_meta = nullptr, *wf_sh_m = nullptr;
     int4 *wf_hit = nullptr;
     uint32_t *wf_qa = nullptr, *wf_qb = nullptr, *wf_free = nullptr, *wf_counters = nullptr;
+    uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr;  // ray reordering
+    char *wf_stmp = nullptr;
+    size_t wf_stmp_bytes = 0;
+    uint32_t wf_sort_cap = 0;
+    WfTiming wf_timing;  // stage times of wavefront renders (MT_OPT_STAGE_TIMING)
     unsigned long long *wf_next = nullptr;
     void *wf_iter = nullptr;
     size_t bytes = 0;
@@ -509,6 +514,7 @@ void mt_scene_destroy(mt_scene s) {
     cudaDeviceSynchronize();
     if (s->nlos_graph.exec) cudaGraphExecDestroy(s->nlos_graph.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    mt_wf_timing_free(&s->wf_timing);
     s->al.free_all();
     delete s;
 }
@@ -645,6 +651,20 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         }
         s->wf_cap = P;
     }
+    const bool sort_rays = (cfg.options & MT_OPT_SORT_RAYS) != 0;
+    if (sort_rays && P > s->wf_sort_cap) {
+        cudaStreamCaptureStatus cs;
+        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                     "the first sorted wavefront render of this size must not be captured (it sizes the sort)");
+        auto &al = s->al;
+        MT_TRY(al.alloc(&s->wf_sk, P, "ray sort keys"));
+        MT_TRY(al.alloc(&s->wf_sko, P, "ray sort keys"));
+        MT_TRY(al.alloc(&s->wf_sq, P, "ray sort queue"));
+        s->wf_stmp_bytes = mt_wf_sort_bytes(P);
+        MT_TRY(al.alloc(&s->wf_stmp, s->wf_stmp_bytes, "ray sort scratch"));
+        s->wf_sort_cap = P;
+    }
     WfParams w{};
     w.H = rp.H;
     w.W = rp.W;
@@ -684,12 +704,20 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     const int fetch_k = (int)((cfg.options >> 8) & 0xFFu);
     w.dynamic_fetch = (cfg.options & MT_OPT_DYNAMIC_FETCH) ? (fetch_k ? std::min(fetch_k, 32) : 8) : 0;
     w.wide = (cfg.options & MT_OPT_WIDE_BVH) ? 1 : 0;
+    w.sort_rays = sort_rays ? 1 : 0;
+    w.sort_keys = s->wf_sk;
+    w.sort_keys_out = s->wf_sko;
+    w.sort_q = s->wf_sq;
+    w.sort_tmp = s->wf_stmp;
+    w.sort_tmp_bytes = s->wf_stmp_bytes;
     if (!(rp.flags & MT_ACCUMULATE)) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
     }
     long long n = 0;
-    const mt_status r = mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n);
+    WfTiming *tm = (cfg.options & MT_OPT_STAGE_TIMING) ? &s->wf_timing : nullptr;
+    const mt_status r =
+        mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n, tm);
     s->launches += n + 1;
     return r;
 }
@@ -931,6 +959,17 @@ mt_status mt_sync(mt_scene s, void *stream) {
     return check_err_word(s);
 }
 
+mt_status mt_stage_times(mt_scene s, double *out, int32_t reset) {
+    MT_CHECK_ARG(s != nullptr && out != nullptr, "bad arguments");
+    for (int k = 0; k < 4; ++k) out[k] = s->wf_timing.ms[k];
+    out[4] = (double)s->wf_timing.iters;
+    if (reset) {
+        for (int k = 0; k < 4; ++k) s->wf_timing.ms[k] = 0.0;
+        s->wf_timing.iters = 0;
+    }
+    return MT_OK;
+}
+
 mt_status mt_read_counters(mt_scene s, uint64_t *out, int32_t reset, void *stream) {
     MT_CHECK_ARG(s != nullptr && out != nullptr, "NULL argument");
     MT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
@@ -960,7 +999,7 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
     MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
     MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | MT_OPT_WAVEFRONT | MT_OPT_DYNAMIC_FETCH |
-                              MT_OPT_WIDE_BVH | 0xFF00u)) == 0,
+                              MT_OPT_WIDE_BVH | MT_OPT_SORT_RAYS | MT_OPT_STAGE_TIMING | 0xFF00u)) == 0,
                  "unknown launch options 0x%x", options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;

@@ -204,6 +204,60 @@ struct LightUnit {
     float4 n;   // unit winding normal, w = original triangle index (int bits), -1 for a point emitter
 };
 
+// L2 eviction priorities (PTX createpolicy / .L2::cache_hint, sm_80 and later),
+// off by default: loading BVH nodes and triangle records (~76 MB for 1.16M
+// triangles, less than the 129 MB L2) as evict-last made the 512x512x256-spp
+// forward render of that scene slower (102.8 against 98.5 ms), and streaming the
+// film atomics as evict-first changed nothing (98.5 ms).
+#ifndef MT_L2_KEEP_BVH
+#define MT_L2_KEEP_BVH 0
+#endif
+#ifndef MT_L2_STREAM_FILM
+#define MT_L2_STREAM_FILM 0
+#endif
+
+__device__ __forceinline__ unsigned long long l2_policy_keep() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_stream() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ldg_keep(const uint4 *a) {
+#if MT_L2_KEEP_BVH
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(a), "l"(l2_policy_keep()));
+    return r;
+#else
+    return __ldg(a);
+#endif
+}
+__device__ __forceinline__ float4 ldg_keep(const float4 *a) {
+#if MT_L2_KEEP_BVH
+    float4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(a), "l"(l2_policy_keep()));
+    return r;
+#else
+    return __ldg(a);
+#endif
+}
+// fire-and-forget float add into global memory, evict-first in L2
+__device__ __forceinline__ void red_add_stream(float *a, float v) {
+#if MT_L2_STREAM_FILM
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(l2_policy_stream())
+                 : "memory");
+#else
+    atomicAdd(a, v);
+#endif
+}
+
 struct DevScene {
     const uint4 *nodes;    // 2 x uint4 per internal node
     const uint4 *wnodes;   // 5 x uint4 per 8-wide node (root = node 0)

@@ -77,7 +77,24 @@ struct WfParams {
     unsigned long long *dump_count;
     int32_t dynamic_fetch;         // 0: off; else idle lanes of a warp that trigger a fetch (1..32)
     int32_t wide;                  // traverse the 8-wide BVH
+    // ray reordering: extension rays sorted by (direction octant, origin Morton code)
+    int32_t sort_rays;
+    uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue
+    void *sort_tmp;
+    size_t sort_tmp_bytes;
 };
+
+size_t mt_wf_sort_bytes(uint32_t P);
+
+// Per-stage device time of wavefront renders, from CUDA events recorded on the
+// render stream at the stage boundaries of every iteration.
+struct WfTiming {
+    cudaEvent_t *ev = nullptr;  // pool of n_ev events
+    int n_ev = 0;
+    double ms[4] = {0, 0, 0, 0};  // setup + generate (+ sort), extend, shade, shadow
+    long long iters = 0;
+};
+void mt_wf_timing_free(WfTiming *t);
 
 struct LaunchCfg {
     int threads, tile, ctas_per_sm, num_sms;
@@ -91,4 +108,4 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
 mt_status mt_launch_nlos(const DevScene &s, const NlosParams &p, const LaunchCfg &cfg, bool dump, bool counters,
                          cudaStream_t st);
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p, int num_sms, bool dump, bool counters,
-                              cudaStream_t st, long long *launches);
+                              cudaStream_t st, long long *launches, WfTiming *timing = nullptr);

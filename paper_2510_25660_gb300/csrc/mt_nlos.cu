@@ -43,7 +43,7 @@ __device__ __forceinline__ HiddenSample sample_hidden(const DevScene &s, const N
     const uint4 R = philox4x32_10(make_uint4((uint32_t)l, smp, 0u, 0u), p.k0, p.k1);
     const int tri = pick_hidden(p, R.x);
     const int k = __ldg(&s.leaf_of[tri]);
-    const float3 v0 = xyz(__ldg(&s.tris[3 * k])), v1 = xyz(__ldg(&s.tris[3 * k + 1])), v2 = xyz(__ldg(&s.tris[3 * k + 2]));
+    const float3 v0 = xyz(ldg_keep(&s.tris[3 * k])), v1 = xyz(ldg_keep(&s.tris[3 * k + 1])), v2 = xyz(ldg_keep(&s.tris[3 * k + 2]));
     h.tri = tri;
     h.y = tri_point(v0, v1, v2, u24(R.y), u24(R.z));
     h.partial = 0.f;

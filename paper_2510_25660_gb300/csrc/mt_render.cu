@@ -408,7 +408,7 @@ struct Tracer {
         cnt.vertices++;
         const float3 x = ps.o + ps.d * th;
         if (!(ps.depth == 1 && (p.flags & MT_UNWARP))) ps.opl += th;
-        const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
+        const float4 p0 = ldg_keep(&s.tris[3 * k]), p1 = ldg_keep(&s.tris[3 * k + 1]), p2 = ldg_keep(&s.tris[3 * k + 2]);
         const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
         const float3 wo = -ps.d;
         const float cwo = dot(ng, wo);

@@ -127,8 +127,8 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
     uint32_t ref = 0;
     for (;;) {
         if (!(ref & 0x80000000u)) {
-            const uint4 a = __ldg(&s.nodes[2 * ref]);
-            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
+            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
@@ -151,9 +151,9 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
         } else {
             const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
             for (int k = first; k < first + n; ++k) {
-                const float4 p0 = __ldg(&s.tris[3 * k]);
-                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
-                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                const float4 p0 = ldg_keep(&s.tris[3 * k]);
+                const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+                const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
                 if (CNT) cnt.tris++;
                 float t;
                 if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
@@ -191,8 +191,8 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
     uint32_t ref = 0;
     for (;;) {
         if (!(ref & 0x80000000u)) {
-            const uint4 a = __ldg(&s.nodes[2 * ref]);
-            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
+            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
@@ -211,9 +211,9 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
         } else {
             const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
             for (int k = first; k < first + n; ++k) {
-                const float4 p0 = __ldg(&s.tris[3 * k]);
-                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
-                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                const float4 p0 = ldg_keep(&s.tris[3 * k]);
+                const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+                const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
                 if (CNT) cnt.tris++;
                 float t;
                 if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) return true;
@@ -253,8 +253,8 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
     while (ref != MT_DONE) {
         // internal nodes; the first leaf met is postponed
         while (ref != MT_DONE && !MT_IS_LEAF(ref)) {
-            const uint4 a = __ldg(&s.nodes[2 * ref]);
-            const uint4 b = __ldg(&s.nodes[2 * ref + 1]);
+            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
+            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
@@ -297,9 +297,9 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
             const int first = (int)(leaf & 0x1FFFFFFFu), n = (int)((leaf >> 29) & 3u) + 1;
             leaf = MT_DONE;
             for (int k = first; k < first + n; ++k) {
-                const float4 p0 = __ldg(&s.tris[3 * k]);
-                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
-                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                const float4 p0 = ldg_keep(&s.tris[3 * k]);
+                const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+                const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
                 if (CNT) cnt.tris++;
                 float t;
                 if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
@@ -373,8 +373,8 @@ template <bool ANY, bool CNT>
 __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, float tmax, TravState &ts, uint2 *st,
                                           TraceCnt &cnt) {
     if (!(ts.ref & 0x80000000u)) {
-        const uint4 a = __ldg(&s.nodes[2 * ts.ref]);
-        const uint4 b = __ldg(&s.nodes[2 * ts.ref + 1]);
+        const uint4 a = ldg_keep(&s.nodes[2 * ts.ref]);
+        const uint4 b = ldg_keep(&s.nodes[2 * ts.ref + 1]);
         if (CNT) cnt.nodes += 32;
         float tn0, tf0, tn1, tf1;
         slab(r, a.x, a.y, a.z, ts.tbest, tn0, tf0);
@@ -403,9 +403,9 @@ __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, floa
     } else {
         const int first = (int)(ts.ref & 0x1FFFFFFFu), n = (int)((ts.ref >> 29) & 3u) + 1;
         for (int k = first; k < first + n; ++k) {
-            const float4 p0 = __ldg(&s.tris[3 * k]);
-            const float4 p1 = __ldg(&s.tris[3 * k + 1]);
-            const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+            const float4 p0 = ldg_keep(&s.tris[3 * k]);
+            const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+            const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
             if (CNT) cnt.tris++;
             float t;
             if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
@@ -510,7 +510,7 @@ __device__ __forceinline__ int trace_wide(const DevScene &s, const RayT &r, floa
     uint32_t node = 0;
     for (;;) {
         const uint4 *np = s.wnodes + MT_WIDE_WORDS * (size_t)node;
-        const uint4 w0 = __ldg(np), w1 = __ldg(np + 1), w2 = __ldg(np + 2), w3 = __ldg(np + 3), w4 = __ldg(np + 4);
+        const uint4 w0 = ldg_keep(np), w1 = ldg_keep(np + 1), w2 = ldg_keep(np + 2), w3 = ldg_keep(np + 3), w4 = ldg_keep(np + 4);
         if (CNT) cnt.nodes += 80;
         const uint32_t hits = wide_hits(r, w0, w2, w3, w4, tbest);
         const uint32_t imask = w0.w >> 24;
@@ -521,9 +521,9 @@ __device__ __forceinline__ int trace_wide(const DevScene &s, const RayT &r, floa
             const uint32_t meta = ((slot < 4 ? w1.z : w1.w) >> (8 * (slot & 3))) & 0xFFu;
             const int first = (int)w1.y + (int)(meta & 31u), last = first + (int)((meta >> 5) & 3u);
             for (int k = first; k <= last; ++k) {
-                const float4 p0 = __ldg(&s.tris[3 * k]);
-                const float4 p1 = __ldg(&s.tris[3 * k + 1]);
-                const float4 p2 = __ldg(&s.tris[3 * k + 2]);
+                const float4 p0 = ldg_keep(&s.tris[3 * k]);
+                const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+                const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
                 if (CNT) cnt.tris++;
                 float t;
                 if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {

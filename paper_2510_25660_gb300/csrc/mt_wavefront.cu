@@ -14,6 +14,8 @@
 // the queue drains; appends to the queues are warp-aggregated.  New paths get
 // consecutive ids (pixel-major), so camera rays of a warp share a pixel.
 // Contributions go to the film with global atomics (no per-tile ownership).
+#include <cub/cub.cuh>
+
 #include "mt_common.cuh"
 #include "mt_internal.h"
 #include "mt_launch.h"
@@ -59,15 +61,15 @@ __device__ __forceinline__ void wf_splat(const WfParams &p, uint32_t pix, float 
     const float x = (opl - p.start) / p.width;
     if (x >= 0.f && x < (float)p.T) {
         float *h = p.film + ((size_t)pix * p.T + (int)x) * 3;
-        atomicAdd(h, c.x);
-        atomicAdd(h + 1, c.y);
-        atomicAdd(h + 2, c.z);
+        red_add_stream(h, c.x);
+        red_add_stream(h + 1, c.y);
+        red_add_stream(h + 2, c.z);
     }
     if (p.steady) {
         float *g = p.steady + (size_t)pix * 3;
-        atomicAdd(g, c.x);
-        atomicAdd(g + 1, c.y);
-        atomicAdd(g + 2, c.z);
+        red_add_stream(g, c.x);
+        red_add_stream(g + 1, c.y);
+        red_add_stream(g + 2, c.z);
     }
 }
 
@@ -180,6 +182,38 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevSc
     if (CNT) {
         warp_count(&s.counters[4], tc.nodes);
         warp_count(&s.counters[5], tc.tris);
+    }
+}
+
+// 9 bits -> every third bit of 27
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x1FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Sort keys of the queued extension rays: direction octant (3 bits) above the
+// Morton code of the origin on a 512^3 grid over the scene box (27 bits).
+// Entries past the queue's end get the largest key and sort to the back.
+__global__ void k_wf_sort_keys(const DevScene s, const WfParams p, const uint32_t *qcur) {
+    const uint32_t n = p.counters[C_CUR];
+    const float gx = 512.0f / (65536.0f * s.q_scale.x), gy = 512.0f / (65536.0f * s.q_scale.y),
+                gz = 512.0f / (65536.0f * s.q_scale.z);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const uint32_t slot = qcur[i];
+            const float4 o = p.o[slot], d = p.d[slot];
+            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), 511.0f);
+            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), 511.0f);
+            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), 511.0f);
+            const uint32_t oct = (d.x < 0.0f ? 1u : 0u) | (d.y < 0.0f ? 2u : 0u) | (d.z < 0.0f ? 4u : 0u);
+            p.sort_keys[i] = (oct << 27) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+        } else {
+            p.sort_keys[i] = 0xFFFFFFFFu;
+        }
     }
 }
 
@@ -304,7 +338,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                 const float th = __int_as_float(h.z);
                 const float3 x = xyz(o4) + dir * th;
                 if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
-                const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
+                const float4 p0 = ldg_keep(&s.tris[3 * k]), p1 = ldg_keep(&s.tris[3 * k + 1]), p2 = ldg_keep(&s.tris[3 * k + 2]);
                 const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
                 const float3 wo = -dir;
                 const float cwo = dot(ng, wo);
@@ -455,8 +489,63 @@ __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsi
 
 }  // namespace
 
+size_t mt_wf_sort_bytes(uint32_t P) {
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                    (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)P, 0, 30);
+    return bytes;
+}
+
+void mt_wf_timing_free(WfTiming *t) {
+    for (int i = 0; i < t->n_ev; ++i) cudaEventDestroy(t->ev[i]);
+    free(t->ev);
+    t->ev = nullptr;
+    t->n_ev = 0;
+}
+
+namespace {
+
+// event k of iteration it (five boundaries per iteration), growing the pool
+mt_status wf_event(WfTiming *t, unsigned long long it, int k, cudaStream_t st) {
+    const long long idx = (long long)it * 5 + k;
+    if (idx >= t->n_ev) {
+        const int n = (int)std::max<long long>(idx + 1, 2 * (long long)t->n_ev + 40);
+        cudaEvent_t *ev = (cudaEvent_t *)realloc(t->ev, sizeof(cudaEvent_t) * n);
+        if (!ev) {
+            mt::set_error("stage timing: out of host memory");
+            return MT_ERR_OUT_OF_MEMORY;
+        }
+        t->ev = ev;
+        for (int i = t->n_ev; i < n; ++i) {
+            if (cudaEventCreate(&t->ev[i]) != cudaSuccess) {
+                t->n_ev = i;
+                mt::set_error("stage timing: cudaEventCreate failed");
+                return MT_ERR_CUDA;
+            }
+            t->n_ev = i + 1;
+        }
+    }
+    MT_CUDA_TRY(cudaEventRecord(t->ev[idx], st));
+    return MT_OK;
+}
+
+// add the stage times of iterations [0, n) once the stream has drained
+mt_status wf_accumulate(WfTiming *t, unsigned long long n) {
+    for (unsigned long long it = 0; it < n; ++it) {
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            MT_CUDA_TRY(cudaEventElapsedTime(&ms, t->ev[it * 5 + k], t->ev[it * 5 + k + 1]));
+            t->ms[k] += ms;
+        }
+    }
+    t->iters += (long long)n;
+    return MT_OK;
+}
+
+}  // namespace
+
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms, bool dump, bool counters,
-                              cudaStream_t st, long long *launches) {
+                              cudaStream_t st, long long *launches, WfTiming *timing) {
     WfParams p = p0;
     const int grid = num_sms * 8;
     k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.free_q, p.P, p.counters,
@@ -467,21 +556,34 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
     const unsigned long long bound =
         (p.total_paths + p.P - 1) / p.P * (unsigned long long)(p.max_depth + 1) + (unsigned long long)p.max_depth + 2;
     for (unsigned long long iter = 0; iter < bound; ++iter) {
+        if (timing) MT_TRY(wf_event(timing, iter, 0, st));
         k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
         k_wf_generate<<<grid, 256, 0, st>>>(s, p, p.iter, qa);
         const bool dyn = p.dynamic_fetch && !dump;
+        const uint32_t *qext = qa;
+        if (p.sort_rays && !dump) {
+            k_wf_sort_keys<<<grid, 256, 0, st>>>(s, p, qa);
+            size_t bytes = p.sort_tmp_bytes;
+            MT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(p.sort_tmp, bytes, p.sort_keys, p.sort_keys_out, qa, p.sort_q,
+                                                        (int)p.P, 0, 30, st));
+            qext = p.sort_q;
+            *launches += 1;
+        }
+        if (timing) MT_TRY(wf_event(timing, iter, 1, st));
         if (dyn) {
             if (counters) k_wf_trace_dyn<false, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<false, false><<<grid, 256, 0, st>>>(s, p, qa);
         } else if (p.wide) {
-            if (counters) k_wf_extend<true, true><<<grid, 256, 0, st>>>(s, p, qa);
-            else k_wf_extend<true, false><<<grid, 256, 0, st>>>(s, p, qa);
+            if (counters) k_wf_extend<true, true><<<grid, 256, 0, st>>>(s, p, qext);
+            else k_wf_extend<true, false><<<grid, 256, 0, st>>>(s, p, qext);
         } else {
-            if (counters) k_wf_extend<false, true><<<grid, 256, 0, st>>>(s, p, qa);
-            else k_wf_extend<false, false><<<grid, 256, 0, st>>>(s, p, qa);
+            if (counters) k_wf_extend<false, true><<<grid, 256, 0, st>>>(s, p, qext);
+            else k_wf_extend<false, false><<<grid, 256, 0, st>>>(s, p, qext);
         }
+        if (timing) MT_TRY(wf_event(timing, iter, 2, st));
         if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
         else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (timing) MT_TRY(wf_event(timing, iter, 3, st));
         if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
@@ -501,6 +603,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_shadow<false, false, false><<<grid, 256, 0, st>>>(s, p);
         }
         MT_CUDA_TRY(cudaGetLastError());
+        if (timing) MT_TRY(wf_event(timing, iter, 4, st));
         *launches += 5;
         uint32_t *t = qa;
         qa = qb;
@@ -510,9 +613,10 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             uint32_t done = 0;
             MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             MT_CUDA_TRY(cudaStreamSynchronize(st));
-            if (done) return MT_OK;
+            if (done) return timing ? wf_accumulate(timing, iter + 1) : MT_OK;
         }
     }
+    if (timing) MT_TRY(wf_accumulate(timing, bound));
     // one more setup decides whether anything is left
     k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
     *launches += 1;
