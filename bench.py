@@ -530,10 +530,74 @@ def compare():
     print(json.dumps(out), flush=True)
 
 
+def _timed(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def secondary(api, autotune, scenes):
-    """Backward grads/s on the differentiable scene and batched NLOS throughput."""
+    """Throughput of the other workloads: backward grads/s on the differentiable
+    scene, batched NLOS, the Cornell box and participating-media forward renders,
+    the media backward pass and the frequency-space (phasor) film."""
     import torch
     out = {}
+    # Cornell box: 64x64, T=256, 16 spp, depth 4 (65,536 paths)
+    sc = scenes.cornell_box()
+    f = scenes.CORNELL_FILM
+    s = api.Scene(sc)
+    film, steady = api.new_film(f.H, f.W, f.T)
+    ms = _timed(lambda: api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 16, 1, 4, out=(film, steady)), 20)
+    s.read_counters(reset=True)
+    api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 16, 1, 4, out=(film, steady))
+    c = s.read_counters(reset=True)
+    out["cornell"] = {"vertices_per_s": c["vertices"] / (ms / 1000.0), "ms_per_render": ms,
+                      "workload": "36-triangle Cornell box, 64x64 px, T=256 x 0.01 m, 16 spp, max_depth 4"}
+    del s, film, steady
+    # participating media: Cornell box + 128^3 heterogeneous medium, 256x256, T=1024, 128 spp, depth 16
+    sc = scenes.media_scene()
+    f = scenes.MEDIA_FILM
+    s = api.Scene(sc)
+    film, steady = api.new_film(f.H, f.W, f.T)
+    ms = _timed(lambda: api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 128, 1, 16, out=(film, steady)), 3)
+    s.read_counters(reset=True)
+    api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 128, 1, 16, out=(film, steady))
+    c = s.read_counters(reset=True)
+    g = torch.randn_like(film)
+    outg = (torch.zeros((sc.n_tris, 3), device="cuda"), torch.zeros((len(sc.emitters), 3), device="cuda"),
+            torch.zeros(1, device="cuda"))
+    bms = _timed(lambda: api.render_backward(s, f.T, f.start_opl, f.bin_width, 128, 1, 16, g, out=outg), 3)
+    s.read_counters(reset=True)
+    api.render_backward(s, f.T, f.start_opl, f.bin_width, 128, 1, 16, g, out=outg)
+    cb = s.read_counters(reset=True)
+    s.sync()
+    out["media"] = {"vertices_per_s": c["vertices"] / (ms / 1000.0), "ms_per_render": ms,
+                    "backward_vertices_per_s": cb["vertices"] / (bms / 1000.0), "ms_per_backward": bms,
+                    "workload": "Cornell box in a 128^3 heterogeneous medium (sigma_t 0.1-2 /m, albedo 0.9, HG 0.3), "
+                                "256x256 px, T=1024 x 0.005 m, 128 spp, max_depth 16; backward = surface and "
+                                "medium albedo gradients"}
+    del s, film, steady, g
+    # frequency-space film of the benchmark frame: 4 wavelengths instead of 2048 time bins
+    sc = scenes.large_scene()
+    f = scenes.LARGE_FILM
+    s = api.Scene(sc)
+    lam = [0.4, 0.2, 0.1, 0.05]
+    ms = _timed(lambda: api.render_phasor(s, f.H, f.W, lam, 256, 1, 8), 3)
+    s.read_counters(reset=True)
+    api.render_phasor(s, f.H, f.W, lam, 256, 1, 8)
+    c = s.read_counters(reset=True)
+    s.sync()
+    out["phasor"] = {"vertices_per_s": c["vertices"] / (ms / 1000.0), "ms_per_render": ms,
+                     "workload": "large static scene, 512x512 px, 256 spp, max_depth 8, K=4 wavelengths "
+                                 "(0.4, 0.2, 0.1, 0.05 m), phasor film [H][W][K][2][3]"}
+    del s
     # backward: 97k-triangle scene, 256x256x512 film, 64 spp, depth 8
     sc = scenes.diff_scene()
     f = scenes.DIFF_FILM

@@ -72,6 +72,8 @@ static void rng4(uint64_t seed, uint32_t a, uint32_t b, uint32_t c, uint32_t d, 
 #define G_SCATTER 1u
 #define G_TRACK 0x100u
 #define G_RATIO 0x10000u
+#define G_DELAY 0x20000u /* scattering delay at a surface vertex */
+#define G_PULSE 0x20010u /* emission time of a contribution (+ kind) */
 
 /* ------------------------------------------------------------------------- */
 /* scene                                                                      */
@@ -111,6 +113,10 @@ struct mo_scene {
     double *dens;
     v3 m_lo, m_hi;
     double m_albedo, m_g, m_major;
+    /* time-resolved materials and sources (Sec. 4.1, scattering delays; Sec. 3, emission L_e(t)) */
+    double *delay;      /* per triangle: mean of an exponential scattering delay (m), NULL = none */
+    int pulse_type;     /* MO_PULSE_* */
+    double pulse_a, pulse_b;
 };
 
 static double cen(const mo_scene *s, int64_t i, int ax) {
@@ -299,7 +305,47 @@ void mo_scene_destroy(mo_scene *s) {
     free(s->v0); free(s->v1); free(s->v2); free(s->ng); free(s->area); free(s->albedo); free(s->rough);
     free(s->type); free(s->tri_em); free(s->tri_lpdf); free(s->em_type); free(s->em_first); free(s->em_n);
     free(s->em_rad); free(s->em_pos); free(s->unit_tri); free(s->unit_em); free(s->unit_cdf); free(s->unit_p);
-    free(s->nodes); free(s->order); free(s->dens); free(s);
+    free(s->nodes); free(s->order); free(s->dens); free(s->delay); free(s);
+}
+
+/* Scattering delays: the light leaving surface vertex x_i is re-emitted a time
+ * dt_i after it arrived, dt_i ~ Exp(mean tau(x_i)) (Sec. 4.1: the time of
+ * flight gains the sum of the delays along the path; rho(x, dt) = rho(x)
+ * times the delay density, so steady-state values are unchanged). */
+int mo_scene_set_delays(mo_scene *s, const double *tau) {
+    free(s->delay);
+    s->delay = NULL;
+    if (!tau) return 0;
+    for (int64_t i = 0; i < s->n; i++)
+        if (!(tau[i] >= 0.0) || !isfinite(tau[i])) return 1;
+    s->delay = (double *)malloc(sizeof(double) * (size_t)s->n);
+    if (!s->delay) return 1;
+    memcpy(s->delay, tau, sizeof(double) * (size_t)s->n);
+    return 0;
+}
+
+/* Emission L_e(x, t) = L_e(x) p(t) with a unit-area pulse p (Eq. 5 generalised):
+ * DELTA p = delta(t); BOX uniform on [0, a); GAUSSIAN mean a, deviation b;
+ * EXPONENTIAL mean a. */
+int mo_scene_set_pulse(mo_scene *s, int type, double a, double b) {
+    if (type < MO_PULSE_DELTA || type > MO_PULSE_EXPONENTIAL || !isfinite(a) || !isfinite(b)) return 1;
+    if ((type == MO_PULSE_BOX || type == MO_PULSE_EXPONENTIAL) && !(a > 0.0)) return 1;
+    if (type == MO_PULSE_GAUSSIAN && !(b > 0.0)) return 1;
+    s->pulse_type = type;
+    s->pulse_a = a;
+    s->pulse_b = b;
+    return 0;
+}
+
+/* one draw of the emission time from u[0], u[1] */
+static double pulse_time(const mo_scene *s, const double u[4]) {
+    switch (s->pulse_type) {
+    case MO_PULSE_BOX: return s->pulse_a * u[0];
+    case MO_PULSE_GAUSSIAN:  /* Box-Muller */
+        return s->pulse_a + s->pulse_b * sqrt(-2.0 * log(1.0 - u[0])) * cos(2.0 * PI_D * u[1]);
+    case MO_PULSE_EXPONENTIAL: return -s->pulse_a * log(1.0 - u[0]);
+    default: return 0.0;
+    }
 }
 
 void mo_scene_set_params(mo_scene *s, const double *albedo, const double *radiance, double medium_albedo) {
@@ -651,6 +697,12 @@ static void deposit(ctx_t *cx, int32_t pix_full, int32_t lp, int32_t sample, int
                     double opl, const double c[3], const double cbar[3], int32_t em, const vlist_t *vl, int nv,
                     const double *own_ratio) {
     const mo_args *a = cx->a;
+    if (cx->s->pulse_type != MO_PULSE_DELTA) {
+        /* the source emitted this contribution's light at a time drawn from the pulse */
+        double u[4];
+        rng4(a->seed, (uint32_t)pix_full, (uint32_t)sample, (uint32_t)depth, G_PULSE + (uint32_t)kind, u);
+        opl += pulse_time(cx->s, u);
+    }
     double x = (opl - a->start) / a->width;
     double fb = floor(x);
     int32_t bin = (fb < -1e9) ? -1000000000 : (fb > 1e9 ? 1000000000 : (int32_t)fb);
@@ -865,6 +917,11 @@ static void trace_path(ctx_t *cx, int32_t px, int32_t py, int32_t lp, uint32_t s
             }
         }
         if (depth == a->max_depth) return;
+        if (s->delay && s->delay[hit] > 0.0) {
+            /* scattering delay of this vertex: every contribution formed here or later carries it */
+            rng4(seed, pix, smp, (uint32_t)depth, G_DELAY, u);
+            opl += -s->delay[hit] * log(1.0 - u[0]);
+        }
         v3 n = side_normal(ng, wo), t, b;
         basis(n, &t, &b);
         v3 wol = to_local(wo, t, b, n);

@@ -78,6 +78,15 @@ void mo_scene_destroy(mo_scene *s);
 /* Replace albedos / emitter radiances / medium albedo; sampling tables are kept. */
 void mo_scene_set_params(mo_scene *s, const double *albedo, const double *radiance, double medium_albedo);
 
+#define MO_PULSE_DELTA 0
+#define MO_PULSE_BOX 1
+#define MO_PULSE_GAUSSIAN 2
+#define MO_PULSE_EXPONENTIAL 3
+/* per-triangle exponential scattering-delay means in metres (copied; NULL clears); 1 on a bad value */
+int mo_scene_set_delays(mo_scene *s, const double *tau);
+/* emission pulse shared by all emitters; 1 on bad parameters */
+int mo_scene_set_pulse(mo_scene *s, int type, double a, double b);
+
 void mo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void mo_philox_batch(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out);
 

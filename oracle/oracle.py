@@ -23,6 +23,7 @@ _LIB = os.path.join(_LIB_DIR, "libmt_oracle.so")
 UNWARP = 1
 ACCUMULATE = 2
 PIXEL_CENTER = 4
+PULSE_DELTA, PULSE_BOX, PULSE_GAUSSIAN, PULSE_EXPONENTIAL = 0, 1, 2, 3
 STRAT_MIS, STRAT_NEE_ONLY, STRAT_BSDF_ONLY = 0, 1, 2
 
 
@@ -67,6 +68,10 @@ def lib():
         _lib.mo_scene_create.argtypes = [P, C.c_int64, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P]
         _lib.mo_scene_destroy.argtypes = [P]
         _lib.mo_scene_set_params.argtypes = [P, P, P, C.c_double]
+        _lib.mo_scene_set_delays.restype = C.c_int
+        _lib.mo_scene_set_delays.argtypes = [P, P]
+        _lib.mo_scene_set_pulse.restype = C.c_int
+        _lib.mo_scene_set_pulse.argtypes = [P, C.c_int, C.c_double, C.c_double]
         _lib.mo_philox4x32_10.argtypes = [P, P, P]
         _lib.mo_philox_batch.argtypes = [P, C.c_int64, C.c_uint64, P]
         _lib.mo_intersect.restype = C.c_int64
@@ -165,6 +170,19 @@ class OracleScene:
         a = None if albedo is None else np.ascontiguousarray(albedo, np.float64).reshape(-1)
         r = None if radiance is None else np.ascontiguousarray(radiance, np.float64).reshape(-1)
         lib().mo_scene_set_params(self.h, _p(a), _p(r), float("nan") if medium_albedo is None else float(medium_albedo))
+
+    def set_delays(self, tau=None):
+        """Per-triangle exponential scattering-delay means (metres of light travel); None clears."""
+        t = None if tau is None else np.ascontiguousarray(tau, np.float64).reshape(-1)
+        if t is not None and t.shape[0] != self.n_tris:
+            raise ValueError("one delay per triangle")
+        if lib().mo_scene_set_delays(self.h, _p(t)) != 0:
+            raise ValueError("bad delay")
+
+    def set_pulse(self, kind=0, a=0.0, b=0.0):
+        """Emission pulse: 0 delta, 1 box [0, a), 2 Gaussian (mean a, deviation b), 3 exponential (mean a)."""
+        if lib().mo_scene_set_pulse(self.h, int(kind), float(a), float(b)) != 0:
+            raise ValueError("bad pulse")
 
     # -- geometry queries -------------------------------------------------
     def intersect(self, o, d, tmax=np.inf, brute=False):
