@@ -210,6 +210,30 @@ mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *s
  * stream).  reset != 0 zeroes them afterwards. */
 mt_status mt_stage_times(mt_scene scene, double *out, int32_t reset);
 
+/* Scattering delays (Sec. 4.1): light arriving at a surface point of triangle
+ * i is re-emitted after a delay dt ~ Exp(mean tau[i]), so every contribution
+ * formed at or after that vertex arrives later; the delay density has unit
+ * area, so steady-state values do not change.  d_tau: device float32
+ * [n_tris] (input triangle order), means in metres of light travel (c = 1),
+ * each finite and >= 0 (0 = instantaneous); copied into the scene.  NULL
+ * removes the delays.  Applies to mt_render (all forms), mt_render_phasor,
+ * mt_render_dump and mt_render_backward; NLOS captures ignore it.
+ * Synchronises `stream`; MT_ERR_INVALID_ARGUMENT (scene unchanged) on a bad
+ * value. */
+mt_status mt_scene_set_delays(mt_scene scene, const float *d_tau, void *stream);
+
+/* Emission pulse p(t) shared by all emitters, L_e(x, t) = L_e(x) p(t) (Sec. 3,
+ * Eq. 5 with a pulse of unit area in place of the delta): every contribution
+ * carries its own emission time drawn from p.  DELTA: t = 0 (default); BOX:
+ * uniform on [0, a), a > 0; GAUSSIAN: mean a, deviation b > 0; EXPONENTIAL:
+ * mean a > 0 (metres of light travel).  Same scope as mt_scene_set_delays.
+ * MT_ERR_INVALID_ARGUMENT (scene unchanged) on bad parameters. */
+#define MT_PULSE_DELTA 0u
+#define MT_PULSE_BOX 1u
+#define MT_PULSE_GAUSSIAN 2u
+#define MT_PULSE_EXPONENTIAL 3u
+mt_status mt_scene_set_pulse(mt_scene scene, uint32_t shape, float a, float b);
+
 /* Scene statistics (out has 8 entries): out[0] n_tris, out[1] BVH internal
  * nodes, out[2] BVH depth, out[3] SAH cost x 1000 (sum of node areas / root
  * area, with unit traversal and intersection costs), out[4] light units,

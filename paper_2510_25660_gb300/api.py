@@ -29,6 +29,7 @@ MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
 MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
 MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH, MT_OPT_WIDE_BVH = 1, 2, 4, 8, 16
 MT_OPT_SORT_RAYS, MT_OPT_STAGE_TIMING = 32, 64
+MT_PULSE_DELTA, MT_PULSE_BOX, MT_PULSE_GAUSSIAN, MT_PULSE_EXPONENTIAL = 0, 1, 2, 3
 
 
 def MT_OPT_REFILL(k):
@@ -82,6 +83,8 @@ SIGNATURES = {
     "mt_sync": (C.c_int, [_P, _P]),
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
     "mt_stage_times": (C.c_int, [_P, _P, _I32]),
+    "mt_scene_set_delays": (C.c_int, [_P, _P, _P]),
+    "mt_scene_set_pulse": (C.c_int, [_P, _U32, C.c_float, C.c_float]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
     "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _U32]),
     "mt_scene_destroy": (None, [_P]),
@@ -176,6 +179,14 @@ def mt_sync(scene, stream):
 
 def mt_read_counters(scene, out, reset, stream):
     return _call("mt_read_counters", scene, out, reset, stream)
+
+
+def mt_scene_set_delays(scene, d_tau, stream):
+    return _call("mt_scene_set_delays", scene, d_tau, stream)
+
+
+def mt_scene_set_pulse(scene, shape, a, b):
+    return _call("mt_scene_set_pulse", scene, shape, a, b)
 
 
 def mt_stage_times(scene, out, reset):
@@ -279,6 +290,19 @@ class Scene:
         keys = ["n_tris", "bvh_nodes", "bvh_depth", "sah_x1000", "light_units", "device_bytes", "build_us",
                 "launches"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def set_delays(self, tau=None, stream=None):
+        """Per-triangle exponential scattering-delay means (metres), a device
+        float32 tensor [n_tris] (copied); None removes them."""
+        if tau is not None:
+            assert tau.is_cuda and tau.dtype.is_floating_point and tau.numel() == self.n_tris
+            tau = tau.float().contiguous()
+        mt_scene_set_delays(self.h, _ptr(tau) if tau is not None else None, _stream(stream))
+
+    def set_pulse(self, shape=0, a=0.0, b=0.0):
+        """Emission pulse of all emitters: MT_PULSE_DELTA / BOX (width a) /
+        GAUSSIAN (mean a, deviation b) / EXPONENTIAL (mean a)."""
+        mt_scene_set_pulse(self.h, int(shape), float(a), float(b))
 
     def stage_times(self, reset=True) -> dict:
         """Milliseconds per wavefront stage of renders run with MT_OPT_STAGE_TIMING."""

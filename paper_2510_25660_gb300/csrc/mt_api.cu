@@ -103,6 +103,8 @@ struct mt_scene_s {
     size_t wf_stmp_bytes = 0;
     uint32_t wf_sort_cap = 0;
     WfTiming wf_timing;  // stage times of wavefront renders (MT_OPT_STAGE_TIMING)
+    float *delay_buf = nullptr;  // per-triangle scattering-delay means (mt_scene_set_delays)
+    int *check_flag = nullptr;   // validation result of mt_scene_set_delays
     unsigned long long *wf_next = nullptr;
     void *wf_iter = nullptr;
     size_t bytes = 0;
@@ -130,6 +132,11 @@ __global__ void k_set_albedo(const float *alb, int n, float4 *mats) {
 __global__ void k_set_radiance(const float *rad, int n, float4 *em) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         em[i] = make_float4(rad[3 * i], rad[3 * i + 1], rad[3 * i + 2], 0.f);
+}
+
+__global__ void k_check_delays(const float *tau, int n, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (!(tau[i] >= 0.0f) || !isfinite(tau[i])) atomicOr(bad, 1);
 }
 
 __global__ void k_leaf_of(const float4 *tris, int n, int32_t *leaf_of) {
@@ -531,6 +538,41 @@ mt_status mt_scene_set_params(mt_scene s, const float *d_albedo, const float *d_
     if (d_medium_albedo)
         MT_CUDA_TRY(cudaMemcpyAsync(s->m_params, d_medium_albedo, sizeof(float), cudaMemcpyDeviceToDevice, st));
     MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+mt_status mt_scene_set_delays(mt_scene s, const float *d_tau, void *stream) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!d_tau) {
+        s->dev.delay = nullptr;
+        return MT_OK;
+    }
+    if (!s->delay_buf) MT_TRY(s->al.alloc(&s->delay_buf, (size_t)s->n_tris, "scattering delays"));
+    if (!s->check_flag) MT_TRY(s->al.alloc(&s->check_flag, 1, "scattering delays"));
+    int *dbad = s->check_flag;
+    MT_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), st));
+    k_check_delays<<<grid_for(s->n_tris, 256, s->num_sms), 256, 0, st>>>(d_tau, (int)s->n_tris, dbad);
+    MT_CUDA_TRY(cudaGetLastError());
+    int hbad = 0;
+    MT_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));
+    MT_CHECK_ARG(hbad == 0, "scattering delays must be finite and >= 0");
+    MT_CUDA_TRY(cudaMemcpyAsync(s->delay_buf, d_tau, (size_t)s->n_tris * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    MT_CUDA_TRY(cudaStreamSynchronize(st));  // the caller may release d_tau on return
+    s->dev.delay = s->delay_buf;
+    return MT_OK;
+}
+
+mt_status mt_scene_set_pulse(mt_scene s, uint32_t shape, float a, float b) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    MT_CHECK_ARG(shape <= MT_PULSE_EXPONENTIAL, "unknown pulse shape %u", shape);
+    MT_CHECK_ARG(std::isfinite(a) && std::isfinite(b), "pulse parameters must be finite");
+    MT_CHECK_ARG(!((shape == MT_PULSE_BOX || shape == MT_PULSE_EXPONENTIAL) && !(a > 0.f)), "pulse width must be > 0");
+    MT_CHECK_ARG(!(shape == MT_PULSE_GAUSSIAN && !(b > 0.f)), "pulse deviation must be > 0");
+    s->dev.pulse_type = (int32_t)shape;
+    s->dev.pulse_a = a;
+    s->dev.pulse_b = b;
     return MT_OK;
 }
 

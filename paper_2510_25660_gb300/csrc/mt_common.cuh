@@ -63,6 +63,8 @@ __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 0x1p
 #define G_SCATTER 1u
 #define G_TRACK 0x100u
 #define G_RATIO 0x10000u
+#define G_DELAY 0x20000u  // scattering delay at a surface vertex
+#define G_PULSE 0x20010u  // emission time of a contribution (+ kind)
 
 struct Rng {
     uint32_t k0, k1;
@@ -272,6 +274,10 @@ struct DevScene {
     int32_t n_tris;
     int32_t n_em;
     int32_t has_medium;
+    // time-resolved materials and sources (Sec. 4.1 scattering delays; Sec. 3 emission pulse)
+    const float *delay;    // per original triangle: exponential delay mean (m), nullptr = none
+    int32_t pulse_type;    // MT_PULSE_*
+    float pulse_a, pulse_b;
     float3 cam_o, cam_f, cam_r, cam_u;
     float tan_half;
     float3 q_lo, q_scale;  // BVH plane quantisation: plane = q_lo + q * q_scale
@@ -286,6 +292,32 @@ struct DevScene {
 };
 
 __device__ __forceinline__ void raise_err(const DevScene &s, uint32_t bit) { atomicOr(s.err, bit); }
+
+// exponential draw of mean `mean` from one Philox word (1 - u > 0)
+__device__ __forceinline__ float exp_draw(float mean, uint32_t x) { return -mean * logf(1.0f - u24(x)); }
+
+// scattering delay of a surface vertex on original triangle `orig` (0 without delays)
+__device__ __forceinline__ float vertex_delay(const DevScene &s, int orig, uint32_t pix, uint32_t smp, uint32_t depth,
+                                              uint32_t k0, uint32_t k1) {
+    if (!s.delay) return 0.0f;
+    const float tau = __ldg(&s.delay[orig]);
+    if (!(tau > 0.0f)) return 0.0f;
+    return exp_draw(tau, philox4x32_10(make_uint4(pix, smp, depth, G_DELAY), k0, k1).x);
+}
+
+// emission time of one contribution (kind 0 = found at vertex `depth`, 1 = next-event there):
+// box [0, a), Gaussian (a, b) by Box-Muller, exponential of mean a; 0 for a delta pulse
+__device__ __forceinline__ float pulse_time(const DevScene &s, uint32_t pix, uint32_t smp, uint32_t depth, int kind,
+                                            uint32_t k0, uint32_t k1) {
+    if (s.pulse_type == 0) return 0.0f;
+    const uint4 R = philox4x32_10(make_uint4(pix, smp, depth, G_PULSE + (uint32_t)kind), k0, k1);
+    switch (s.pulse_type) {
+    case 1: return s.pulse_a * u24(R.x);
+    case 2: return s.pulse_a + s.pulse_b * sqrtf(-2.0f * logf(1.0f - u24(R.x))) * cospif(2.0f * u24(R.y));
+    case 3: return exp_draw(s.pulse_a, R.x);
+    default: return 0.0f;
+    }
+}
 
 // Add v to addr[0..n) (shared or global memory).  With aggregate set, the
 // lanes of the warp that target the same address first sum their values with

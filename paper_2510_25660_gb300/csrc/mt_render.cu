@@ -147,6 +147,8 @@ struct Tracer {
     // kind 0 = found by the path at vertex `vert`, kind 1 = next-event at `vert`
     __device__ __forceinline__ void deposit(PathState &ps, int vert, int kind, int tri, float opl, float3 c,
                                             float3 cb, int em, float3 own_r) {
+        // the source emitted this contribution's light at a time drawn from its pulse
+        opl += pulse_time(s, ps.pix, ps.smp, (uint32_t)vert, kind, rng.k0, rng.k1);
         const float x = (opl - p.start) / p.width;
         const bool in = x >= 0.f && x < (float)p.T;
         const int bin = in ? (int)x : -1;
@@ -426,6 +428,8 @@ struct Tracer {
             deposit(ps, ps.depth, 0, orig, ps.opl, c, cb, em, f3(0.f, 0.f, 0.f));
         }
         if (ps.depth == p.max_depth) return false;
+        // scattering delay of this vertex: every later contribution carries it
+        ps.opl += vertex_delay(s, orig, ps.pix, ps.smp, (uint32_t)ps.depth, rng.k0, rng.k1);
         const float3 n = cwo >= 0.f ? ng : -ng;
         float3 tb, bb;
         onb(n, tb, bb);

@@ -349,13 +349,16 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     if (depth > 1) w = mis2w(d4.w, (U.v1.w / U.v0.w) * th * th / cwo);
                     const int em = __float_as_int(U.v2.w);
                     const float3 c = mul(beta * w, xyz(s.em_rad[em])) * p.scale;
-                    wf_splat(p, pix, opl, c);
+                    const float oc = opl + pulse_time(s, pix, smp, (uint32_t)depth, 0, p.k0, p.k1);
+                    wf_splat(p, pix, oc, c);
                     contribs++;
-                    if (DUMP) wf_dump(p, pix, smp, depth, 0, orig, opl, c);
+                    if (DUMP) wf_dump(p, pix, smp, depth, 0, orig, oc, c);
                 }
                 if (depth == p.max_depth) {
                     done = true;
                 } else {
+                    // scattering delay of this vertex: every later contribution carries it
+                    opl += vertex_delay(s, orig, pix, smp, (uint32_t)depth, p.k0, p.k1);
                     const float3 nn = cwo >= 0.f ? ng : -ng;
                     float3 tb, bb;
                     onb(nn, tb, bb);
@@ -393,7 +396,9 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                             if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
                                 shadow = true;
                                 sh_o = make_float4(xo.x, xo.y, xo.z, dist - (is_pt ? 0.0f : eps_of(y)));
-                                sh_d = make_float4(wi.x, wi.y, wi.z, opl + dist);
+                                sh_d = make_float4(wi.x, wi.y, wi.z,
+                                                   opl + dist + pulse_time(s, pix, smp, (uint32_t)depth, 1, p.k0,
+                                                                           p.k1));
                                 sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
                                 sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
                             }
