@@ -680,6 +680,11 @@ typedef struct {
     /* backward inputs/outputs */
     const double *gfilm, *gsteady;
     double *galb, *grad, *gmed;
+    /* forward-mode derivative: tangent direction of the parameters; film and
+     * steady then receive dC = sum over vertices of C * ratio * dtheta + Cbar * dLe */
+    int tangent;
+    const double *dalb, *drad;
+    double dmed;
     uint64_t cnt[4];
 } ctx_t;
 
@@ -708,6 +713,25 @@ static void deposit(ctx_t *cx, int32_t pix_full, int32_t lp, int32_t sample, int
     int32_t bin = (fb < -1e9) ? -1000000000 : (fb > 1e9 ? 1000000000 : (int32_t)fb);
     int in = bin >= 0 && bin < a->T;
     cx->cnt[2]++;
+    if (cx->tangent) {
+        /* C is a product of per-vertex factors: dC = C * sum_v (dfactor_v / factor_v) dtheta_v,
+         * plus Cbar dLe for the emitter (C is linear in its radiance) */
+        double dc[3];
+        for (int k = 0; k < 3; k++) {
+            double sum = 0.0;
+            for (int v = 1; v <= nv; v++) {
+                const double *r = (v == nv && own_ratio) ? own_ratio : vl->ratio[v];
+                double dth = vl->tri[v] >= 0 ? (cx->dalb ? cx->dalb[(int64_t)vl->tri[v] * 3 + k] : 0.0) : cx->dmed;
+                sum += r[k] * dth;
+            }
+            dc[k] = c[k] * sum + (em >= 0 && cx->drad ? cbar[k] * cx->drad[(int64_t)em * 3 + k] : 0.0);
+        }
+        for (int k = 0; k < 3; k++) {
+            if (in) cx->film[((int64_t)lp * a->T + bin) * 3 + k] += dc[k];
+            if (cx->steady) cx->steady[(int64_t)lp * 3 + k] += dc[k];
+        }
+        return;
+    }
     if (!cx->backward) {
         /* frequency space (Sec. 4.3, Eq. 12): C * exp(-i * 2 pi * tof / lambda) per wavelength */
         for (int32_t q = 0; q < cx->K; q++) {
@@ -1084,6 +1108,33 @@ int mo_render_backward(const mo_scene *s, const mo_args *a, const double *grad_f
     for (int64_t i = 0; i < ne * 3; i++) grad_radiance[i] += gr[i] * sc;
     if (grad_medium_albedo) *grad_medium_albedo += gm * sc;
     free(ga); free(gr);
+    return 0;
+}
+
+/* Forward-mode derivative (Sec. 4.4, forward mode): the film of
+ * dI/dtheta . dtheta for one tangent direction over per-triangle albedos
+ * (dalb [n][3], NULL = 0), emitter radiances (drad [n_em][3], NULL = 0) and
+ * the medium albedo (dmed).  tfilm / tsteady are crop-sized like mo_render's
+ * film / steady and are overwritten (accumulated with MO_ACCUMULATE). */
+int mo_render_tangent(const mo_scene *s, const mo_args *a, const double *dalb, const double *drad, double dmed,
+                      double *tfilm, double *tsteady) {
+    ctx_t cx;
+    memset(&cx, 0, sizeof(cx));
+    cx.s = s; cx.a = a; cx.tangent = 1;
+    cx.dalb = dalb; cx.drad = drad; cx.dmed = dmed;
+    cx.film = tfilm; cx.steady = tsteady;
+    int64_t npx = (int64_t)(a->x1 - a->x0) * (a->y1 - a->y0);
+    if (!(a->flags & MO_ACCUMULATE)) {
+        memset(tfilm, 0, sizeof(double) * (size_t)(npx * a->T * 3));
+        if (tsteady) memset(tsteady, 0, sizeof(double) * (size_t)(npx * 3));
+    }
+    int rc = run(&cx);
+    if (rc) return rc;
+    if (!(a->flags & MO_ACCUMULATE) && a->spp > 0) {
+        double sc = 1.0 / a->spp;
+        for (int64_t i = 0; i < npx * a->T * 3; i++) tfilm[i] *= sc;
+        if (tsteady) for (int64_t i = 0; i < npx * 3; i++) tsteady[i] *= sc;
+    }
     return 0;
 }
 

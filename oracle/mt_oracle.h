@@ -112,6 +112,8 @@ int mo_render(const mo_scene *s, const mo_args *a, double *film, double *steady,
               mo_contrib *dump, int64_t dump_cap, int64_t *n_dump, uint64_t *counters);
 int mo_render_phasor(const mo_scene *s, const mo_args *a, const double *lambdas, int32_t K, double *phasor,
                      double *steady);
+int mo_render_tangent(const mo_scene *s, const mo_args *a, const double *dalb, const double *drad, double dmed,
+                      double *tfilm, double *tsteady);
 int mo_render_backward(const mo_scene *s, const mo_args *a, const double *grad_film,
                        const double *grad_steady, double *grad_albedo, double *grad_radiance,
                        double *grad_medium_albedo);

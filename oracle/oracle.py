@@ -96,6 +96,8 @@ def lib():
         _lib.mo_render.argtypes = [P, P, P, P, P, P, C.c_int64, P, P]
         _lib.mo_render_phasor.restype = C.c_int
         _lib.mo_render_phasor.argtypes = [P, P, P, C.c_int32, P, P]
+        _lib.mo_render_tangent.restype = C.c_int
+        _lib.mo_render_tangent.argtypes = [P, P, P, P, C.c_double, P, P]
         _lib.mo_render_backward.restype = C.c_int
         _lib.mo_render_backward.argtypes = [P, P, P, P, P, P, P]
         _lib.mo_render_nlos.restype = C.c_int
@@ -241,6 +243,19 @@ class OracleScene:
             out["n_dump"] = nd.value
         del npx
         return out
+
+    def render_tangent(self, H, W, T, start, width, spp, seed, max_depth, dalb=None, drad=None, dmed=0.0, flags=0,
+                       sample_offset=0, crop=None):
+        """Forward-mode derivative film dI/dtheta . dtheta (crop-sized) and its steady image."""
+        x0, x1, y0, y1 = crop if crop is not None else (0, W, 0, H)
+        film = np.zeros((y1 - y0, x1 - x0, T, 3), np.float64)
+        steady = np.zeros((y1 - y0, x1 - x0, 3), np.float64)
+        a = Args(H, W, T, start, width, flags, spp, seed, max_depth, sample_offset, x0, x1, y0, y1, STRAT_MIS)
+        da = None if dalb is None else np.ascontiguousarray(dalb, np.float64).reshape(-1)
+        dr = None if drad is None else np.ascontiguousarray(drad, np.float64).reshape(-1)
+        if lib().mo_render_tangent(self.h, C.byref(a), _p(da), _p(dr), float(dmed), _p(film), _p(steady)):
+            raise ValueError("oracle tangent render: invalid arguments")
+        return dict(film=film, steady=steady)
 
     def render_phasor(self, H, W, lambdas, spp, seed, max_depth, flags=0, sample_offset=0, crop=None):
         """Frequency-space film [h, w, K, 2 (re, im), 3] (Sec. 4.3) and the steady image."""

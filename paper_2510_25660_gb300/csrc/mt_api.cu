@@ -746,6 +746,8 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     const int fetch_k = (int)((cfg.options >> 8) & 0xFFu);
     w.dynamic_fetch = (cfg.options & MT_OPT_DYNAMIC_FETCH) ? (fetch_k ? std::min(fetch_k, 32) : 8) : 0;
     w.wide = (cfg.options & MT_OPT_WIDE_BVH) ? 1 : 0;
+    w.lambdas = rp.lambdas;
+    w.K = rp.lambdas ? rp.K : 0;
     w.sort_rays = sort_rays ? 1 : 0;
     w.sort_keys = s->wf_sk;
     w.sort_keys_out = s->wf_sko;
@@ -819,7 +821,7 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
-    if ((mode == 0 || mode == 1) && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
+    if ((mode == 0 || mode == 1 || mode == 3) && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
         return render_wavefront(s, f, p, cfg, mode == 1, st);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
     s->launches += 1;

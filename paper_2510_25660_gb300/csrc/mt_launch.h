@@ -77,6 +77,8 @@ struct WfParams {
     unsigned long long *dump_count;
     int32_t dynamic_fetch;         // 0: off; else idle lanes of a warp that trigger a fetch (1..32)
     int32_t wide;                  // traverse the 8-wide BVH
+    const float *lambdas;          // frequency-space film: K wavelengths (m), the film has T = 2K; K = 0: bins
+    int32_t K;
     // ray reordering: extension rays sorted by (direction octant, origin Morton code)
     int32_t sort_rays;
     uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue

@@ -8,10 +8,13 @@ from gpu_util import build_and_load, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def test_phasor_matches_oracle(oracle_mod, scenes_mod):
+@pytest.mark.parametrize("form", ["megakernel", "wavefront"])
+def test_phasor_matches_oracle(oracle_mod, scenes_mod, form):
     api = build_and_load()
     sc = scenes_mod.cornell_box()
     s = api.Scene(sc)
+    if form == "wavefront":
+        s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
     lam = np.array([0.2, 0.133, 0.066])
     ph, st = api.render_phasor(s, 64, 64, lam, spp=8, seed=3, max_depth=4)
     s.sync()
