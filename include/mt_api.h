@@ -179,6 +179,21 @@ mt_status mt_render_nlos(mt_scene scene, mt_film film, const mt_scan *scan, int3
 mt_status mt_render_phasor(mt_scene scene, mt_film film, const float *d_lambdas, int32_t K, int32_t spp,
                            uint64_t seed, int32_t max_depth, uint64_t sample_offset, void *stream);
 
+/* Forward-mode derivative (Sec. 4.4, forward mode): the film of
+ * dI/dtheta . dtheta for one direction dtheta in parameter space, i.e. the
+ * time-resolved derivative of the image along that direction, with the same
+ * paths as mt_render (same seed and sample_offset).  Parameters as in
+ * mt_render_backward: d_dalbedo device float32 [n_tris][3] (input triangle
+ * order) or NULL, d_dradiance device float32 [n_emitters][3] or NULL, dmedium
+ * the medium-albedo component (ignored without a medium).  The film (C = 3)
+ * and its steady image receive the tangent; same flags, ownership and errors
+ * as mt_render.  Each contribution C adds C * sum_v ratio_v * dtheta_v over
+ * its vertices plus Cbar * dLe: exact for the estimator (no finite
+ * differences), the transpose of mt_render_backward. */
+mt_status mt_render_tangent(mt_scene scene, mt_film film, const float *d_dalbedo, const float *d_dradiance,
+                            float dmedium, int32_t spp, uint64_t seed, int32_t max_depth, uint64_t sample_offset,
+                            void *stream);
+
 /* Backward mode by path replay (Sec. 4.4, Eqs. 13-15): regenerate every path of
  * mt_render(scene, film, spp, seed, max_depth, sample_offset) from its Philox
  * key and add dL/dalbedo (device [n_tris][3]), dL/dradiance (device

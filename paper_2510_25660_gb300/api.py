@@ -83,6 +83,7 @@ SIGNATURES = {
     "mt_sync": (C.c_int, [_P, _P]),
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
     "mt_stage_times": (C.c_int, [_P, _P, _I32]),
+    "mt_render_tangent": (C.c_int, [_P, _P, _P, _P, C.c_float, _I32, _U64, _I32, _U64, _P]),
     "mt_scene_set_delays": (C.c_int, [_P, _P, _P]),
     "mt_scene_set_pulse": (C.c_int, [_P, _U32, C.c_float, C.c_float]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
@@ -187,6 +188,11 @@ def mt_scene_set_delays(scene, d_tau, stream):
 
 def mt_scene_set_pulse(scene, shape, a, b):
     return _call("mt_scene_set_pulse", scene, shape, a, b)
+
+
+def mt_render_tangent(scene, film, d_dalbedo, d_dradiance, dmedium, spp, seed, max_depth, sample_offset, stream):
+    return _call("mt_render_tangent", scene, film, d_dalbedo, d_dradiance, dmedium, spp, seed, max_depth,
+                 sample_offset, stream)
 
 
 def mt_stage_times(scene, out, reset):
@@ -372,6 +378,20 @@ def render_phasor(scene: Scene, H, W, lambdas, spp, seed, max_depth, sample_offs
     f = Film(film, steady, 0.0, 1.0, flags)
     mt_render_phasor(scene.h, f.h, _ptr(lam), K, spp, seed, max_depth, sample_offset, _stream(stream))
     return film.view(H, W, K, 2, 3), steady
+
+
+def render_tangent(scene: Scene, H, W, T, start, width, spp, seed, max_depth, dalbedo=None, dradiance=None,
+                   dmedium=0.0, sample_offset=0, flags=0, out=None, stream=None):
+    """Forward-mode derivative film dI/dtheta . dtheta [H, W, T, 3] and its
+    steady image for the tangent (dalbedo [n_tris, 3], dradiance [n_em, 3],
+    dmedium) on the same paths as render()."""
+    film, steady = out if out is not None else new_film(H, W, T, 3)
+    f = Film(film, steady, start, width, flags)
+    da = None if dalbedo is None else dalbedo.float().contiguous()
+    dr = None if dradiance is None else dradiance.float().contiguous()
+    mt_render_tangent(scene.h, f.h, _ptr(da), _ptr(dr), float(dmedium), spp, seed, max_depth, sample_offset,
+                      _stream(stream))
+    return film, steady
 
 
 def render_backward(scene: Scene, T, start, width, spp, seed, max_depth, grad_film, grad_steady=None,

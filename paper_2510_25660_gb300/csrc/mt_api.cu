@@ -769,7 +769,8 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
 static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
                                uint64_t sample_offset, int mode, const float *gfilm, const float *gsteady,
                                float *galb, float *grad, float *gmed, mt_contrib *dump, int64_t cap,
-                               int64_t *dcount, cudaStream_t st, const float *lambdas = nullptr, int32_t K = 0) {
+                               int64_t *dcount, cudaStream_t st, const float *lambdas = nullptr, int32_t K = 0,
+                               const float *dalb = nullptr, const float *drad = nullptr, float dmed = 0.f) {
     MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
     MT_CHECK_ARG(f->C == 3, "path-traced films have C = 3");
     MT_CHECK_ARG(spp >= 1, "spp must be >= 1");
@@ -817,6 +818,9 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     p.refill_min = std::max(1, std::min(32, (cfg.options >> 8) & 0xFF));
     p.lambdas = lambdas;
     p.K = K;
+    p.dalb = dalb;
+    p.drad = drad;
+    p.dmed = dmed;
     if (mode != 2 && D < f->T && !acc) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
@@ -841,6 +845,16 @@ mt_status mt_render_phasor(mt_scene s, mt_film f, const float *d_lambdas, int32_
     MT_CHECK_ARG(f->T == 2 * K && f->C == 3, "phasor films have T = 2K (real, imaginary) and C = 3");
     return render_common(s, f, spp, seed, max_depth, sample_offset, 3, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr, 0, nullptr, (cudaStream_t)stream, d_lambdas, K);
+}
+
+mt_status mt_render_tangent(mt_scene s, mt_film f, const float *d_dalbedo, const float *d_dradiance, float dmedium,
+                            int32_t spp, uint64_t seed, int32_t max_depth, uint64_t sample_offset, void *stream) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
+    MT_CHECK_ARG(std::isfinite(dmedium), "medium-albedo tangent must be finite");
+    MT_CHECK_ARG(f->C == 3, "tangent films have C = 3");
+    return render_common(s, f, spp, seed, max_depth, sample_offset, 4, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, 0, nullptr, (cudaStream_t)stream, nullptr, 0, d_dalbedo, d_dradiance,
+                         s->dev.has_medium ? dmedium : 0.f);
 }
 
 mt_status mt_render_backward(mt_scene s, mt_film f, const float *d_grad_film, const float *d_grad_steady, int32_t spp,

@@ -28,6 +28,8 @@ struct RenderParams {
     int32_t refill_min;        // idle lanes needed before a warp starts new paths (1..32)
     const float *lambdas;      // frequency-space film: K wavelengths (m); the film has T = 2K
     int32_t K;
+    const float *dalb, *drad;  // forward-mode derivative: tangent of albedos [n][3] and radiances [e][3] (or null)
+    float dmed;                // and of the medium albedo
 };
 
 struct NlosParams {

@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2, MODE_PHASOR = 3;
+constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2, MODE_PHASOR = 3, MODE_TAN = 4;
 
 // CTAs of 256 threads the register allocation must leave room for per SM: 4
 // (64 registers) measured fastest on GB300 for the large scene (205 ms against
@@ -47,6 +47,8 @@ struct PathState {
     int depth, lp;
     uint32_t pix, smp;
     float3 acc;     // steady-image sum of this path (forward)
+    float3 sig;     // forward-mode derivative: sum over earlier vertices of ratio * dtheta
+    float3 dv;      // forward-mode derivative: dtheta of the current vertex
 };
 
 struct Counters {
@@ -155,6 +157,13 @@ struct Tracer {
         c = c * p.scale;
         cb = cb * p.scale;
         cnt.contribs++;
+        if (MODE == MODE_TAN) {
+            // forward-mode derivative (Sec. 4.4): dC = C * (sum of ratio * dtheta over the
+            // vertices, the next-event's own term included) + Cbar * dLe; splatted like C
+            float3 dc = mul(c, ps.sig + own_r);
+            if (p.drad) dc = dc + mul(cb, f3(p.drad[em * 3], p.drad[em * 3 + 1], p.drad[em * 3 + 2]));
+            c = dc;
+        }
         if (MODE == MODE_PHASOR) {
             // frequency space (Sec. 4.3, Eq. 12): C exp(-i 2 pi opl / lambda) per wavelength;
             // "bin" 2q holds the real part, 2q + 1 the imaginary part
@@ -248,6 +257,8 @@ struct Tracer {
         ps.prev_pdf = 0.f;
         ps.depth = 1;
         ps.acc = f3(0.f, 0.f, 0.f);
+        ps.sig = f3(0.f, 0.f, 0.f);
+        ps.dv = f3(0.f, 0.f, 0.f);
         cnt.paths++;
         if (MODE == MODE_BWD) vr[0].tri = -2;
     }
@@ -340,6 +351,7 @@ struct Tracer {
                 if (!MEDIA) w = mis2(pA * dist * dist / cy, pb);
             }
             if (MODE == MODE_BWD) own = bsdf_dratio(m, wol, wil);
+            if (MODE == MODE_TAN) own = mul(bsdf_dratio(m, wol, wil), ps.dv);
         } else {
             const float ph = hg_eval(s.m_params[1], dot(ps.d, wi));
             fc = f3(ph, ph, ph);
@@ -348,6 +360,7 @@ struct Tracer {
                 const float ia = 1.0f / s.m_params[0];
                 own = f3(ia, ia, ia);
             }
+            if (MODE == MODE_TAN) own = ps.dv;  // (1 / albedo) * dalbedo, set at the vertex
         }
         const float k = geo * w * Tr;
         const float3 cb = mul(ps.beta, fc) * k;
@@ -396,10 +409,15 @@ struct Tracer {
                         const float ia = 1.0f / alb;
                         vr[ps.depth].r = f3(ia, ia, ia);
                     }
+                    if (MODE == MODE_TAN) {
+                        const float dr = p.dmed / alb;
+                        ps.dv = f3(dr, dr, dr);
+                    }
                     if (ps.depth == p.max_depth) return false;
                     if (s.n_units > 0) nee(ps, x, false, f3(0, 0, 1), f3(1, 0, 0), f3(0, 1, 0), f3(0, 0, 1), Mat{});
                     const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
                     ps.d = hg_sample(s.m_params[1], ps.d, u24(R.x), u24(R.y));
+                    if (MODE == MODE_TAN) ps.sig = ps.sig + ps.dv;
                     ps.o = x;
                     ps.depth++;
                     return true;
@@ -415,6 +433,9 @@ struct Tracer {
         const float3 wo = -ps.d;
         const float cwo = dot(ng, wo);
         const int unit = __ldg(&s.tri_unit[orig]);
+        // the vertex is recorded before anything can end the path here, so that light
+        // found at the last vertex still reaches the earlier vertices' gradients
+        if (MODE == MODE_BWD) vr[ps.depth].tri = orig;
         if (unit >= 0 && cwo > 0.f && (ps.depth == 1 || !MEDIA)) {
             const LightUnit U = s.units[unit];
             float w = 1.0f;
@@ -436,7 +457,8 @@ struct Tracer {
         const float3 wol = to_local(wo, tb, bb, n);
         const float4 mm = __ldg(&s.mats[orig]);
         const Mat m{xyz(mm), mm.w};
-        if (MODE == MODE_BWD) vr[ps.depth].tri = orig;
+        if (MODE == MODE_TAN)
+            ps.dv = p.dalb ? f3(p.dalb[orig * 3], p.dalb[orig * 3 + 1], p.dalb[orig * 3 + 2]) : f3(0.f, 0.f, 0.f);
         if (s.n_units > 0) nee(ps, x, true, n, tb, bb, wol, m);
         const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
         float3 wil;
@@ -447,6 +469,7 @@ struct Tracer {
         if (!(pb > 0.f)) return false;
         ps.beta = mul(ps.beta, f) * (wil.z / pb);
         if (MODE == MODE_BWD) vr[ps.depth].r = bsdf_dratio(m, wol, wil);
+        if (MODE == MODE_TAN) ps.sig = ps.sig + mul(bsdf_dratio(m, wol, wil), ps.dv);
         ps.prev_pdf = pb;
         ps.o = x + n * eps_of(x);
         ps.d = to_world(wil, tb, bb, n);
@@ -614,6 +637,11 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
     if (mode == 0) { MT_DISPATCH(MODE_FWD) }
     if (mode == 1) { MT_DISPATCH(MODE_DUMP) }
     if (mode == 3) { MT_DISPATCH(MODE_PHASOR) }
+    if (mode == 4) {
+        // forward-mode derivative: no counting or aggregating variants
+        return media ? launch_one<MODE_TAN, true, false, false>(s, p, cfg, st)
+                     : launch_one<MODE_TAN, false, false, false>(s, p, cfg, st);
+    }
     MT_DISPATCH(MODE_BWD)
 #undef MT_DISPATCH
 }

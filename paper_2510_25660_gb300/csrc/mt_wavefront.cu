@@ -57,21 +57,26 @@ __device__ __forceinline__ uint32_t wf_append(uint32_t *count, bool want) {
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// frequency space (Sec. 4.3, Eq. 12): C exp(-i 2 pi opl / lambda); "bin" 2q real, 2q + 1 imaginary.
+// Out of line so that its registers do not weigh on the time-binned path.
+__device__ __noinline__ void wf_splat_phasor(const WfParams &p, uint32_t pix, float opl, float3 c) {
+    for (int q = 0; q < p.K; ++q) {
+        float sn, cs;
+        sincospif(2.0f * opl / __ldg(&p.lambdas[q]), &sn, &cs);
+        float *h = p.film + ((size_t)pix * p.T + 2 * q) * 3;
+        red_add_stream(h, c.x * cs);
+        red_add_stream(h + 1, c.y * cs);
+        red_add_stream(h + 2, c.z * cs);
+        red_add_stream(h + 3, -c.x * sn);
+        red_add_stream(h + 4, -c.y * sn);
+        red_add_stream(h + 5, -c.z * sn);
+    }
+}
+
 __device__ __forceinline__ void wf_splat(const WfParams &p, uint32_t pix, float opl, float3 c) {
     const float x = (opl - p.start) / p.width;
     if (p.K > 0) {
-        // frequency space (Sec. 4.3, Eq. 12): C exp(-i 2 pi opl / lambda); "bin" 2q real, 2q + 1 imaginary
-        for (int q = 0; q < p.K; ++q) {
-            float sn, cs;
-            sincospif(2.0f * opl / __ldg(&p.lambdas[q]), &sn, &cs);
-            float *h = p.film + ((size_t)pix * p.T + 2 * q) * 3;
-            red_add_stream(h, c.x * cs);
-            red_add_stream(h + 1, c.y * cs);
-            red_add_stream(h + 2, c.z * cs);
-            red_add_stream(h + 3, -c.x * sn);
-            red_add_stream(h + 4, -c.y * sn);
-            red_add_stream(h + 5, -c.z * sn);
-        }
+        wf_splat_phasor(p, pix, opl, c);
     } else if (x >= 0.f && x < (float)p.T) {
         float *h = p.film + ((size_t)pix * p.T + (int)x) * 3;
         red_add_stream(h, c.x);

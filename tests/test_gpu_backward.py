@@ -57,6 +57,31 @@ def test_gradient_matches_oracle(setup):
     assert np.allclose(gr.cpu().numpy()[:1], ref["radiance"], rtol=0.02)
 
 
+@pytest.mark.parametrize("which", ["steady", "film"])
+def test_gradient_per_term_matches_oracle_tightly(setup, which):
+    """Random dL/dsteady (every contribution, also those outside the time
+    window, e.g. light found at the last vertex) or random dL/dfilm alone:
+    the replay's albedo and radiance gradients equal the oracle's to FP32
+    accuracy, not merely within a few percent."""
+    import torch
+    api, sc, s, osc = setup
+    spp, seed, depth = 4, 77, 4
+    gen = torch.Generator("cuda").manual_seed(2)
+    gf = torch.randn((H, W, T, 3), device="cuda", generator=gen)
+    gs = torch.randn((H, W, 3), device="cuda", generator=gen)
+    if which == "steady":
+        gf.zero_()
+    else:
+        gs.zero_()
+    ga, gr, gm = api.render_backward(s, T, START, WIDTH, spp, seed, depth, gf, gs)
+    s.sync()
+    ref = osc.render_backward(H, W, T, START, WIDTH, spp, seed, depth, gf.cpu().numpy().astype(np.float64),
+                              gs.cpu().numpy().astype(np.float64))
+    ra = ref["albedo"]
+    assert np.linalg.norm(ga.cpu().numpy() - ra) < 2e-3 * np.linalg.norm(ra)
+    assert np.linalg.norm(gr.cpu().numpy()[:1] - ref["radiance"]) < 2e-3 * np.linalg.norm(ref["radiance"])
+
+
 def test_gradient_matches_gpu_finite_differences(setup):
     import torch
     api, sc, s, osc = setup
