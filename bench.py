@@ -649,6 +649,16 @@ def secondary(api, autotune, scenes):
                        "ms_per_backward": ms, "forward_ms": fwd0.elapsed_time(fwd1) / 3,
                        "params_per_s": sc.n_tris * 3 / (ms / 1000.0),
                        "workload": "97k-triangle scene, 256x256x512 film, 64 spp, max_depth 8"}
+    # forward-mode derivative film on the same scene and paths (tangent over every albedo)
+    dalb = torch.randn((sc.n_tris, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    tfilm, tsteady = api.new_film(f.H, f.W, f.T)
+    tms = _timed(lambda: api.render_tangent(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8, dalb, None,
+                                            out=(tfilm, tsteady)), 3)
+    s.sync()
+    out["tangent"] = {"vertices_per_s": c["vertices"] / 3 / (tms / 1000.0), "ms_per_tangent": tms,
+                      "workload": "97k-triangle scene, 256x256x512 film, 64 spp, max_depth 8, one tangent "
+                                  "direction over all albedos (forward mode)"}
+    del tfilm, tsteady
     del s
     # NLOS confocal 64x64 x 1024 spp, T=4096
     sc = scenes.nlos_scene()
