@@ -10,6 +10,7 @@
  */
 #include "mt_oracle.h"
 
+#include <complex.h>
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
@@ -1134,6 +1135,272 @@ int mo_render_tangent(const mo_scene *s, const mo_args *a, const double *dalb, c
         double sc = 1.0 / a->spp;
         for (int64_t i = 0; i < npx * a->T * 3; i++) tfilm[i] *= sc;
         if (tsteady) for (int64_t i = 0; i < npx * 3; i++) tsteady[i] *= sc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Transient polarization (Sec. 4.2, "Transient polarization tracking"):      */
+/* a Stokes vector (S0..S3) per colour channel and time bin.                  */
+/*                                                                            */
+/* Conventions: a Stokes vector of light propagating along k is given in a    */
+/* reference frame x (unit, perpendicular to k), y = k x x; S1 = I_x - I_y,   */
+/* S2 = I(+45) - I(-45).  Expressing it in a frame x' = cos(t) x + sin(t) y   */
+/* multiplies it by R(t) (rows 1, 2 rotated by 2t).  The throughput of a path */
+/* is a 4x4 Mueller matrix per channel mapping light leaving the current      */
+/* vertex toward the camera (in the segment's frame) to the Stokes vector the */
+/* camera measures (frame x = the camera's horizontal axis).  Emitters emit   */
+/* unpolarised light.  Lambert is an ideal depolariser; the GGX conductor     */
+/* reflects at its microfacet with the Fresnel Mueller matrix of a complex    */
+/* index 1 + i kappa, kappa = 2 sqrt(F0 / (1 - F0)) (normal-incidence         */
+/* reflectance F0), in the s/p frames of the scattering plane.                */
+/* ------------------------------------------------------------------------- */
+typedef struct { double m[4][4]; } mat4;
+
+static mat4 m4_ident(double v) {
+    mat4 r;
+    memset(&r, 0, sizeof(r));
+    for (int i = 0; i < 4; i++) r.m[i][i] = v;
+    return r;
+}
+static mat4 m4_mul(const mat4 *a, const mat4 *b) {
+    mat4 r;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; k++) acc += a->m[i][k] * b->m[k][j];
+            r.m[i][j] = acc;
+        }
+    return r;
+}
+static mat4 m4_scale(const mat4 *a, double v) {
+    mat4 r;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) r.m[i][j] = a->m[i][j] * v;
+    return r;
+}
+/* Stokes rotation into a frame turned by t about the propagation direction */
+static mat4 m4_rot(double t) {
+    mat4 r = m4_ident(1.0);
+    double c = cos(2.0 * t), s = sin(2.0 * t);
+    r.m[1][1] = c; r.m[1][2] = s;
+    r.m[2][1] = -s; r.m[2][2] = c;
+    return r;
+}
+/* angle t with x_to = cos t x_from + sin t (k x x_from) */
+static double frame_angle(v3 k, v3 x_from, v3 x_to) {
+    return atan2(dot(x_to, cross(k, x_from)), dot(x_to, x_from));
+}
+/* unit vector perpendicular to the plane of a and b, or to a alone when they are parallel */
+static v3 plane_normal(v3 a, v3 b) {
+    v3 c = cross(a, b);
+    double l = len(c);
+    if (l > 1e-12) return scl(c, 1.0 / l);
+    v3 t, bb;
+    basis(a, &t, &bb);
+    return t;
+}
+/* Fresnel reflection Mueller matrix at incidence cosine ci, index 1 + i kappa, in s/p frames */
+static mat4 fresnel_mueller(double ci, double kappa) {
+    double complex N = 1.0 + I * kappa;
+    double s2 = 1.0 - ci * ci;
+    double complex ct = csqrt(1.0 - s2 / (N * N));
+    double complex rs = (ci - N * ct) / (ci + N * ct);
+    double complex rp = (N * ci - ct) / (N * ci + ct);
+    double Rs = creal(rs * conj(rs)), Rp = creal(rp * conj(rp));
+    double complex X = rs * conj(rp);
+    mat4 m;
+    memset(&m, 0, sizeof(m));
+    m.m[0][0] = m.m[1][1] = 0.5 * (Rs + Rp);
+    m.m[0][1] = m.m[1][0] = 0.5 * (Rs - Rp);
+    m.m[2][2] = m.m[3][3] = creal(X);
+    m.m[2][3] = cimag(X);
+    m.m[3][2] = -cimag(X);
+    return m;
+}
+double mo_conductor_kappa(double F0) {
+    double f = F0 < 0.0 ? 0.0 : (F0 > 0.999 ? 0.999 : F0);
+    return 2.0 * sqrt(f / (1.0 - f));
+}
+/* Mueller matrix of one surface vertex for light arriving along -wi (world) and
+ * leaving along -d toward the camera, in the frame s = plane normal of (wi, d)
+ * for both; scalar factors D G2 / (4 cos cos) included, cosine and pdf not */
+static void vertex_mueller(uint32_t ty, const double *alb, double rgh, v3 wol, v3 wil, mat4 M[3]) {
+    if (ty == 0) {
+        for (int c = 0; c < 3; c++) { memset(&M[c], 0, sizeof(mat4)); M[c].m[0][0] = alb[c] / PI_D; }
+        return;
+    }
+    double a = ggx_alpha(rgh);
+    v3 h = nrm(add(wol, wil));
+    double D = ggx_D(a, h);
+    double G2 = 1.0 / (1.0 + ggx_lambda(a, wol) + ggx_lambda(a, wil));
+    double k = D * G2 / (4.0 * wol.z * wil.z);
+    double cd = dot(wil, h);
+    for (int c = 0; c < 3; c++) {
+        mat4 F = fresnel_mueller(cd, mo_conductor_kappa(alb[c]));
+        M[c] = m4_scale(&F, k);
+    }
+}
+
+typedef struct {
+    const mo_scene *s;
+    const mo_args *a;
+    double *film, *steady; /* [px][T][4][3], [px][4][3] */
+} pctx_t;
+
+static void pol_deposit(pctx_t *cx, int32_t pix_full, int32_t lp, int32_t sample, int depth, int kind, double opl,
+                        const double S[3][4]) {
+    const mo_args *a = cx->a;
+    if (cx->s->pulse_type != MO_PULSE_DELTA) {
+        double u[4];
+        rng4(a->seed, (uint32_t)pix_full, (uint32_t)sample, (uint32_t)depth, G_PULSE + (uint32_t)kind, u);
+        opl += pulse_time(cx->s, u);
+    }
+    double fb = floor((opl - a->start) / a->width);
+    int in = fb >= 0.0 && fb < (double)a->T;
+    for (int k = 0; k < 4; k++)
+        for (int c = 0; c < 3; c++) {
+            if (in) cx->film[(((int64_t)lp * a->T + (int64_t)fb) * 4 + k) * 3 + c] += S[c][k];
+            cx->steady[((int64_t)lp * 4 + k) * 3 + c] += S[c][k];
+        }
+}
+
+/* the same estimator as trace_path (surfaces only), with Mueller throughput */
+static void trace_path_pol(pctx_t *cx, int32_t px, int32_t py, int32_t lp, uint32_t smp) {
+    const mo_scene *s = cx->s;
+    const mo_args *a = cx->a;
+    uint32_t pix = (uint32_t)(py * a->W + px);
+    uint64_t seed = a->seed;
+    double u[4];
+    rng4(seed, pix, smp, 0, 0, u);
+    double jx = (a->flags & MO_PIXEL_CENTER) ? 0.5 : u[0];
+    double jy = (a->flags & MO_PIXEL_CENTER) ? 0.5 : u[1];
+    v3 o, d;
+    cam_ray(s, a->W, a->H, px, py, jx, jy, &o, &d);
+    mat4 P[3];
+    for (int c = 0; c < 3; c++) P[c] = m4_ident(1.0);
+    v3 xf = nrm(sub(s->cam_r, scl(d, dot(s->cam_r, d))));  /* frame of the current segment */
+    double opl = 0.0, prev_pdf = 0.0;
+    for (int depth = 1; depth <= a->max_depth; depth++) {
+        double th;
+        int64_t hit = closest(s, o, d, INFINITY, 0, &th);
+        if (hit < 0) return;
+        v3 x = add(o, scl(d, th));
+        if (!(depth == 1 && (a->flags & MO_UNWARP))) opl += th;
+        v3 wo = scl(d, -1.0);
+        v3 ng = s->ng[hit];
+        int32_t em = s->tri_em[hit];
+        if (em >= 0 && dot(ng, wo) > 0.0) {
+            double w = 1.0;
+            if (depth > 1) {
+                double pl = s->tri_lpdf[hit] * th * th / dot(ng, wo);
+                w = mis2(prev_pdf, pl);
+            }
+            double S[3][4];
+            for (int c = 0; c < 3; c++)
+                for (int k = 0; k < 4; k++) S[c][k] = P[c].m[k][0] * s->em_rad[3 * em + c] * w;
+            pol_deposit(cx, (int32_t)pix, lp, (int32_t)smp, depth, 0, opl, S);
+        }
+        if (depth == a->max_depth) return;
+        if (s->delay && s->delay[hit] > 0.0) {
+            rng4(seed, pix, smp, (uint32_t)depth, G_DELAY, u);
+            opl += -s->delay[hit] * log(1.0 - u[0]);
+        }
+        v3 n = side_normal(ng, wo), t, b;
+        basis(n, &t, &b);
+        v3 wol = to_local(wo, t, b, n);
+        const double *alb = s->albedo + 3 * hit;
+        uint32_t ty = s->type[hit];
+        double rgh = s->rough[hit];
+        if (s->n_units > 0) {
+            rng4(seed, pix, smp, (uint32_t)depth, G_NEE, u);
+            int64_t un = pick_unit(s, u[0]);
+            int32_t eml = s->unit_em[un];
+            int is_pt = s->unit_tri[un] < 0;
+            v3 y, ny = mk(0, 0, 0);
+            if (is_pt) y = s->em_pos[eml];
+            else { y = tri_point(s, s->unit_tri[un], u[1], u[2]); ny = s->ng[s->unit_tri[un]]; }
+            v3 xo = offset(x, n);
+            v3 dl = sub(y, xo);
+            double dist = len(dl);
+            v3 wi = scl(dl, 1.0 / dist);
+            double cx_ = dot(n, wi), cy = is_pt ? 1.0 : -dot(ny, wi);
+            if (cx_ > 0.0 && cy > 0.0) {
+                double tmax = dist - (is_pt ? 0.0 : eps_of(y));
+                if (!occluded(s, xo, wi, tmax, 0)) {
+                    v3 wil = to_local(wi, t, b, n);
+                    double f[3], pb;
+                    bsdf_local(ty, alb, rgh, wol, wil, f, &pb);
+                    if (pb > 0.0 || ty == 0) {
+                        double geo, w = 1.0;
+                        if (is_pt) geo = 1.0 / (dist * dist) / s->unit_p[un];
+                        else {
+                            double pA = s->unit_p[un] / s->area[s->unit_tri[un]];
+                            geo = cy / (dist * dist) / pA;
+                            w = mis2(pA * dist * dist / cy, pb);
+                        }
+                        mat4 Mv[3];
+                        vertex_mueller(ty, alb, rgh, wol, wil, Mv);
+                        v3 sv = plane_normal(wi, d);
+                        mat4 R = m4_rot(frame_angle(wo, sv, xf));
+                        double S[3][4];
+                        for (int c = 0; c < 3; c++) {
+                            mat4 A = m4_mul(&P[c], &R);
+                            mat4 B = m4_mul(&A, &Mv[c]);
+                            double k = cx_ * geo * w * s->em_rad[3 * eml + c];
+                            for (int q = 0; q < 4; q++) S[c][q] = B.m[q][0] * k;
+                        }
+                        pol_deposit(cx, (int32_t)pix, lp, (int32_t)smp, depth, 1, opl + dist, S);
+                    }
+                }
+            }
+        }
+        rng4(seed, pix, smp, (uint32_t)depth, G_SCATTER, u);
+        v3 wil;
+        if (!bsdf_sample_local(ty, rgh, wol, u[0], u[1], &wil)) return;
+        double f[3], pb;
+        bsdf_local(ty, alb, rgh, wol, wil, f, &pb);
+        if (pb <= 0.0) return;
+        v3 wi = to_world(wil, t, b, n);
+        mat4 Mv[3];
+        vertex_mueller(ty, alb, rgh, wol, wil, Mv);
+        v3 sv = plane_normal(wi, d);
+        mat4 R = m4_rot(frame_angle(wo, sv, xf));
+        for (int c = 0; c < 3; c++) {
+            mat4 A = m4_mul(&P[c], &R);
+            mat4 B = m4_mul(&A, &Mv[c]);
+            P[c] = m4_scale(&B, wil.z / pb);
+        }
+        xf = sv;
+        prev_pdf = pb;
+        o = offset(x, n);
+        d = wi;
+    }
+}
+
+/* Stokes film [crop px][T][4][3] and steady [crop px][4][3] (divided by spp
+ * unless MO_ACCUMULATE); scenes with a medium are rejected (returns 1). */
+int mo_render_polarized(const mo_scene *s, const mo_args *a, double *film, double *steady) {
+    if (s->has_medium) return 1;
+    if (a->x0 < 0 || a->x1 > a->W || a->y0 < 0 || a->y1 > a->H || a->x0 > a->x1 || a->y0 > a->y1) return 1;
+    if (a->max_depth > MO_MAX_DEPTH || a->max_depth < 1 || a->spp < 0 || a->T < 0) return 1;
+    pctx_t cx = {s, a, film, steady};
+    int64_t npx = (int64_t)(a->x1 - a->x0) * (a->y1 - a->y0);
+    if (!(a->flags & MO_ACCUMULATE)) {
+        memset(film, 0, sizeof(double) * (size_t)(npx * a->T * 12));
+        memset(steady, 0, sizeof(double) * (size_t)(npx * 12));
+    }
+    int cw = a->x1 - a->x0;
+    for (int py = a->y0; py < a->y1; py++)
+        for (int px = a->x0; px < a->x1; px++) {
+            int32_t lp = (py - a->y0) * cw + (px - a->x0);
+            for (int32_t sI = 0; sI < a->spp; sI++)
+                trace_path_pol(&cx, px, py, lp, (uint32_t)(a->sample_offset + (uint64_t)sI));
+        }
+    if (!(a->flags & MO_ACCUMULATE) && a->spp > 0) {
+        double sc = 1.0 / a->spp;
+        for (int64_t i = 0; i < npx * a->T * 12; i++) film[i] *= sc;
+        for (int64_t i = 0; i < npx * 12; i++) steady[i] *= sc;
     }
     return 0;
 }

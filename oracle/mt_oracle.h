@@ -112,6 +112,10 @@ int mo_render(const mo_scene *s, const mo_args *a, double *film, double *steady,
               mo_contrib *dump, int64_t dump_cap, int64_t *n_dump, uint64_t *counters);
 int mo_render_phasor(const mo_scene *s, const mo_args *a, const double *lambdas, int32_t K, double *phasor,
                      double *steady);
+/* Stokes film [crop px][T][4][3] and steady [crop px][4][3] (transient polarization) */
+int mo_render_polarized(const mo_scene *s, const mo_args *a, double *film, double *steady);
+/* conductor extinction coefficient of the polarized GGX model for a normal-incidence reflectance F0 */
+double mo_conductor_kappa(double F0);
 int mo_render_tangent(const mo_scene *s, const mo_args *a, const double *dalb, const double *drad, double dmed,
                       double *tfilm, double *tsteady);
 int mo_render_backward(const mo_scene *s, const mo_args *a, const double *grad_film,

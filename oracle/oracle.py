@@ -96,6 +96,10 @@ def lib():
         _lib.mo_render.argtypes = [P, P, P, P, P, P, C.c_int64, P, P]
         _lib.mo_render_phasor.restype = C.c_int
         _lib.mo_render_phasor.argtypes = [P, P, P, C.c_int32, P, P]
+        _lib.mo_render_polarized.restype = C.c_int
+        _lib.mo_render_polarized.argtypes = [P, P, P, P]
+        _lib.mo_conductor_kappa.restype = C.c_double
+        _lib.mo_conductor_kappa.argtypes = [C.c_double]
         _lib.mo_render_tangent.restype = C.c_int
         _lib.mo_render_tangent.argtypes = [P, P, P, P, C.c_double, P, P]
         _lib.mo_render_backward.restype = C.c_int
@@ -109,6 +113,11 @@ def lib():
 
 def _p(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def conductor_kappa(F0: float) -> float:
+    """Extinction coefficient of the polarized conductor model (index 1 + i kappa) for reflectance F0."""
+    return float(lib().mo_conductor_kappa(float(F0)))
 
 
 def philox(ctr, key) -> np.ndarray:
@@ -255,6 +264,16 @@ class OracleScene:
         dr = None if drad is None else np.ascontiguousarray(drad, np.float64).reshape(-1)
         if lib().mo_render_tangent(self.h, C.byref(a), _p(da), _p(dr), float(dmed), _p(film), _p(steady)):
             raise ValueError("oracle tangent render: invalid arguments")
+        return dict(film=film, steady=steady)
+
+    def render_polarized(self, H, W, T, start, width, spp, seed, max_depth, flags=0, sample_offset=0, crop=None):
+        """Stokes film [h, w, T, 4, 3] and steady Stokes image [h, w, 4, 3] (crop-sized)."""
+        x0, x1, y0, y1 = crop if crop is not None else (0, W, 0, H)
+        film = np.zeros((y1 - y0, x1 - x0, T, 4, 3), np.float64)
+        steady = np.zeros((y1 - y0, x1 - x0, 4, 3), np.float64)
+        a = Args(H, W, T, start, width, flags, spp, seed, max_depth, sample_offset, x0, x1, y0, y1, STRAT_MIS)
+        if lib().mo_render_polarized(self.h, C.byref(a), _p(film), _p(steady)):
+            raise ValueError("oracle polarized render: invalid arguments")
         return dict(film=film, steady=steady)
 
     def render_phasor(self, H, W, lambdas, spp, seed, max_depth, flags=0, sample_offset=0, crop=None):
