@@ -612,6 +612,19 @@ def secondary(api, autotune, scenes):
     api.render_phasor(s, f.H, f.W, lam, 256, 1, 8)
     c = s.read_counters(reset=True)
     s.sync()
+    # transient polarization of the benchmark frame at 64 spp (Stokes film [512][512][2048][4][3] would be
+    # 25.8 GB; T = 512 bins x 0.02 m keeps it at 6.4 GB)
+    pf, pst = (torch.empty((f.H, f.W, 512, 4, 3), device="cuda"), torch.empty((f.H, f.W, 4, 3), device="cuda"))
+    pms = _timed(lambda: api.render_polarized(s, f.H, f.W, 512, f.start_opl, 0.02, 64, 1, 8, out=(pf, pst)), 2)
+    s.read_counters(reset=True)
+    api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8)
+    cp = s.read_counters(reset=True)
+    s.sync()
+    out["polarized"] = {"vertices_per_s": cp["vertices"] / (pms / 1000.0), "ms_per_render": pms,
+                        "workload": "large static scene, 512x512 px, 64 spp, max_depth 8, Stokes film "
+                                    "[512][512][512 bins x 0.02 m][4][3] (vertices counted by the scalar render "
+                                    "of the same paths)"}
+    del pf, pst
     out["phasor"] = {"vertices_per_s": c["vertices"] / (ms / 1000.0), "ms_per_render": ms,
                      "workload": "large static scene, 512x512 px, 256 spp, max_depth 8, K=4 wavelengths "
                                  "(0.4, 0.2, 0.1, 0.05 m), phasor film [H][W][K][2][3], benchmark launch "

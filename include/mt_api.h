@@ -145,7 +145,8 @@ mt_status mt_scene_set_params(mt_scene scene, const float *d_albedo, const float
  * optional d_steady device float32 [H][W][C] (Sec. 2 listing returns both; the
  * steady image is the time integral including contributions outside the
  * window, Sec. 3 "Path reuse").  C must be 3 for mt_render / mt_render_backward
- * and 1 for mt_render_nlos.  bin_width > 0, T >= 1. */
+ * / mt_render_tangent / mt_render_phasor, 1 for mt_render_nlos and 12 for
+ * mt_render_polarized.  bin_width > 0, T >= 1. */
 mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start_opl, float bin_width,
                          float *d_film, float *d_steady, uint32_t flags, mt_film *out);
 
@@ -178,6 +179,21 @@ mt_status mt_render_nlos(mt_scene scene, mt_film film, const mt_scan *scan, int3
  * Asynchronous; allocates nothing. */
 mt_status mt_render_phasor(mt_scene scene, mt_film film, const float *d_lambdas, int32_t K, int32_t spp,
                            uint64_t seed, int32_t max_depth, uint64_t sample_offset, void *stream);
+
+/* Transient polarization (Sec. 4.2, "Transient polarization tracking"): the
+ * same paths as mt_render with a Stokes vector (S0 intensity, S1 = I_x - I_y,
+ * S2 = I(+45) - I(-45), S3 circular) per colour channel.  The film has C = 12,
+ * laid out [H][W][T][4 Stokes][3 colours], and its steady image [H][W][4][3]
+ * is required.  x is the camera's horizontal axis, y = k x x for light
+ * travelling along k.  Emitters are unpolarised, Lambert surfaces depolarise,
+ * GGX conductors reflect with the Fresnel Mueller matrix of the complex index
+ * 1 + i kappa, kappa = 2 sqrt(F0 / (1 - F0)) (normal-incidence reflectance
+ * F0 = albedo, clamped to 0.999) at the microfacet, so S0 of a conductor
+ * differs from mt_render's Schlick value.  Scattering delays and the emission
+ * pulse apply.  MT_ERR_UNSUPPORTED for scenes with a medium; other errors as
+ * mt_render. */
+mt_status mt_render_polarized(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, int32_t max_depth,
+                              uint64_t sample_offset, void *stream);
 
 /* Forward-mode derivative (Sec. 4.4, forward mode): the film of
  * dI/dtheta . dtheta for one direction dtheta in parameter space, i.e. the

@@ -84,6 +84,7 @@ SIGNATURES = {
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
     "mt_stage_times": (C.c_int, [_P, _P, _I32]),
     "mt_render_tangent": (C.c_int, [_P, _P, _P, _P, C.c_float, _I32, _U64, _I32, _U64, _P]),
+    "mt_render_polarized": (C.c_int, [_P, _P, _I32, _U64, _I32, _U64, _P]),
     "mt_scene_set_delays": (C.c_int, [_P, _P, _P]),
     "mt_scene_set_pulse": (C.c_int, [_P, _U32, C.c_float, C.c_float]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
@@ -193,6 +194,10 @@ def mt_scene_set_pulse(scene, shape, a, b):
 def mt_render_tangent(scene, film, d_dalbedo, d_dradiance, dmedium, spp, seed, max_depth, sample_offset, stream):
     return _call("mt_render_tangent", scene, film, d_dalbedo, d_dradiance, dmedium, spp, seed, max_depth,
                  sample_offset, stream)
+
+
+def mt_render_polarized(scene, film, spp, seed, max_depth, sample_offset, stream):
+    return _call("mt_render_polarized", scene, film, spp, seed, max_depth, sample_offset, stream)
 
 
 def mt_stage_times(scene, out, reset):
@@ -333,8 +338,10 @@ class Scene:
 class Film:
     """A film handle over caller-owned torch tensors."""
 
-    def __init__(self, film, steady, start, width, flags=0):
-        H, W, T, Cc = film.shape
+    def __init__(self, film, steady, start, width, flags=0, C_=None):
+        H, W, T = film.shape[:3]
+        Cc = film.shape[3] if C_ is None else C_
+        assert C_ is None or film[0, 0, 0].numel() == C_
         self.film, self.steady = film, steady
         h = C.c_void_p()
         mt_film_create(H, W, T, Cc, float(start), float(width), _ptr(film), _ptr(steady), int(flags), C.byref(h))
@@ -391,6 +398,20 @@ def render_tangent(scene: Scene, H, W, T, start, width, spp, seed, max_depth, da
     dr = None if dradiance is None else dradiance.float().contiguous()
     mt_render_tangent(scene.h, f.h, _ptr(da), _ptr(dr), float(dmedium), spp, seed, max_depth, sample_offset,
                       _stream(stream))
+    return film, steady
+
+
+def render_polarized(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_offset=0, flags=0, out=None,
+                     stream=None):
+    """Transient polarization: Stokes film [H, W, T, 4, 3] and steady Stokes image [H, W, 4, 3]."""
+    import torch
+    if out is None:
+        film = torch.empty((H, W, T, 4, 3), dtype=torch.float32, device="cuda")
+        steady = torch.empty((H, W, 4, 3), dtype=torch.float32, device="cuda")
+    else:
+        film, steady = out
+    f = Film(film, steady, start, width, flags, C_=12)
+    mt_render_polarized(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
     return film, steady
 
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmt.so")
-SOURCES = ["mt_render.cu", "mt_nlos.cu", "mt_bvh.cu", "mt_api.cu", "mt_micro.cu", "mt_wavefront.cu"]
+SOURCES = ["mt_render.cu", "mt_nlos.cu", "mt_bvh.cu", "mt_api.cu", "mt_micro.cu", "mt_wavefront.cu", "mt_polar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

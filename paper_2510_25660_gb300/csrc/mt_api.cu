@@ -581,7 +581,7 @@ mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start
     MT_CHECK_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
     MT_CHECK_ARG(H >= 1 && W >= 1 && T >= 1, "film size H=%d W=%d T=%d must be positive", H, W, T);
-    MT_CHECK_ARG(C == 1 || C == 3, "C must be 1 or 3");
+    MT_CHECK_ARG(C == 1 || C == 3 || C == 12, "C must be 1, 3 or 12 (Stokes x colour)");
     MT_CHECK_ARG(std::isfinite(start_opl) && std::isfinite(bin_width) && bin_width > 0.f, "bad time window");
     MT_CHECK_ARG(d_film != nullptr, "film pointer is NULL");
     MT_CHECK_ARG((flags & ~(MT_UNWARP | MT_ACCUMULATE | MT_PIXEL_CENTER | MT_COUNTERS)) == 0, "unknown flags 0x%x", flags);
@@ -836,6 +836,32 @@ mt_status mt_render(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t m
                     void *stream) {
     return render_common(s, f, spp, seed, max_depth, sample_offset, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+mt_status mt_render_polarized(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
+                              uint64_t sample_offset, void *stream) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
+    MT_CHECK_ARG(f->C == 12, "polarized films have C = 12 (4 Stokes components x 3 colours)");
+    MT_CHECK_ARG(f->steady != nullptr, "polarized renders need the steady Stokes image");
+    MT_CHECK_ARG(spp >= 1, "spp must be >= 1");
+    MT_CHECK_ARG(max_depth >= 1 && max_depth <= MT_MAX_DEPTH, "max_depth must lie in [1, %d]", MT_MAX_DEPTH);
+    MT_CHECK_ARG(sample_offset + (uint64_t)spp <= 0xFFFFFFFFull, "sample indices must fit in 32 bits");
+    if (s->dev.has_medium) {
+        mt::set_error("polarization tracking does not support participating media");
+        return MT_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool acc = f->flags & MT_ACCUMULATE;
+    if (!acc) {
+        MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 12 * sizeof(float), st));
+        MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 12 * sizeof(float), st));
+    }
+    uint32_t k0, k1;
+    seed_key(seed, k0, k1);
+    s->launches += 1;
+    return mt_launch_polarized(s->dev, f->H, f->W, f->T, f->start, f->width, acc ? 1.0f : 1.0f / (float)spp,
+                               f->flags, spp, max_depth, (uint32_t)sample_offset, k0, k1, f->film, f->steady,
+                               s->num_sms, st);
 }
 
 mt_status mt_render_phasor(mt_scene s, mt_film f, const float *d_lambdas, int32_t K, int32_t spp, uint64_t seed,

@@ -90,6 +90,10 @@ struct WfParams {
 
 size_t mt_wf_sort_bytes(uint32_t P);
 
+mt_status mt_launch_polarized(const DevScene &s, int32_t H, int32_t W, int32_t T, float start, float width,
+                              float scale, uint32_t flags, int32_t spp, int32_t max_depth, uint32_t sample_offset,
+                              uint32_t k0, uint32_t k1, float *film, float *steady, int num_sms, cudaStream_t st);
+
 // Per-stage device time of wavefront renders, from CUDA events recorded on the
 // render stream at the stage boundaries of every iteration.
 struct WfTiming {

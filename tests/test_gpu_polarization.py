@@ -1,0 +1,76 @@
+"""GPU transient polarization (Sec. 4.2) against the oracle on the same Philox
+stream: the Lambertian limit, a single conductor reflection, a Cornell box
+with conductor blocks (multiple reflections, circular light), physical
+Stokes vectors."""
+import numpy as np
+import pytest
+
+from gpu_util import build_and_load, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def test_lambertian_limit(scenes_mod):
+    api = build_and_load()
+    sc = scenes_mod.cornell_box()
+    s = api.Scene(sc)
+    pf, ps = api.render_polarized(s, 64, 64, 128, 3.5, 0.02, 8, 5, 4)
+    f, st = api.render(s, 64, 64, 128, 3.5, 0.02, 8, 5, 4)
+    s.sync()
+    assert (pf[:, :, :, 1:, :] == 0).all().item() and (ps[:, :, 1:, :] == 0).all().item()
+    assert rel_l2(pf[:, :, :, 0, :].cpu().numpy(), f.cpu().numpy()) < 1e-5
+    assert rel_l2(ps[:, :, 0, :].cpu().numpy(), st.cpu().numpy()) < 1e-5
+
+
+def test_single_conductor_reflection_matches_oracle(oracle_mod, scenes_mod):
+    api = build_and_load()
+    sc = scenes_mod.point_light_plane()
+    sc.mtype[:] = 1
+    sc.roughness[:] = 0.3
+    sc.albedo[:] = np.array([0.9, 0.6, 0.3], np.float32)
+    s = api.Scene(sc)
+    n = 16
+    pf, ps = api.render_polarized(s, n, n, 4, 0.0, 100.0, 1, 3, 2, flags=api.MT_PIXEL_CENTER)
+    s.sync()
+    ref = oracle_mod.OracleScene(sc).render_polarized(n, n, 4, 0.0, 100.0, 1, 3, 2, flags=oracle_mod.PIXEL_CENTER)
+    g, r = ps.cpu().numpy(), ref["steady"]
+    assert np.abs(r[:, :, 1:]).max() > 1e-3 * r[:, :, 0].max()
+    assert np.abs(g - r).max() < 2e-4 * np.abs(r).max()
+
+
+@pytest.fixture(scope="module")
+def conductor_box(oracle_mod, scenes_mod):
+    sc = scenes_mod.cornell_box()
+    sc.mtype[10:34] = 1
+    sc.roughness[10:34] = 0.08
+    sc.albedo[10:34] = np.clip(sc.albedo[10:34] + 0.3, 0, 0.95)
+    return sc, oracle_mod.OracleScene(sc)
+
+
+def test_conductor_box_matches_oracle(conductor_box):
+    api = build_and_load()
+    sc, osc = conductor_box
+    s = api.Scene(sc)
+    T, start, width = 200, 3.0, 0.02
+    pf, ps = api.render_polarized(s, 64, 64, T, start, width, 16, 5, 6)
+    s.sync()
+    crop = (24, 40, 24, 40)
+    ref = osc.render_polarized(64, 64, T, start, width, 16, 5, 6, crop=crop)
+    g = ps.cpu().numpy()[24:40, 24:40]
+    r = ref["steady"]
+    assert rel_l2(g[:, :, 0], r[:, :, 0]) < 0.01
+    assert np.linalg.norm(g[:, :, 1:] - r[:, :, 1:]) < 0.02 * np.linalg.norm(r[:, :, 1:])
+    assert np.abs(r[:, :, 3]).max() > 0
+    gf = pf.cpu().numpy()[24:40, 24:40]
+    assert rel_l2(gf[..., 0, :], ref["film"][..., 0, :]) < 0.01
+    # physical Stokes vectors everywhere (FP32 slack)
+    S = ps.cpu().numpy()
+    assert np.all(S[:, :, 0] + 1e-6 >= np.sqrt((S[:, :, 1:] ** 2).sum(2)) * (1 - 1e-5))
+
+
+def test_media_rejected(scenes_mod):
+    api = build_and_load()
+    s = api.Scene(scenes_mod.media_scene(res=8))
+    with pytest.raises(api.MtError) as e:
+        api.render_polarized(s, 8, 8, 4, 0.0, 1.0, 1, 1, 2)
+    assert e.value.status == api.MT_ERR_UNSUPPORTED
