@@ -407,6 +407,41 @@ def point_light_plane(albedo: float = 0.6, intensity: float = 5.0, light_pos=(0.
     return Scene(tris, albedo, np.zeros(2, np.float32), np.zeros(2, np.uint32), emitters, camera)
 
 
+def mirror_wall(f0=(0.9, 0.6, 0.3), rough: float = 1e-4, wall_albedo: float = 0.7) -> Scene:
+    """A near-perfect conductor floor (y = 0, GGX) reflecting a Lambertian wall
+    (z = -3) lit by a point emitter off to the side; the camera looks down at
+    the floor, so most pixels see the wall through one specular reflection."""
+    S = 10.0
+    floor = quad((-S, 0.0, S), (S, 0.0, S), (S, 0.0, -S), (-S, 0.0, -S))
+    wall = quad((-S, 0.0, -3.0), (S, 0.0, -3.0), (S, 2 * S, -3.0), (-S, 2 * S, -3.0))
+    tris = np.concatenate([floor, wall]).astype(np.float32)
+    albedo = np.concatenate([np.tile(np.array(f0, np.float32), (2, 1)), np.full((2, 3), wall_albedo, np.float32)])
+    rough_a = np.array([rough, rough, 0.0, 0.0], np.float32)
+    mtype = np.array([1, 1, 0, 0], np.uint32)
+    emitters = [dict(type=EMITTER_POINT, first_tri=0, n_tris=0, radiance=(8.0,) * 3, position=(2.5, 1.5, -2.0))]
+    camera = dict(origin=(0.0, 2.0, 2.0), target=(0.0, 0.0, -1.0), up=(0.0, 1.0, 0.0), fov_x_deg=40.0)
+    return Scene(tris, albedo, rough_a, mtype, emitters, camera)
+
+
+def mirror_corner(f0_floor=(0.9, 0.6, 0.3), f0_wall=(0.5, 0.8, 0.95), rough: float = 1e-4) -> Scene:
+    """Two near-perfect conductors, the floor (y = 0) and a back wall (z = -3),
+    and a Lambertian ceiling (y = 6) lit by a point emitter off to the side:
+    the camera sees the ceiling through a reflection in the floor followed by
+    one in the back wall."""
+    S = 12.0
+    floor = quad((-S, 0.0, S), (S, 0.0, S), (S, 0.0, -3.0), (-S, 0.0, -3.0))
+    wall = quad((-S, 0.0, -3.0), (S, 0.0, -3.0), (S, 6.0, -3.0), (-S, 6.0, -3.0))
+    ceil = quad((-S, 6.0, -3.0), (S, 6.0, -3.0), (S, 6.0, S), (-S, 6.0, S))
+    tris = np.concatenate([floor, wall, ceil]).astype(np.float32)
+    albedo = np.concatenate([np.tile(np.array(f0_floor, np.float32), (2, 1)),
+                             np.tile(np.array(f0_wall, np.float32), (2, 1)), np.full((2, 3), 0.7, np.float32)])
+    rough_a = np.array([rough, rough, rough, rough, 0.0, 0.0], np.float32)
+    mtype = np.array([1, 1, 1, 1, 0, 0], np.uint32)
+    emitters = [dict(type=EMITTER_POINT, first_tri=0, n_tris=0, radiance=(30.0,) * 3, position=(6.0, 5.5, 2.0))]
+    camera = dict(origin=(0.0, 2.0, 2.0), target=(0.0, 0.0, -1.0), up=(0.0, 1.0, 0.0), fov_x_deg=40.0)
+    return Scene(tris, albedo, rough_a, mtype, emitters, camera)
+
+
 def furnace_sphere(level: int = 4, radius: float = 1.0, albedo: float = 0.5, radiance: float = 1.0) -> Scene:
     """Closed inward-facing icosphere, every triangle emissive and Lambertian;
     the camera sits at the centre."""

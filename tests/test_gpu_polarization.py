@@ -74,3 +74,23 @@ def test_media_rejected(scenes_mod):
     with pytest.raises(api.MtError) as e:
         api.render_polarized(s, 8, 8, 4, 0.0, 1.0, 1, 1, 2)
     assert e.value.status == api.MT_ERR_UNSUPPORTED
+
+
+def test_two_reflections_match_oracle(oracle_mod, scenes_mod):
+    """Conductor floor and back wall before a Lambertian ceiling (the frames of
+    two polarising reflections chained on the continuation path)."""
+    api = build_and_load()
+    sc = scenes_mod.mirror_corner()
+    s = api.Scene(sc)
+    n = 24
+    pf, ps = api.render_polarized(s, n, n, 4, 0.0, 100.0, 1, 4, 4, flags=api.MT_PIXEL_CENTER)
+    s.sync()
+    ref = oracle_mod.OracleScene(sc).render_polarized(n, n, 4, 0.0, 100.0, 1, 4, 4, flags=oracle_mod.PIXEL_CENTER)
+    g, r = ps.cpu().numpy(), ref["steady"]
+    lit = r[:, :, 0, :] > 1e-3 * r[:, :, 0, :].max()
+    assert lit.sum() > 100
+    ratio_g = g[:, :, 1:, :] / np.where(lit, g[:, :, 0, :], 1.0)[:, :, None, :]
+    ratio_r = r[:, :, 1:, :] / np.where(lit, r[:, :, 0, :], 1.0)[:, :, None, :]
+    err = np.abs(ratio_g - ratio_r).max(axis=2)[lit]
+    assert np.quantile(err, 0.95) < 1e-3 and err.max() < 2e-2, (np.quantile(err, 0.95), err.max())
+    assert rel_l2(g[:, :, 0, :], r[:, :, 0, :]) < 1e-3

@@ -155,3 +155,135 @@ def test_rotating_the_camera_rotates_the_linear_part(oracle_mod, scenes_mod):
         assert np.allclose(np.abs(z), np.abs(z0), rtol=1e-10)
         ang = np.angle(z / z0)
         assert np.allclose(np.abs(np.angle(np.exp(1j * (np.abs(ang) - 2 * phi)))), 0.0, atol=1e-9), (phi, ang)
+
+
+def test_reflection_on_the_continuation_path_closed_form(oracle_mod, scenes_mod):
+    """Camera -> near-perfect conductor floor -> Lambertian wall lit by a point
+    light: the wall depolarises, so what reaches the camera through the floor
+    is one Fresnel reflection made on the continuation path (Mueller update and
+    change of frame), not in a next-event estimate: S1/S0 and S2/S0 follow the
+    same closed form as a single reflection at the mirror direction, S3 = 0;
+    pixels that see the wall directly are unpolarised."""
+    f0 = np.array([0.9, 0.6, 0.3])
+    sc = scenes_mod.mirror_wall(tuple(f0))
+    osc = oracle_mod.OracleScene(sc)
+    n = 12
+    st = osc.render_polarized(n, n, 4, 0.0, 100.0, 1, 9, 3, flags=oracle_mod.PIXEL_CENTER)["steady"]
+    cam = sc.camera
+    f = np.array(cam["target"], np.float64) - np.array(cam["origin"], np.float64)
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.array(cam["up"], np.float64))
+    r /= np.linalg.norm(r)
+    n_mirror = n_direct = 0
+    errs = []
+    for py in range(n):
+        for px in range(n):
+            d = np.zeros(3)
+            o = np.zeros(3)
+            oracle_mod.lib().mo_camera_ray(osc.h, n, n, px, py, 0.5, 0.5, oracle_mod._p(o), oracle_mod._p(d))
+            S = st[py, px]
+            t_floor = -o[1] / d[1] if d[1] < 0 else np.inf
+            t_wall = (-3.0 - o[2]) / d[2] if d[2] < 0 else np.inf
+            if S[0].min() <= 0:
+                continue
+            if t_wall < t_floor:
+                assert np.all(S[1:] == 0.0)
+                n_direct += 1
+                continue
+            wi = d * np.array([1.0, -1.0, 1.0])          # mirror direction off the floor
+            ci = wi[1]                                    # microfacet normal ~ floor normal
+            rs, rp = _fresnel_rs_rp(ci, f0)
+            s = np.cross(wi, d)
+            s /= np.linalg.norm(s)
+            xc = r - np.dot(r, d) * d
+            xc /= np.linalg.norm(xc)
+            t = np.arctan2(np.dot(xc, np.cross(-d, s)), np.dot(xc, s))
+            dolp = (rs - rp) / (rs + rp)
+            errs.append(max(np.abs(S[1] / S[0] - dolp * np.cos(2 * t)).max(),
+                            np.abs(S[2] / S[0] + dolp * np.sin(2 * t)).max()))
+            assert np.abs(S[3]).max() <= 1e-6 * S[0].max()
+            n_mirror += 1
+    assert n_mirror > n * n // 3 and n_direct > 0
+    # the floor's GGX (alpha 1e-4) scatters a few sampled directions by ~1e-3 rad (heavy tails);
+    # a wrong frame or sign would be off by O(0.1 - 1)
+    assert np.quantile(errs, 0.9) < 5e-4 and max(errs) < 2e-2, (np.quantile(errs, 0.9), max(errs))
+
+
+def _jones_reflect(E, k_in, k_out, n, f0):
+    """Reflect a complex 3-D field E (perpendicular to k_in) off a conductor of
+    normal-incidence reflectance f0 (index 1 + i kappa): s = normal of the
+    plane of incidence, p = k x s on each side (polarization ray tracing)."""
+    s = np.cross(k_in, k_out)
+    s /= np.linalg.norm(s)
+    p_in, p_out = np.cross(k_in, s), np.cross(k_out, s)
+    ci = -np.dot(k_in, n)
+    kappa = 2.0 * np.sqrt(f0 / (1.0 - f0))
+    N = 1.0 + 1j * kappa
+    ct = np.sqrt(1.0 - (1.0 - ci ** 2) / N ** 2 + 0j)
+    rs = (ci - N * ct) / (ci + N * ct)
+    rp = (N * ci - ct) / (N * ci + ct)
+    return rs * np.dot(E, s) * s + rp * np.dot(E, p_in) * p_out
+
+
+def test_two_reflections_against_jones_calculus(oracle_mod, scenes_mod):
+    """Camera -> conductor floor -> conductor back wall -> Lambertian ceiling
+    lit by a point light: the Stokes vector the camera sees, computed with
+    Mueller matrices and frame rotations in the oracle, equals the incoherent
+    sum over two orthogonal polarisations leaving the ceiling of the fields
+    reflected by the two conductors (3-D Jones calculus): S1/S0, S2/S0 and
+    |S3|/S0 per colour."""
+    f0a = np.array([0.9, 0.6, 0.3])
+    f0b = np.array([0.5, 0.8, 0.95])
+    sc = scenes_mod.mirror_corner(tuple(f0a), tuple(f0b))
+    osc = oracle_mod.OracleScene(sc)
+    n = 12
+    st = osc.render_polarized(n, n, 4, 0.0, 100.0, 1, 4, 4, flags=oracle_mod.PIXEL_CENTER)["steady"]
+    cam = sc.camera
+    f = np.array(cam["target"], np.float64) - np.array(cam["origin"], np.float64)
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.array(cam["up"], np.float64))
+    r /= np.linalg.norm(r)
+    checked = 0
+    errs = []
+    for py in range(n):
+        for px in range(n):
+            d = np.zeros(3)
+            o = np.zeros(3)
+            oracle_mod.lib().mo_camera_ray(osc.h, n, n, px, py, 0.5, 0.5, oracle_mod._p(o), oracle_mod._p(d))
+            if d[1] >= 0:
+                continue
+            x1 = o + d * (-o[1] / d[1])                   # floor
+            d2 = d * np.array([1.0, -1.0, 1.0])
+            if x1[2] <= -3.0 or d2[2] >= 0:
+                continue
+            x2 = x1 + d2 * ((-3.0 - x1[2]) / d2[2])       # back wall
+            if not (0.0 < x2[1] < 6.0):
+                continue
+            d3 = d2 * np.array([1.0, 1.0, -1.0])
+            if d3[1] <= 0:
+                continue
+            S = st[py, px]
+            if S[0].min() <= 0:
+                continue
+            k1, k2, k3 = -d, -d2, -d3                     # propagation of the light, ceiling -> camera
+            xc = r - np.dot(r, d) * d
+            xc /= np.linalg.norm(xc)
+            yc = np.cross(k1, xc)
+            e1 = np.cross(k3, [0.3, 0.1, 0.9])
+            e1 /= np.linalg.norm(e1)
+            e2 = np.cross(k3, e1)
+            for c in range(3):
+                acc = np.zeros(4)
+                for E in (e1.astype(complex), e2.astype(complex)):
+                    Eb = _jones_reflect(E, k3, k2, np.array([0.0, 0.0, 1.0]), f0b[c])
+                    Ea = _jones_reflect(Eb, k2, k1, np.array([0.0, 1.0, 0.0]), f0a[c])
+                    ex, ey = np.dot(Ea, xc), np.dot(Ea, yc)
+                    acc += [abs(ex) ** 2 + abs(ey) ** 2, abs(ex) ** 2 - abs(ey) ** 2,
+                            2 * (ex * np.conj(ey)).real, 2 * (ex * np.conj(ey)).imag]
+                got = S[:, c] / S[0, c]
+                want = acc / acc[0]
+                errs.append(max(np.abs(got[1:3] - want[1:3]).max(), abs(abs(got[3]) - abs(want[3]))))
+            checked += 1
+    assert checked > 10
+    # near-specular GGX sampling (alpha 1e-4) perturbs a few paths by ~1e-3 rad; frame errors would be O(0.1 - 1)
+    assert np.quantile(errs, 0.9) < 5e-4 and max(errs) < 2e-2, (np.quantile(errs, 0.9), max(errs))
