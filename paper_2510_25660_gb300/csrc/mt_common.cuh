@@ -128,7 +128,8 @@ __device__ __forceinline__ void bsdf_eval(const Mat &m, float3 wo, float3 wi, fl
     }
     const float a = fmaxf(m.rough, 1e-4f), a2 = a * a;
     const float3 h = normalize(wo + wi);
-    const float k = h.z * h.z * (a2 - 1.0f) + 1.0f;
+    // 1 - h.z^2 (a^2 - 1) written as (h.x^2 + h.y^2) + a^2 h.z^2: no cancellation for small a in FP32
+    const float k = (h.x * h.x + h.y * h.y) + a2 * (h.z * h.z);
     const float D = a2 / (MT_PI * k * k);
     const float lo = ggx_lambda(a2, wo), li = ggx_lambda(a2, wi);
     const float G2 = 1.0f / (1.0f + lo + li), G1o = 1.0f / (1.0f + lo);

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128) k_render_pol(const DevScene s, const PolP
                         } else {
                             const float a = fmaxf(m.rough, 1e-4f), a2 = a * a;
                             const float3 h = normalize(wol + wil);
-                            const float kd = h.z * h.z * (a2 - 1.0f) + 1.0f;
+                            const float kd = (h.x * h.x + h.y * h.y) + a2 * (h.z * h.z);
                             const float D = a2 / (MT_PI * kd * kd);
                             const float G2 = 1.0f / (1.0f + ggx_lambda(a2, wol) + ggx_lambda(a2, wil));
                             const float kf = D * G2 / (4.0f * wol.z * wil.z) * cx * geo * w;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_render_pol(const DevScene s, const PolP
             } else {
                 const float a = fmaxf(m.rough, 1e-4f), a2 = a * a;
                 const float3 h = normalize(wol + wil);
-                const float kd = h.z * h.z * (a2 - 1.0f) + 1.0f;
+                const float kd = (h.x * h.x + h.y * h.y) + a2 * (h.z * h.z);
                 const float D = a2 / (MT_PI * kd * kd);
                 const float G2 = 1.0f / (1.0f + ggx_lambda(a2, wol) + ggx_lambda(a2, wil));
                 const float kf = D * G2 / (4.0f * wol.z * wil.z) * wil.z / pb;
