@@ -150,6 +150,16 @@ mt_status mt_scene_set_params(mt_scene scene, const float *d_albedo, const float
 mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start_opl, float bin_width,
                          float *d_film, float *d_steady, uint32_t flags, mt_film *out);
 
+/* Make the film a window of a taller frame: its H rows are rows [row0, row0 + H)
+ * of a frame_H x W image (same camera, same per-pixel random numbers), so a
+ * frame rendered window by window equals the frame rendered at once (crop
+ * rendering; e.g. to copy finished rows to the host while later rows render).
+ * Default: frame_H = H, row0 = 0.  Applies to mt_render, mt_render_dump,
+ * mt_render_phasor, mt_render_backward, mt_render_tangent and
+ * mt_render_polarized; dump records carry frame pixel ids.
+ * MT_ERR_INVALID_ARGUMENT if the window does not fit. */
+mt_status mt_film_set_window(mt_film film, int32_t frame_H, int32_t row0);
+
 /* Transient path tracing (Sec. 3, transient_path integrator): for each pixel,
  * spp paths with samples sample_offset .. sample_offset + spp - 1 from the
  * Philox stream keyed by `seed`, at most max_depth segments each (1 = emitters

@@ -83,6 +83,7 @@ SIGNATURES = {
     "mt_sync": (C.c_int, [_P, _P]),
     "mt_read_counters": (C.c_int, [_P, _P, _I32, _P]),
     "mt_stage_times": (C.c_int, [_P, _P, _I32]),
+    "mt_film_set_window": (C.c_int, [_P, _I32, _I32]),
     "mt_render_tangent": (C.c_int, [_P, _P, _P, _P, C.c_float, _I32, _U64, _I32, _U64, _P]),
     "mt_render_polarized": (C.c_int, [_P, _P, _I32, _U64, _I32, _U64, _P]),
     "mt_scene_set_delays": (C.c_int, [_P, _P, _P]),
@@ -198,6 +199,10 @@ def mt_render_tangent(scene, film, d_dalbedo, d_dradiance, dmedium, spp, seed, m
 
 def mt_render_polarized(scene, film, spp, seed, max_depth, sample_offset, stream):
     return _call("mt_render_polarized", scene, film, spp, seed, max_depth, sample_offset, stream)
+
+
+def mt_film_set_window(film, frame_H, row0):
+    return _call("mt_film_set_window", film, frame_H, row0)
 
 
 def mt_stage_times(scene, out, reset):
@@ -338,7 +343,7 @@ class Scene:
 class Film:
     """A film handle over caller-owned torch tensors."""
 
-    def __init__(self, film, steady, start, width, flags=0, C_=None):
+    def __init__(self, film, steady, start, width, flags=0, C_=None, window=None):
         H, W, T = film.shape[:3]
         Cc = film.shape[3] if C_ is None else C_
         assert C_ is None or film[0, 0, 0].numel() == C_
@@ -346,6 +351,8 @@ class Film:
         h = C.c_void_p()
         mt_film_create(H, W, T, Cc, float(start), float(width), _ptr(film), _ptr(steady), int(flags), C.byref(h))
         self.h = h
+        if window is not None:  # (frame_H, row0): these rows of a taller frame
+            mt_film_set_window(h, int(window[0]), int(window[1]))
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -363,10 +370,11 @@ def new_film(H, W, T, Cc=3, device="cuda"):
 
 
 def render(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_offset=0, flags=0, out=None,
-           stream=None):
-    """Transient render; returns (film [H,W,T,3], steady [H,W,3]) torch tensors."""
+           stream=None, window=None):
+    """Transient render; returns (film [H,W,T,3], steady [H,W,3]) torch tensors.
+    window=(frame_H, row0): the H rows are rows row0.. of a frame_H-row image."""
     film, steady = out if out is not None else new_film(H, W, T, 3)
-    f = Film(film, steady, start, width, flags)
+    f = Film(film, steady, start, width, flags, window=window)
     mt_render(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
     return film, steady
 
@@ -402,7 +410,7 @@ def render_tangent(scene: Scene, H, W, T, start, width, spp, seed, max_depth, da
 
 
 def render_polarized(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_offset=0, flags=0, out=None,
-                     stream=None):
+                     stream=None, window=None):
     """Transient polarization: Stokes film [H, W, T, 4, 3] and steady Stokes image [H, W, 4, 3]."""
     import torch
     if out is None:
@@ -410,7 +418,7 @@ def render_polarized(scene: Scene, H, W, T, start, width, spp, seed, max_depth, 
         steady = torch.empty((H, W, 4, 3), dtype=torch.float32, device="cuda")
     else:
         film, steady = out
-    f = Film(film, steady, start, width, flags, C_=12)
+    f = Film(film, steady, start, width, flags, C_=12, window=window)
     mt_render_polarized(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
     return film, steady
 
@@ -456,7 +464,7 @@ def render_nlos(scene: Scene, lasers, sensors, mode, T, start, width, spp, seed,
 
 
 def render_dump(scene: Scene, H, W, T, start, width, spp, seed, max_depth, cap, sample_offset=0, flags=0,
-                scan_args=None, stream=None):
+                scan_args=None, stream=None, window=None):
     """Forward render (or NLOS when scan_args is given) that also returns every
     contribution record as a numpy structured array (CONTRIB_DTYPE)."""
     import torch
@@ -464,7 +472,7 @@ def render_dump(scene: Scene, H, W, T, start, width, spp, seed, max_depth, cap, 
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     if scan_args is None:
         film, steady = new_film(H, W, T, 3)
-        f = Film(film, steady, start, width, flags)
+        f = Film(film, steady, start, width, flags, window=window)
         mt_render_dump(scene.h, f.h, None, spp, seed, max_depth, sample_offset, _ptr(dump), cap, _ptr(cnt),
                        _stream(stream))
     else:

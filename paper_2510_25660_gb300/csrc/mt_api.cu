@@ -60,6 +60,7 @@ struct mt_film_s {
     float start, width;
     float *film, *steady;
     uint32_t flags;
+    int32_t H_full, row0;  // window: rows [row0, row0 + H) of an H_full x W frame
 };
 
 struct GraphCache {
@@ -457,6 +458,27 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
     return MT_OK;
 }
 
+// true when no float has an all-ones exponent (no infinity or NaN)
+static bool all_finite(const float *v, size_t n) {
+    const uint32_t *b = reinterpret_cast<const uint32_t *>(v);
+    uint32_t bad = 0;
+    for (size_t i = 0; i < n; ++i) bad |= (uint32_t)((b[i] & 0x7F800000u) == 0x7F800000u);
+    return bad == 0;
+}
+
+static bool materials_ok(const mt_material *m, int64_t n) {
+    uint32_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const mt_material &x = m[i];
+        bad |= (uint32_t)!(x.albedo[0] >= 0.f && x.albedo[0] < INFINITY);
+        bad |= (uint32_t)!(x.albedo[1] >= 0.f && x.albedo[1] < INFINITY);
+        bad |= (uint32_t)!(x.albedo[2] >= 0.f && x.albedo[2] < INFINITY);
+        bad |= (uint32_t)(x.type != MT_LAMBERT && x.type != MT_GGX_CONDUCTOR);
+        bad |= (uint32_t)(x.type == MT_GGX_CONDUCTOR && !(x.roughness > 0.f && x.roughness <= 1.f));
+    }
+    return bad == 0;
+}
+
 mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials, const mt_emitter *emitters,
                           int32_t n_emitters, const mt_camera *camera, const mt_medium *medium, void *stream,
                           mt_scene *out) {
@@ -465,16 +487,22 @@ mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *
     MT_CHECK_ARG(tris != nullptr && materials != nullptr && camera != nullptr, "tris, materials and camera must not be NULL");
     MT_CHECK_ARG(n_tris >= 1 && n_tris < (1LL << 29), "n_tris = %lld outside [1, 2^29)", (long long)n_tris);
     MT_CHECK_ARG(n_emitters >= 0 && (n_emitters == 0 || emitters != nullptr), "bad emitter list");
-    for (int64_t i = 0; i < n_tris * 9; ++i)
-        MT_CHECK_ARG(std::isfinite(tris[i]), "non-finite vertex coordinate at triangle %lld", (long long)(i / 9));
-    for (int64_t i = 0; i < n_tris; ++i) {
-        const mt_material &m = materials[i];
-        MT_CHECK_ARG(m.type == MT_LAMBERT || m.type == MT_GGX_CONDUCTOR, "triangle %lld: unknown material type %u",
-                     (long long)i, m.type);
-        for (int k = 0; k < 3; ++k)
-            MT_CHECK_ARG(std::isfinite(m.albedo[k]) && m.albedo[k] >= 0.f, "triangle %lld: bad albedo", (long long)i);
-        MT_CHECK_ARG(m.type != MT_GGX_CONDUCTOR || (m.roughness > 0.f && m.roughness <= 1.f),
-                     "triangle %lld: GGX roughness must lie in (0, 1]", (long long)i);
+    // branch-free passes first (vectorisable); the offending element is located only on failure
+    if (!all_finite(tris, (size_t)n_tris * 9)) {
+        for (int64_t i = 0; i < n_tris * 9; ++i)
+            MT_CHECK_ARG(std::isfinite(tris[i]), "non-finite vertex coordinate at triangle %lld", (long long)(i / 9));
+    }
+    if (!materials_ok(materials, n_tris)) {
+        for (int64_t i = 0; i < n_tris; ++i) {
+            const mt_material &m = materials[i];
+            MT_CHECK_ARG(m.type == MT_LAMBERT || m.type == MT_GGX_CONDUCTOR,
+                         "triangle %lld: unknown material type %u", (long long)i, m.type);
+            for (int k = 0; k < 3; ++k)
+                MT_CHECK_ARG(std::isfinite(m.albedo[k]) && m.albedo[k] >= 0.f, "triangle %lld: bad albedo",
+                             (long long)i);
+            MT_CHECK_ARG(m.type != MT_GGX_CONDUCTOR || (m.roughness > 0.f && m.roughness <= 1.f),
+                         "triangle %lld: GGX roughness must lie in (0, 1]", (long long)i);
+        }
     }
     for (int e = 0; e < n_emitters; ++e) {
         const mt_emitter &em = emitters[e];
@@ -586,9 +614,19 @@ mt_status mt_film_create(int32_t H, int32_t W, int32_t T, int32_t C, float start
     MT_CHECK_ARG(d_film != nullptr, "film pointer is NULL");
     MT_CHECK_ARG((flags & ~(MT_UNWARP | MT_ACCUMULATE | MT_PIXEL_CENTER | MT_COUNTERS)) == 0, "unknown flags 0x%x", flags);
     MT_CHECK_ARG((int64_t)H * W < (1LL << 31), "too many pixels");
-    mt_film_s *f = new (std::nothrow) mt_film_s{H, W, T, C, start_opl, bin_width, d_film, d_steady, flags};
+    mt_film_s *f = new (std::nothrow) mt_film_s{H, W, T, C, start_opl, bin_width, d_film, d_steady, flags, H, 0};
     if (!f) return MT_ERR_OUT_OF_MEMORY;
     *out = f;
+    return MT_OK;
+}
+
+mt_status mt_film_set_window(mt_film f, int32_t frame_H, int32_t row0) {
+    MT_CHECK_ARG(f != nullptr, "film is NULL");
+    MT_CHECK_ARG(row0 >= 0 && frame_H >= 1 && (int64_t)row0 + f->H <= frame_H,
+                 "window rows [%d, %d) do not fit a frame of %d rows", row0, row0 + f->H, frame_H);
+    MT_CHECK_ARG((int64_t)frame_H * f->W < (1LL << 31), "too many pixels");
+    f->H_full = frame_H;
+    f->row0 = row0;
     return MT_OK;
 }
 
@@ -710,6 +748,9 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     WfParams w{};
     w.H = rp.H;
     w.W = rp.W;
+    w.H_full = rp.H_full;
+    w.row0 = rp.row0;
+    w.pix_base = rp.pix_base;
     w.T = rp.T;
     w.start = rp.start;
     w.width = rp.width;
@@ -788,6 +829,9 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
     RenderParams p{};
     p.H = f->H;
     p.W = f->W;
+    p.H_full = f->H_full;
+    p.row0 = f->row0;
+    p.pix_base = (uint32_t)f->row0 * (uint32_t)f->W;
     p.T = f->T;
     p.D = D;
     p.start = f->start;
@@ -859,7 +903,8 @@ mt_status mt_render_polarized(mt_scene s, mt_film f, int32_t spp, uint64_t seed,
     uint32_t k0, k1;
     seed_key(seed, k0, k1);
     s->launches += 1;
-    return mt_launch_polarized(s->dev, f->H, f->W, f->T, f->start, f->width, acc ? 1.0f : 1.0f / (float)spp,
+    return mt_launch_polarized(s->dev, f->H, f->W, f->T, f->H_full, f->row0, f->start, f->width,
+                               acc ? 1.0f : 1.0f / (float)spp,
                                f->flags, spp, max_depth, (uint32_t)sample_offset, k0, k1, f->film, f->steady,
                                s->num_sms, st);
 }

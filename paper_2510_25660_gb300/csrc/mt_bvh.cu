@@ -569,9 +569,10 @@ __device__ __forceinline__ uint32_t child_ref(const BNode *nodes, const int *map
 }
 
 __device__ __forceinline__ void quant_box(const BNode &n, const float *qlo, const float *qs, uint32_t *q) {
+    const bool empty = n.left < 0 && n.count <= 0;  // inverted planes: never hit
     for (int k = 0; k < 3; ++k) {
-        q[k] = qfloor(n.lo[k], qlo[k], qs[k]);
-        q[3 + k] = qceil(n.hi[k], qlo[k], qs[k]);
+        q[k] = empty ? 65535u : qfloor(n.lo[k], qlo[k], qs[k]);
+        q[3 + k] = empty ? 0u : qceil(n.hi[k], qlo[k], qs[k]);
     }
 }
 
@@ -776,11 +777,17 @@ __global__ void k_sah(const BNode *nodes, int n, double inv_root, double *acc) {
 __global__ void k_validate(const uint4 *nodes, int n_int, int n, int *bad, unsigned long long *leaf_sum) {
     unsigned long long cnt = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_int; i += gridDim.x * blockDim.x) {
-        const uint4 b = nodes[2 * i + 1];
+        const uint4 a = nodes[2 * i], b = nodes[2 * i + 1];
         const uint32_t refs[2] = {b.z, b.w};
+        // an empty child must have inverted planes on every axis (the traversal relies on it)
+        const uint32_t words[2][3] = {{a.x, a.y, a.z}, {a.w, b.x, b.y}};
         for (int c = 0; c < 2; ++c) {
             const uint32_t r = refs[c];
-            if (r == MT_EMPTY_REF) continue;
+            if (r == MT_EMPTY_REF) {
+                for (int k = 0; k < 3; ++k)
+                    if ((words[c][k] & 0xFFFFu) <= (words[c][k] >> 16)) atomicOr(bad, 16);
+                continue;
+            }
             if (!(r & 0x80000000u)) {
                 if (r >= (uint32_t)n_int || r == 0u) atomicOr(bad, 1);
             } else {

@@ -10,6 +10,8 @@
 
 struct RenderParams {
     int32_t H, W, T, D;        // film size; D = bins per pixel privatised in shared memory
+    int32_t H_full, row0;      // the film holds rows [row0, row0 + H) of an H_full x W frame
+    uint32_t pix_base;         // row0 * W: frame pixel id of the film's first pixel
     float start, width, scale; // time window (OPL metres) and 1/spp (1 when accumulating)
     uint32_t flags;
     int32_t spp, max_depth;
@@ -58,6 +60,8 @@ struct NlosParams {
 
 struct WfParams {
     int32_t H, W, T;
+    int32_t H_full, row0;          // film window in the frame (see RenderParams)
+    uint32_t pix_base;
     float start, width, scale;
     uint32_t flags;
     int32_t spp, max_depth;
@@ -90,9 +94,10 @@ struct WfParams {
 
 size_t mt_wf_sort_bytes(uint32_t P);
 
-mt_status mt_launch_polarized(const DevScene &s, int32_t H, int32_t W, int32_t T, float start, float width,
-                              float scale, uint32_t flags, int32_t spp, int32_t max_depth, uint32_t sample_offset,
-                              uint32_t k0, uint32_t k1, float *film, float *steady, int num_sms, cudaStream_t st);
+mt_status mt_launch_polarized(const DevScene &s, int32_t H, int32_t W, int32_t T, int32_t H_full, int32_t row0,
+                              float start, float width, float scale, uint32_t flags, int32_t spp, int32_t max_depth,
+                              uint32_t sample_offset, uint32_t k0, uint32_t k1, float *film, float *steady,
+                              int num_sms, cudaStream_t st);
 
 // Per-stage device time of wavefront renders, from CUDA events recorded on the
 // render stream at the stage boundaries of every iteration.

@@ -98,6 +98,7 @@ __device__ __forceinline__ void rotate_columns(Mueller &P, float t) {
 
 struct PolParams {
     int32_t H, W, T;
+    int32_t H_full, row0;  // film window: rows [row0, row0 + H) of an H_full x W frame
     float start, width, scale;
     uint32_t flags;
     int32_t spp, max_depth;
@@ -110,8 +111,9 @@ __device__ __forceinline__ void pol_deposit(const DevScene &s, const PolParams &
     opl += pulse_time(s, pix, smp, (uint32_t)depth, kind, p.k0, p.k1);
     const float x = (opl - p.start) / p.width;
     const bool in = x >= 0.f && x < (float)p.T;
-    float *f = in ? p.film + ((size_t)pix * p.T + (int)x) * 12 : nullptr;
-    float *st = p.steady + (size_t)pix * 12;
+    const uint32_t lp = pix - (uint32_t)p.row0 * (uint32_t)p.W;  // film pixel of frame pixel pix
+    float *f = in ? p.film + ((size_t)lp * p.T + (int)x) * 12 : nullptr;
+    float *st = p.steady + (size_t)lp * 12;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -129,14 +131,16 @@ __global__ void __launch_bounds__(128) k_render_pol(const DevScene s, const PolP
     TraceCnt tc{0, 0};
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_paths;
          j += (long long)gridDim.x * blockDim.x) {
-        const uint32_t pix = (uint32_t)(j / p.spp);
-        const uint32_t smp = p.sample_offset + (uint32_t)(j - (long long)pix * p.spp);
+        const uint32_t lpix = (uint32_t)(j / p.spp);
+        const uint32_t smp = p.sample_offset + (uint32_t)(j - (long long)lpix * p.spp);
+        const uint32_t pix = lpix + (uint32_t)p.row0 * (uint32_t)p.W;  // frame pixel id
         const int px = (int)(pix % (uint32_t)p.W), py = (int)(pix / (uint32_t)p.W);
         const uint4 R0 = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.k0, p.k1);
         const bool center = p.flags & MT_PIXEL_CENTER;
         const float jx = center ? 0.5f : u24(R0.x), jy = center ? 0.5f : u24(R0.y);
         const float sx = (2.0f * ((float)px + jx) / (float)p.W - 1.0f) * s.tan_half;
-        const float sy = (1.0f - 2.0f * ((float)py + jy) / (float)p.H) * s.tan_half * ((float)p.H / (float)p.W);
+        const float sy =
+            (1.0f - 2.0f * ((float)py + jy) / (float)p.H_full) * s.tan_half * ((float)p.H_full / (float)p.W);
         float3 o = s.cam_o;
         float3 d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
         Mueller P;
@@ -312,10 +316,11 @@ __global__ void __launch_bounds__(128) k_render_pol(const DevScene s, const PolP
 
 }  // namespace
 
-mt_status mt_launch_polarized(const DevScene &s, int32_t H, int32_t W, int32_t T, float start, float width,
-                              float scale, uint32_t flags, int32_t spp, int32_t max_depth, uint32_t sample_offset,
-                              uint32_t k0, uint32_t k1, float *film, float *steady, int num_sms, cudaStream_t st) {
-    PolParams p{H, W, T, start, width, scale, flags, spp, max_depth, sample_offset, k0, k1, film, steady};
+mt_status mt_launch_polarized(const DevScene &s, int32_t H, int32_t W, int32_t T, int32_t H_full, int32_t row0,
+                              float start, float width, float scale, uint32_t flags, int32_t spp, int32_t max_depth,
+                              uint32_t sample_offset, uint32_t k0, uint32_t k1, float *film, float *steady,
+                              int num_sms, cudaStream_t st) {
+    PolParams p{H, W, T, H_full, row0, start, width, scale, flags, spp, max_depth, sample_offset, k0, k1, film, steady};
     const long long n = (long long)H * W * spp;
     const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, (long long)num_sms * 8));
     k_render_pol<<<grid, 128, 0, st>>>(s, p);

@@ -150,7 +150,7 @@ struct Tracer {
     __device__ __forceinline__ void deposit(PathState &ps, int vert, int kind, int tri, float opl, float3 c,
                                             float3 cb, int em, float3 own_r) {
         // the source emitted this contribution's light at a time drawn from its pulse
-        opl += pulse_time(s, ps.pix, ps.smp, (uint32_t)vert, kind, rng.k0, rng.k1);
+        opl += pulse_time(s, gp(ps), ps.smp, (uint32_t)vert, kind, rng.k0, rng.k1);
         const float x = (opl - p.start) / p.width;
         const bool in = x >= 0.f && x < (float)p.T;
         const int bin = in ? (int)x : -1;
@@ -199,7 +199,7 @@ struct Tracer {
                 const unsigned long long slot = atomicAdd(p.dump_count, 1ull);
                 if ((long long)slot < p.dump_cap) {
                     mt_contrib r;
-                    r.pixel = (int32_t)ps.pix;
+                    r.pixel = (int32_t)gp(ps);
                     r.sample = (int32_t)ps.smp;
                     r.depth = vert;
                     r.kind = kind;
@@ -239,17 +239,21 @@ struct Tracer {
         }
     }
 
+    // frame pixel id of the path (Philox counters, dump records); ps.pix indexes the film
+    __device__ __forceinline__ uint32_t gp(const PathState &ps) const { return ps.pix + p.pix_base; }
+
     __device__ __forceinline__ void begin(PathState &ps, int j, int pix0, int x0, int ty) {
         ps.lp = j / p.spp;
         const int sI = j - ps.lp * p.spp;
         ps.pix = (uint32_t)(pix0 + ps.lp);
         ps.smp = p.sample_offset + (uint32_t)sI;
-        const uint4 R = rng.raw(ps.pix, ps.smp, 0, 0);
+        const uint4 R = rng.raw(gp(ps), ps.smp, 0, 0);
         const bool center = p.flags & MT_PIXEL_CENTER;
         const float jx = center ? 0.5f : u24(R.x), jy = center ? 0.5f : u24(R.y);
         const int px = x0 + ps.lp;
         const float sx = (2.0f * ((float)px + jx) / (float)p.W - 1.0f) * s.tan_half;
-        const float sy = (1.0f - 2.0f * ((float)ty + jy) / (float)p.H) * s.tan_half * ((float)p.H / (float)p.W);
+        const float sy =
+            (1.0f - 2.0f * ((float)(ty + p.row0) + jy) / (float)p.H_full) * s.tan_half * ((float)p.H_full / (float)p.W);
         ps.o = s.cam_o;
         ps.d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
         ps.beta = f3(1.f, 1.f, 1.f);
@@ -308,7 +312,7 @@ struct Tracer {
     // next-event estimate from x (surface: side normal n and frame, or medium)
     __device__ __forceinline__ void nee(PathState &ps, float3 x, bool surface, float3 n, float3 tb, float3 bb,
                                         float3 wol, const Mat &m) {
-        const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_NEE);
+        const uint4 R = rng.raw(gp(ps), ps.smp, (uint32_t)ps.depth, G_NEE);
         const int un = pick_unit(s, R.x);
         const LightUnit U = s.units[un];
         const int em = __float_as_int(U.v2.w);
@@ -328,7 +332,7 @@ struct Tracer {
         float Tr = 1.0f;
         if (MEDIA) {
             bool ok;
-            Tr = transmittance(s, rng, xo, wi, tmax, ps.pix, ps.smp, (uint32_t)ps.depth, ok);
+            Tr = transmittance(s, rng, xo, wi, tmax, gp(ps), ps.smp, (uint32_t)ps.depth, ok);
             if (!ok) {
                 raise_err(s, MT_EFLAG_TRACK);
                 return;
@@ -390,7 +394,7 @@ struct Tracer {
                         raise_err(s, MT_EFLAG_TRACK);
                         return false;
                     }
-                    const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)(ps.depth - 1), G_TRACK + j);
+                    const uint4 R = rng.raw(gp(ps), ps.smp, (uint32_t)(ps.depth - 1), G_TRACK + j);
                     t += -logf(1.0f - u24(R.x)) * inv;
                     if (t >= mb) break;
                     if (u24(R.y) < density_at(s, ps.o + ps.d * t) * inv) {
@@ -415,7 +419,7 @@ struct Tracer {
                     }
                     if (ps.depth == p.max_depth) return false;
                     if (s.n_units > 0) nee(ps, x, false, f3(0, 0, 1), f3(1, 0, 0), f3(0, 1, 0), f3(0, 0, 1), Mat{});
-                    const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
+                    const uint4 R = rng.raw(gp(ps), ps.smp, (uint32_t)ps.depth, G_SCATTER);
                     ps.d = hg_sample(s.m_params[1], ps.d, u24(R.x), u24(R.y));
                     if (MODE == MODE_TAN) ps.sig = ps.sig + ps.dv;
                     ps.o = x;
@@ -450,7 +454,7 @@ struct Tracer {
         }
         if (ps.depth == p.max_depth) return false;
         // scattering delay of this vertex: every later contribution carries it
-        ps.opl += vertex_delay(s, orig, ps.pix, ps.smp, (uint32_t)ps.depth, rng.k0, rng.k1);
+        ps.opl += vertex_delay(s, orig, gp(ps), ps.smp, (uint32_t)ps.depth, rng.k0, rng.k1);
         const float3 n = cwo >= 0.f ? ng : -ng;
         float3 tb, bb;
         onb(n, tb, bb);
@@ -460,7 +464,7 @@ struct Tracer {
         if (MODE == MODE_TAN)
             ps.dv = p.dalb ? f3(p.dalb[orig * 3], p.dalb[orig * 3 + 1], p.dalb[orig * 3 + 2]) : f3(0.f, 0.f, 0.f);
         if (s.n_units > 0) nee(ps, x, true, n, tb, bb, wol, m);
-        const uint4 R = rng.raw(ps.pix, ps.smp, (uint32_t)ps.depth, G_SCATTER);
+        const uint4 R = rng.raw(gp(ps), ps.smp, (uint32_t)ps.depth, G_SCATTER);
         float3 wil;
         if (!bsdf_sample(m, wol, u24(R.x), u24(R.y), wil)) return false;
         float3 f;

@@ -19,6 +19,14 @@
 
 #define MT_EMPTY_REF 0xFFFFFFFFu
 
+// An empty child also has inverted planes (lower 65535, upper 0 on every axis),
+// which the slab test rejects for either direction sign, so the traversal does
+// not need to look at its reference.
+#ifndef MT_CHECK_EMPTY
+#define MT_CHECK_EMPTY 0
+#endif
+#define MT_LIVE(ref) (!MT_CHECK_EMPTY || (ref) != MT_EMPTY_REF)
+
 struct RayT {
     float3 o, d;
     float3 sa, sb;   // slab: t = (2^23 + q) * sa + sb for a quantised plane q
@@ -133,8 +141,8 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
             slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
-            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
-            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
                 if (sp < MT_STACK) {
@@ -197,8 +205,8 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
             slab(r, a.w, b.x, b.y, tmax, tn1, tf1);
-            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
-            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
                 if (sp < MT_STACK) st_ref[sp++] = f0 ? b.w : b.z;
@@ -259,8 +267,8 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
             slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
-            const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
-            const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+            const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
                 if (sp < MT_STACK) {
@@ -379,8 +387,8 @@ __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, floa
         float tn0, tf0, tn1, tf1;
         slab(r, a.x, a.y, a.z, ts.tbest, tn0, tf0);
         slab(r, a.w, b.x, b.y, ts.tbest, tn1, tf1);
-        const bool h0 = tn0 <= tf0 && b.z != MT_EMPTY_REF;
-        const bool h1 = tn1 <= tf1 && b.w != MT_EMPTY_REF;
+        const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+        const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
         if (h0 && h1) {
             const bool f0 = tn0 <= tn1;
             if (ts.sp < MT_STACK) {

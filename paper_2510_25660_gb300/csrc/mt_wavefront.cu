@@ -58,12 +58,12 @@ __device__ __forceinline__ uint32_t wf_append(uint32_t *count, bool want) {
 }
 
 // frequency space (Sec. 4.3, Eq. 12): C exp(-i 2 pi opl / lambda); "bin" 2q real, 2q + 1 imaginary.
-// Out of line so that its registers do not weigh on the time-binned path.
-__device__ __noinline__ void wf_splat_phasor(const WfParams &p, uint32_t pix, float opl, float3 c) {
+// Out of line so that its registers do not weigh on the time-binned path.  lp = film pixel.
+__device__ __noinline__ void wf_splat_phasor(const WfParams &p, uint32_t lp, float opl, float3 c) {
     for (int q = 0; q < p.K; ++q) {
         float sn, cs;
         sincospif(2.0f * opl / __ldg(&p.lambdas[q]), &sn, &cs);
-        float *h = p.film + ((size_t)pix * p.T + 2 * q) * 3;
+        float *h = p.film + ((size_t)lp * p.T + 2 * q) * 3;
         red_add_stream(h, c.x * cs);
         red_add_stream(h + 1, c.y * cs);
         red_add_stream(h + 2, c.z * cs);
@@ -73,18 +73,20 @@ __device__ __noinline__ void wf_splat_phasor(const WfParams &p, uint32_t pix, fl
     }
 }
 
+// pix is the frame pixel id; the film holds the window that starts at p.pix_base
 __device__ __forceinline__ void wf_splat(const WfParams &p, uint32_t pix, float opl, float3 c) {
+    const uint32_t lp = pix - p.pix_base;
     const float x = (opl - p.start) / p.width;
     if (p.K > 0) {
-        wf_splat_phasor(p, pix, opl, c);
+        wf_splat_phasor(p, lp, opl, c);
     } else if (x >= 0.f && x < (float)p.T) {
-        float *h = p.film + ((size_t)pix * p.T + (int)x) * 3;
+        float *h = p.film + ((size_t)lp * p.T + (int)x) * 3;
         red_add_stream(h, c.x);
         red_add_stream(h + 1, c.y);
         red_add_stream(h + 2, c.z);
     }
     if (p.steady) {
-        float *g = p.steady + (size_t)pix * 3;
+        float *g = p.steady + (size_t)lp * 3;
         red_add_stream(g, c.x);
         red_add_stream(g + 1, c.y);
         red_add_stream(g + 2, c.z);
@@ -145,14 +147,16 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < it.n_new; i += gridDim.x * blockDim.x) {
         const uint32_t slot = p.free_q[it.free_before - 1 - i];
         const unsigned long long j = it.base + i;
-        const uint32_t pix = (uint32_t)(j / p.spp);
-        const uint32_t smp = p.sample_offset + (uint32_t)(j - (unsigned long long)pix * p.spp);
+        const uint32_t lpix = (uint32_t)(j / p.spp);
+        const uint32_t smp = p.sample_offset + (uint32_t)(j - (unsigned long long)lpix * p.spp);
+        const uint32_t pix = lpix + p.pix_base;  // frame pixel id
         const uint4 R = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.k0, p.k1);
         const bool center = p.flags & MT_PIXEL_CENTER;
         const float jx = center ? 0.5f : u24(R.x), jy = center ? 0.5f : u24(R.y);
         const uint32_t py = pix / (uint32_t)p.W, px = pix - py * (uint32_t)p.W;
         const float sx = (2.0f * ((float)px + jx) / (float)p.W - 1.0f) * s.tan_half;
-        const float sy = (1.0f - 2.0f * ((float)py + jy) / (float)p.H) * s.tan_half * ((float)p.H / (float)p.W);
+        const float sy =
+            (1.0f - 2.0f * ((float)py + jy) / (float)p.H_full) * s.tan_half * ((float)p.H_full / (float)p.W);
         const float3 d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
         p.o[slot] = make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f);
         p.d[slot] = make_float4(d.x, d.y, d.z, 0.f);
