@@ -53,6 +53,32 @@ mt_status alloc_device(void **p, size_t bytes, const char *what) {
     }
     return MT_OK;
 }
+
+mt_status alloc_device_async(void **p, size_t bytes, const char *what, cudaStream_t st) {
+    const long long k = ++g_alloc_count;
+    if (fault_at() > 0 && k == fault_at()) {
+        set_error("injected allocation failure (%s, %zu bytes)", what, bytes);
+        return MT_ERR_OUT_OF_MEMORY;
+    }
+    static std::once_flag once;
+    std::call_once(once, [] {
+        // keep freed blocks of this process's default pool for the next scene build
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = 8ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocAsync of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MT_ERR_OUT_OF_MEMORY : MT_ERR_CUDA;
+    }
+    return MT_OK;
+}
 }  // namespace mt
 
 struct mt_film_s {
@@ -538,6 +564,12 @@ mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *
         cudaStreamSynchronize((cudaStream_t)stream);
         sc->al.free_all();
         delete sc;
+        // return the build's pooled temporaries too: a failed creation keeps nothing
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+        cudaGetLastError();
         return st;
     }
     *out = sc;

@@ -805,7 +805,9 @@ __global__ void k_validate(const uint4 *nodes, int n_int, int n, int *bad, unsig
 
 mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::AllocList &al, BvhResult *out) {
     auto t0 = std::chrono::steady_clock::now();
-    mt::AllocList tmpal;
+    mt::AllocList tmpal;  // temporaries: stream-ordered, returned to the pool when the build ends
+    tmpal.stream_ordered = true;
+    tmpal.stream = st;
     struct Guard {
         mt::AllocList &a;
         ~Guard() { a.free_all(); }

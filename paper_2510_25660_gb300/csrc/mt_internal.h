@@ -22,20 +22,29 @@ void set_error(const char *fmt, ...);
 const char *get_error();
 
 mt_status alloc_device(void **p, size_t bytes, const char *what);
+// stream-ordered allocation from the device's default memory pool (which keeps
+// freed memory for reuse), for temporaries used on one stream only
+mt_status alloc_device_async(void **p, size_t bytes, const char *what, cudaStream_t st);
 
 struct AllocList {
     std::vector<void *> ptrs;
+    bool stream_ordered = false;  // allocate and free on `stream` (temporaries)
+    cudaStream_t stream = nullptr;
     template <class T>
     mt_status alloc(T **p, size_t count, const char *what) {
         void *q = nullptr;
-        mt_status st = alloc_device(&q, count * sizeof(T) + (count == 0 ? 16 : 0), what);
+        const size_t bytes = count * sizeof(T) + (count == 0 ? 16 : 0);
+        mt_status st = stream_ordered ? alloc_device_async(&q, bytes, what, stream) : alloc_device(&q, bytes, what);
         if (st != MT_OK) return st;
         ptrs.push_back(q);
         *p = (T *)q;
         return MT_OK;
     }
     void free_all() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : ptrs) {
+            if (stream_ordered) cudaFreeAsync(p, stream);
+            else cudaFree(p);
+        }
         ptrs.clear();
     }
     size_t bytes = 0;
