@@ -317,7 +317,9 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * queued rays are sorted by direction octant and the Morton code of their
  * origin, so that a warp traces similar rays (the film is the same).
  * MT_OPT_STAGE_TIMING (with MT_OPT_WAVEFRONT) = CUDA events on the render
- * stream at every stage boundary; read the totals with mt_stage_times. */
+ * stream at every stage boundary; read the totals with mt_stage_times.
+ * MT_OPT_SORT_SHADOW (with MT_OPT_WAVEFRONT) = shadow rays are traced in the
+ * order of (direction cell, origin Morton code) (the film is the same). */
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
 #define MT_OPT_WAVEFRONT 4u
@@ -325,6 +327,7 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
 #define MT_OPT_WIDE_BVH 16u
 #define MT_OPT_SORT_RAYS 32u
 #define MT_OPT_STAGE_TIMING 64u
+#define MT_OPT_SORT_SHADOW 128u
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1

@@ -125,7 +125,7 @@ struct mt_scene_s {
     uint4 *wf_meta = nullptr, *wf_sh_m = nullptr;
     int4 *wf_hit = nullptr;
     uint32_t *wf_qa = nullptr, *wf_qb = nullptr, *wf_free = nullptr, *wf_counters = nullptr;
-    uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr;  // ray reordering
+    uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr, *wf_shperm = nullptr;  // ray reordering
     char *wf_stmp = nullptr;
     size_t wf_stmp_bytes = 0;
     uint32_t wf_sort_cap = 0;
@@ -764,7 +764,8 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         s->wf_cap = P;
     }
     const bool sort_rays = (cfg.options & MT_OPT_SORT_RAYS) != 0;
-    if (sort_rays && P > s->wf_sort_cap) {
+    const bool sort_shadow = (cfg.options & MT_OPT_SORT_SHADOW) != 0 && !dump;
+    if ((sort_rays || sort_shadow) && P > s->wf_sort_cap) {
         cudaStreamCaptureStatus cs;
         MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
         MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
@@ -775,6 +776,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_TRY(al.alloc(&s->wf_sq, P, "ray sort queue"));
         s->wf_stmp_bytes = mt_wf_sort_bytes(P);
         MT_TRY(al.alloc(&s->wf_stmp, s->wf_stmp_bytes, "ray sort scratch"));
+        MT_TRY(al.alloc(&s->wf_shperm, P, "shadow ray order"));
         s->wf_sort_cap = P;
     }
     WfParams w{};
@@ -827,6 +829,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.sort_q = s->wf_sq;
     w.sort_tmp = s->wf_stmp;
     w.sort_tmp_bytes = s->wf_stmp_bytes;
+    w.sh_perm = sort_shadow ? s->wf_shperm : nullptr;
     if (!(rp.flags & MT_ACCUMULATE)) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
@@ -1160,7 +1163,8 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     MT_CHECK_ARG(tile >= 0 && tile <= 4096 && ctas_per_sm >= 0 && ctas_per_sm <= 32, "bad tile / ctas_per_sm");
     MT_CHECK_ARG(priv_bins >= -1, "priv_bins must be >= -1");
     MT_CHECK_ARG((options & ~(MT_OPT_AGGREGATE | MT_OPT_NO_GRAPH | MT_OPT_WAVEFRONT | MT_OPT_DYNAMIC_FETCH |
-                              MT_OPT_WIDE_BVH | MT_OPT_SORT_RAYS | MT_OPT_STAGE_TIMING | 0xFF00u)) == 0,
+                              MT_OPT_WIDE_BVH | MT_OPT_SORT_RAYS | MT_OPT_STAGE_TIMING | MT_OPT_SORT_SHADOW |
+                              0xFF00u)) == 0,
                  "unknown launch options 0x%x", options);
     LaunchCfg &c = s->cfg[kind];
     c.threads = threads ? threads : 256;

@@ -88,6 +88,7 @@ struct WfParams {
     // ray reordering: extension rays sorted by (direction octant, origin Morton code)
     int32_t sort_rays;
     uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue
+    uint32_t *sh_perm;             // shadow rays in sorted order (record indices), null = queue order
     void *sort_tmp;
     size_t sort_tmp_bytes;
 };

@@ -239,6 +239,36 @@ __global__ void k_wf_sort_keys(const DevScene s, const WfParams p, const uint32_
     }
 }
 
+// Sort keys of the queued shadow rays: an octahedral cell of the direction
+// (4 + 4 bits) above the Morton code of the origin on a 128^3 grid (21 bits);
+// the values are record indices.
+__global__ void k_wf_shadow_keys(const DevScene s, const WfParams p) {
+    const uint32_t n = p.counters[C_SHADOW];
+    const float gx = 128.0f / (65536.0f * s.q_scale.x), gy = 128.0f / (65536.0f * s.q_scale.y),
+                gz = 128.0f / (65536.0f * s.q_scale.z);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
+        uint32_t key = 0xFFFFFFFFu;
+        if (i < n) {
+            const float4 o = p.sh_o[i], d = p.sh_d[i];
+            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), 127.0f);
+            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), 127.0f);
+            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), 127.0f);
+            const float l1 = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
+            float u = d.x / l1, v = d.y / l1;
+            if (d.z < 0.0f) {
+                const float uu = (1.0f - fabsf(v)) * (u < 0.0f ? -1.0f : 1.0f);
+                v = (1.0f - fabsf(u)) * (v < 0.0f ? -1.0f : 1.0f);
+                u = uu;
+            }
+            const uint32_t du = (uint32_t)fminf(fmaxf((u + 1.0f) * 8.0f, 0.0f), 15.0f);
+            const uint32_t dv = (uint32_t)fminf(fmaxf((v + 1.0f) * 8.0f, 0.0f), 15.0f);
+            key = (du << 25) | (dv << 21) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+        }
+        p.sort_keys[i] = key;
+        p.sort_q[i] = i;
+    }
+}
+
 // Extension and shadow rays with dynamic fetch: a lane whose ray is done
 // takes the next queue entry as soon as at least p.dynamic_fetch lanes of its
 // warp are idle, so a warp does not wait for its longest ray.  Between two
@@ -476,8 +506,9 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
         if (lane == 0) base = atomicAdd(&p.counters[C_SH_CUR], 32u);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) break;
-        const uint32_t i = base + lane;
-        if (i < n) {
+        const uint32_t q = base + lane;
+        if (q < n) {
+            const uint32_t i = p.sh_perm ? __ldg(&p.sh_perm[q]) : q;
             const float4 o = p.sh_o[i], d = p.sh_d[i];
             const RayT r = make_ray(s, xyz(o), xyz(d));
             rays++;
@@ -610,6 +641,13 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
         if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
         else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (p.sh_perm) {
+            k_wf_shadow_keys<<<grid, 256, 0, st>>>(s, p);
+            size_t bytes = p.sort_tmp_bytes;
+            MT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(p.sort_tmp, bytes, p.sort_keys, p.sort_keys_out, p.sort_q,
+                                                        p.sh_perm, (int)p.P, 0, 29, st));
+            *launches += 1;
+        }
         if (timing) MT_TRY(wf_event(timing, iter, 3, st));
         if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);

@@ -292,12 +292,13 @@ def _form_options(api, opts):
     return {"wavefront": api.MT_OPT_WAVEFRONT,
             "wavefront_wide_bvh": api.MT_OPT_WAVEFRONT | api.MT_OPT_WIDE_BVH,
             "wavefront_sorted": api.MT_OPT_WAVEFRONT | api.MT_OPT_SORT_RAYS,
+            "wavefront_sorted_shadow": api.MT_OPT_WAVEFRONT | api.MT_OPT_SORT_SHADOW,
             "wavefront_dynamic_fetch": api.MT_OPT_WAVEFRONT | api.MT_OPT_DYNAMIC_FETCH,
             "megakernel_refill16": api.MT_OPT_REFILL(16)}[opts]
 
 
-@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_sorted", "wavefront_dynamic_fetch",
-                                  "megakernel_refill16"])
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_sorted", "wavefront_sorted_shadow",
+                                  "wavefront_dynamic_fetch", "megakernel_refill16"])
 def test_forward_forms_per_path_parity(api, cornell, opts):
     """The wavefront form (with or without dynamic ray fetch in its traversal
     kernels) and the megakernel with deferred refill compute the same
@@ -327,7 +328,8 @@ def test_forward_forms_per_path_parity(api, cornell, opts):
     assert rel_l2(f2.cpu().numpy(), f3.cpu().numpy()) < 1e-4
 
 
-@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_sorted", "wavefront_dynamic_fetch"])
+@pytest.mark.parametrize("opts", ["wavefront", "wavefront_wide_bvh", "wavefront_sorted", "wavefront_sorted_shadow",
+                                  "wavefront_dynamic_fetch"])
 def test_wavefront_large_scene_matches_megakernel(api, scenes_mod, opts):
     sc = scenes_mod.diff_scene()
     s = api.Scene(sc)
