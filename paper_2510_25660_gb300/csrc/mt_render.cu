@@ -33,6 +33,17 @@ constexpr int MODE_FWD = 0, MODE_DUMP = 1, MODE_BWD = 2, MODE_PHASOR = 3, MODE_T
 #ifndef MT_RENDER_MINB
 #define MT_RENDER_MINB 4
 #endif
+// with a participating medium the free-flight and ratio-tracking loops need
+// more registers: 2 CTAs per SM (128 registers) measured 479 ms against 553 ms
+// at 4 for the 256x256x128-spp, depth-16 render of the medium-filled box
+#ifndef MT_RENDER_MINB_MEDIA
+#define MT_RENDER_MINB_MEDIA 2
+#endif
+// the path replay keeps per-vertex records
+#ifndef MT_RENDER_MINB_BWD
+#define MT_RENDER_MINB_BWD 4
+#endif
+#define MT_MINB_OF(MODE, MEDIA) ((MEDIA) ? MT_RENDER_MINB_MEDIA : ((MODE) == MODE_BWD ? MT_RENDER_MINB_BWD : MT_RENDER_MINB))
 
 struct VRec {
     int32_t tri;   // original triangle index, -1 for a medium vertex
@@ -483,7 +494,7 @@ struct Tracer {
 };
 
 template <int MODE, bool MEDIA, bool CNT, bool AGG>
-__global__ void __launch_bounds__(256, MT_RENDER_MINB) k_render(const DevScene s, const RenderParams p) {
+__global__ void __launch_bounds__(256, MT_MINB_OF(MODE, MEDIA)) k_render(const DevScene s, const RenderParams p) {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
