@@ -904,7 +904,7 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
-    if ((mode == 0 || mode == 1 || mode == 3) && (cfg.options & MT_OPT_WAVEFRONT) && !s->dev.has_medium)
+    if ((mode == 0 || mode == 1 || mode == 3) && (cfg.options & MT_OPT_WAVEFRONT))
         return render_wavefront(s, f, p, cfg, mode == 1, st);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
     s->launches += 1;

@@ -294,6 +294,75 @@ struct DevScene {
 
 __device__ __forceinline__ void raise_err(const DevScene &s, uint32_t bit) { atomicOr(s.err, bit); }
 
+// ---------------------------------------------------------------------------
+// participating medium (Sec. 4.1): trilinear density, box overlap, ratio tracking
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float density_at(const DevScene &s, float3 p) {
+    const float gx = (p.x - s.m_lo.x) / (s.m_hi.x - s.m_lo.x) * s.rx - 0.5f;
+    const float gy = (p.y - s.m_lo.y) / (s.m_hi.y - s.m_lo.y) * s.ry - 0.5f;
+    const float gz = (p.z - s.m_lo.z) / (s.m_hi.z - s.m_lo.z) * s.rz - 0.5f;
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const float fx = gx - fx0, fy = gy - fy0, fz = gz - fz0;
+    const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+    const int x0 = min(max(ix, 0), s.rx - 1), x1 = min(max(ix + 1, 0), s.rx - 1);
+    const int y0 = min(max(iy, 0), s.ry - 1), y1 = min(max(iy + 1, 0), s.ry - 1);
+    const int z0 = min(max(iz, 0), s.rz - 1), z1 = min(max(iz + 1, 0), s.rz - 1);
+    auto D = [&](int x, int y, int z) { return __ldg(&s.dens[((size_t)z * s.ry + y) * s.rx + x]); };
+    const float c00 = D(x0, y0, z0) * (1.f - fx) + D(x1, y0, z0) * fx;
+    const float c10 = D(x0, y1, z0) * (1.f - fx) + D(x1, y1, z0) * fx;
+    const float c01 = D(x0, y0, z1) * (1.f - fx) + D(x1, y0, z1) * fx;
+    const float c11 = D(x0, y1, z1) * (1.f - fx) + D(x1, y1, z1) * fx;
+    const float c0 = c00 * (1.f - fy) + c10 * fy, c1 = c01 * (1.f - fy) + c11 * fy;
+    return c0 * (1.f - fz) + c1 * fz;
+}
+
+// overlap of the ray with the medium box, clipped to [0, tmax]
+__device__ __forceinline__ bool medium_span(const DevScene &s, float3 o, float3 d, float tmax, float &a, float &b) {
+    float t0 = 0.f, t1 = tmax;
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    const float lo[3] = {s.m_lo.x, s.m_lo.y, s.m_lo.z}, hi[3] = {s.m_hi.x, s.m_hi.y, s.m_hi.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (dd[k] == 0.f) {
+            if (oo[k] < lo[k] || oo[k] > hi[k]) return false;
+            continue;
+        }
+        float ta = (lo[k] - oo[k]) / dd[k], tb = (hi[k] - oo[k]) / dd[k];
+        if (ta > tb) {
+            const float x = ta;
+            ta = tb;
+            tb = x;
+        }
+        t0 = fmaxf(t0, ta);
+        t1 = fminf(t1, tb);
+    }
+    if (t0 >= t1) return false;
+    a = t0;
+    b = t1;
+    return true;
+}
+
+// ratio-tracking transmittance over [0, dist]; ok = false if the step cap was hit
+__device__ __forceinline__ float transmittance(const DevScene &s, const Rng &rng, float3 o, float3 d, float dist,
+                                               uint32_t pix, uint32_t smp, uint32_t depth, bool &ok) {
+    ok = true;
+    float a, b;
+    if (!medium_span(s, o, d, dist, a, b)) return 1.0f;
+    float T = 1.0f, t = a;
+    const float inv = 1.0f / s.m_major;
+    for (uint32_t j = 0;; ++j) {
+        if (j >= MT_TRACK_STEPS) {
+            ok = false;
+            return 0.f;
+        }
+        const uint4 R = rng.raw(pix, smp, depth, G_RATIO + j);
+        t += -logf(1.0f - u24(R.x)) * inv;
+        if (t >= b) break;
+        T *= 1.0f - density_at(s, o + d * t) * inv;
+    }
+    return T;
+}
+
 // exponential draw of mean `mean` from one Philox word (1 - u > 0)
 __device__ __forceinline__ float exp_draw(float mean, uint32_t x) { return -mean * logf(1.0f - u24(x)); }
 

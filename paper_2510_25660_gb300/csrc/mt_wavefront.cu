@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
 #define MT_WF_TRACE_MINB 6
 #endif
 
-template <bool WIDE, bool CNT>
+// hit record: (leaf-order triangle or -1, original triangle, t bits, 1 if the
+// path scatters in the medium at t before reaching that surface)
+template <bool WIDE, bool CNT, bool MEDIA>
 __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
     const uint32_t n = p.counters[C_CUR];
     const int lane = threadIdx.x & 31;
@@ -194,9 +196,34 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevSc
             const RayT r = make_ray(s, xyz(o), xyz(d));
             float t;
             int orig;
-            const int k = WIDE ? trace_wide<false, CNT>(s, r, INFINITY, t, orig, tc)
-                               : trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
-            p.hit[slot] = make_int4(k, orig, __float_as_int(t), 0);
+            int k = WIDE ? trace_wide<false, CNT>(s, r, INFINITY, t, orig, tc)
+                         : trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
+            int collided = 0;
+            if (MEDIA) {
+                // delta tracking over the part of the segment inside the medium (Sec. 4.1)
+                float ma, mb;
+                if (medium_span(s, xyz(o), xyz(d), k >= 0 ? t : 1e30f, ma, mb)) {
+                    const uint4 m = p.meta[slot];
+                    const float inv = 1.0f / s.m_major;
+                    float tt = ma;
+                    for (uint32_t j = 0;; ++j) {
+                        if (j >= MT_TRACK_STEPS) {
+                            raise_err(s, MT_EFLAG_TRACK);
+                            k = -1;  // the path is dropped
+                            break;
+                        }
+                        const uint4 R = philox4x32_10(make_uint4(m.x, m.y, m.z - 1u, G_TRACK + j), p.k0, p.k1);
+                        tt += -logf(1.0f - u24(R.x)) * inv;
+                        if (tt >= mb) break;
+                        if (u24(R.y) < density_at(s, xyz(o) + xyz(d) * tt) * inv) {
+                            collided = 1;
+                            t = tt;
+                            break;
+                        }
+                    }
+                }
+            }
+            p.hit[slot] = make_int4(k, orig, __float_as_int(t), collided);
             rays++;
         }
     }
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(256) k_wf_trace_dyn(const DevScene s, const Wf
 #define MT_WF_SHADE_MINB 3
 #endif
 
-template <bool DUMP>
+template <bool DUMP, bool MEDIA>
 __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
                                                   uint32_t *qnext) {
     const uint32_t n = p.counters[C_CUR];
@@ -382,7 +409,55 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             float opl = o4.w;
             float3 beta = xyz(b4);
             const float3 dir = xyz(d4);
-            if (h.x < 0) {
+            if (MEDIA && h.w) {
+                // scattering in the medium: albedo, next-event estimate through the medium
+                // (phase function, no MIS; the shadow stage applies the transmittance),
+                // Henyey-Greenstein continuation
+                verts++;
+                const float th = __int_as_float(h.z);
+                const float3 x = xyz(o4) + dir * th;
+                if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
+                beta = beta * s.m_params[0];
+                if (depth == p.max_depth) {
+                    done = true;
+                } else {
+                    if (s.n_units > 0) {
+                        const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_NEE), p.k0, p.k1);
+                        const int un = pick_unit_wf(s, R.x);
+                        const LightUnit U = s.units[un];
+                        const int em = __float_as_int(U.v2.w);
+                        const bool is_pt = __float_as_int(U.n.w) < 0;
+                        const float3 y = is_pt ? xyz(U.v0)
+                                               : tri_point(xyz(U.v0), xyz(U.v1), xyz(U.v2), u24(R.y), u24(R.z));
+                        const float3 dl = y - x;
+                        const float dist = sqrtf(dot(dl, dl));
+                        const float3 wi = dl * (1.0f / dist);
+                        const float cy = is_pt ? 1.0f : -dot(xyz(U.n), wi);
+                        if (cy > 0.f && dist > 0.f) {
+                            const float ph = hg_eval(s.m_params[1], dot(dir, wi));
+                            const float pick = U.v1.w;
+                            const float geo = is_pt ? 1.0f / (dist * dist) / pick : cy / (dist * dist) / (pick / U.v0.w);
+                            const float3 c = mul(beta * (ph * geo), xyz(s.em_rad[em])) * p.scale;
+                            if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
+                                shadow = true;
+                                sh_o = make_float4(x.x, x.y, x.z, dist - (is_pt ? 0.0f : eps_of(y)));
+                                sh_d = make_float4(wi.x, wi.y, wi.z,
+                                                   opl + dist + pulse_time(s, pix, smp, (uint32_t)depth, 1, p.k0,
+                                                                           p.k1));
+                                sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
+                                sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                            }
+                        }
+                    }
+                    const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_SCATTER), p.k0, p.k1);
+                    const float3 nd = hg_sample(s.m_params[1], dir, u24(R.x), u24(R.y));
+                    p.o[slot] = make_float4(x.x, x.y, x.z, opl);
+                    p.d[slot] = make_float4(nd.x, nd.y, nd.z, 0.f);
+                    p.beta[slot] = make_float4(beta.x, beta.y, beta.z, 0.f);
+                    p.meta[slot] = make_uint4(pix, smp, (uint32_t)(depth + 1), 0u);
+                    cont = true;
+                }
+            } else if (h.x < 0) {
                 done = true;
             } else {
                 verts++;
@@ -395,7 +470,8 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                 const float3 wo = -dir;
                 const float cwo = dot(ng, wo);
                 const int unit = __ldg(&s.tri_unit[orig]);
-                if (unit >= 0 && cwo > 0.f) {
+                // with a medium, emission found by the path counts only at the camera vertex
+                if (unit >= 0 && cwo > 0.f && (!MEDIA || depth == 1)) {
                     const LightUnit U = s.units[unit];
                     float w = 1.0f;
                     if (depth > 1) w = mis2w(d4.w, (U.v1.w / U.v0.w) * th * th / cwo);
@@ -442,7 +518,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                             else {
                                 const float pA = pick / U.v0.w;
                                 geo = cy / (dist * dist) / pA;
-                                w = mis2w(pA * dist * dist / cy, pb);
+                                if (!MEDIA) w = mis2w(pA * dist * dist / cy, pb);
                             }
                             const float3 c = mul(mul(beta, f) * (cx * geo * w), xyz(s.em_rad[em])) * p.scale;
                             if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
@@ -495,7 +571,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
     warp_count(&s.counters[2], contribs);
 }
 
-template <bool DUMP, bool CNT, bool WIDE>
+template <bool DUMP, bool CNT, bool WIDE, bool MEDIA>
 __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevScene s, const WfParams p) {
     const uint32_t n = p.counters[C_SHADOW];
     const int lane = threadIdx.x & 31;
@@ -519,11 +595,24 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
             if (!occluded) {
                 const float4 c = p.sh_c[i];
                 const uint32_t pix = (uint32_t)__float_as_int(c.w);
-                wf_splat(p, pix, d.w, xyz(c));
-                contribs++;
-                if (DUMP) {
+                float3 cv = xyz(c);
+                bool keep = true;
+                if (MEDIA) {
+                    // ratio-tracking transmittance of the shadow segment (Sec. 4.1)
                     const uint4 m = p.sh_m[i];
-                    wf_dump(p, pix, m.x, (int)m.y, 1, (int)m.z, d.w, xyz(c));
+                    bool ok;
+                    const float Tr = transmittance(s, Rng{p.k0, p.k1}, xyz(o), xyz(d), o.w, pix, m.x, m.y, ok);
+                    if (!ok) raise_err(s, MT_EFLAG_TRACK);
+                    keep = ok && Tr != 0.f;
+                    cv = cv * Tr;
+                }
+                if (keep) {
+                    wf_splat(p, pix, d.w, cv);
+                    contribs++;
+                    if (DUMP) {
+                        const uint4 m = p.sh_m[i];
+                        wf_dump(p, pix, m.x, (int)m.y, 1, (int)m.z, d.w, cv);
+                    }
                 }
             }
         }
@@ -617,7 +706,9 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (timing) MT_TRY(wf_event(timing, iter, 0, st));
         k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
         k_wf_generate<<<grid, 256, 0, st>>>(s, p, p.iter, qa);
-        const bool dyn = p.dynamic_fetch && !dump;
+        const bool media = s.has_medium != 0;
+        const bool dyn = p.dynamic_fetch && !dump && !media;
+        const bool wide = p.wide && !media;  // the medium forms traverse the binary tree
         const uint32_t *qext = qa;
         if (p.sort_rays && !dump) {
             k_wf_sort_keys<<<grid, 256, 0, st>>>(s, p, qa);
@@ -631,16 +722,24 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (dyn) {
             if (counters) k_wf_trace_dyn<false, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<false, false><<<grid, 256, 0, st>>>(s, p, qa);
-        } else if (p.wide) {
-            if (counters) k_wf_extend<true, true><<<grid, 256, 0, st>>>(s, p, qext);
-            else k_wf_extend<true, false><<<grid, 256, 0, st>>>(s, p, qext);
+        } else if (media) {
+            if (counters) k_wf_extend<false, true, true><<<grid, 256, 0, st>>>(s, p, qext);
+            else k_wf_extend<false, false, true><<<grid, 256, 0, st>>>(s, p, qext);
+        } else if (wide) {
+            if (counters) k_wf_extend<true, true, false><<<grid, 256, 0, st>>>(s, p, qext);
+            else k_wf_extend<true, false, false><<<grid, 256, 0, st>>>(s, p, qext);
         } else {
-            if (counters) k_wf_extend<false, true><<<grid, 256, 0, st>>>(s, p, qext);
-            else k_wf_extend<false, false><<<grid, 256, 0, st>>>(s, p, qext);
+            if (counters) k_wf_extend<false, true, false><<<grid, 256, 0, st>>>(s, p, qext);
+            else k_wf_extend<false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
         }
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
-        if (dump) k_wf_shade<true><<<grid, 256, 0, st>>>(s, p, qa, qb);
-        else k_wf_shade<false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (media) {
+            if (dump) k_wf_shade<true, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        } else {
+            if (dump) k_wf_shade<true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        }
         if (p.sh_perm) {
             k_wf_shadow_keys<<<grid, 256, 0, st>>>(s, p);
             size_t bytes = p.sort_tmp_bytes;
@@ -652,20 +751,28 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
-        } else if (p.wide) {
+        } else if (media) {
             if (dump) {
-                if (counters) k_wf_shadow<true, true, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<true, false, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<true, true, false, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<true, false, false, true><<<grid, 256, 0, st>>>(s, p);
             } else {
-                if (counters) k_wf_shadow<false, true, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, false, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, false, true><<<grid, 256, 0, st>>>(s, p);
+            }
+        } else if (wide) {
+            if (dump) {
+                if (counters) k_wf_shadow<true, true, true, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<true, false, true, false><<<grid, 256, 0, st>>>(s, p);
+            } else {
+                if (counters) k_wf_shadow<false, true, true, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, true, false><<<grid, 256, 0, st>>>(s, p);
             }
         } else if (dump) {
-            if (counters) k_wf_shadow<true, true, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<true, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<true, true, false, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<true, false, false, false><<<grid, 256, 0, st>>>(s, p);
         } else {
-            if (counters) k_wf_shadow<false, true, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<false, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<false, true, false, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<false, false, false, false><<<grid, 256, 0, st>>>(s, p);
         }
         MT_CUDA_TRY(cudaGetLastError());
         if (timing) MT_TRY(wf_event(timing, iter, 4, st));

@@ -17,12 +17,18 @@ def media(oracle_mod, scenes_mod):
     return api, sc, api.Scene(sc), oracle_mod.OracleScene(sc)
 
 
-def test_media_contributions_and_film(media):
+@pytest.mark.parametrize("form", ["megakernel", "wavefront"])
+def test_media_contributions_and_film(media, form):
     api, sc, s, osc = media
     H = W = 64
     T, start, width = 1024, 3.5, 0.005
     spp, seed, depth = 4, 25660, 8
-    film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=3_000_000)
+    if form == "wavefront":
+        s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    try:
+        film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=3_000_000)
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
     crop = (24, 40, 24, 40)
     ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=3_000_000)
     px = rec["pixel"] % W
@@ -34,6 +40,23 @@ def test_media_contributions_and_film(media):
     assert bad <= 5e-3 * nm, (bad, worst)
     f = film.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
     assert rel_l2(f.sum(2), ref["film"].sum(2)) < 0.01
+
+
+def test_media_wavefront_equals_megakernel(media):
+    """Same estimator and random numbers in both forms: equal films up to the
+    order of floating-point additions."""
+    api, sc, s, osc = media
+    H = W = 64
+    T, start, width = 512, 3.5, 0.01
+    a, sa = api.render(s, H, W, T, start, width, 16, 9, 12)
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    try:
+        b, sb = api.render(s, H, W, T, start, width, 16, 9, 12)
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-4
+    assert rel_l2(sb.cpu().numpy(), sa.cpu().numpy()) < 1e-4
 
 
 def test_medium_albedo_gradient(media):
@@ -68,5 +91,13 @@ def test_bounded_tracking_reports_timeout(api_free_scene=None):
         s.sync()
     assert e.value.status == api.MT_ERR_TIMEOUT
     # the context stays usable
+    api.render(s, 8, 8, 16, 3.5, 0.1, 1, 1, 1)
+    torch.cuda.synchronize()
+    # the wavefront form reports the same
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    api.render(s, 8, 8, 16, 3.5, 0.1, 1, 1, 2)
+    with pytest.raises(api.MtError) as e:
+        s.sync()
+    assert e.value.status == api.MT_ERR_TIMEOUT
     api.render(s, 8, 8, 16, 3.5, 0.1, 1, 1, 1)
     torch.cuda.synchronize()
