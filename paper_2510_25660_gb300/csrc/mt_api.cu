@@ -125,6 +125,7 @@ struct mt_scene_s {
     uint4 *wf_meta = nullptr, *wf_sh_m = nullptr;
     int4 *wf_hit = nullptr;
     uint32_t *wf_qa = nullptr, *wf_qb = nullptr, *wf_free = nullptr, *wf_counters = nullptr;
+    float4 *wf_sig = nullptr;  // forward-mode prefix sums of the path pool
     uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr, *wf_shperm = nullptr;  // ray reordering
     char *wf_stmp = nullptr;
     size_t wf_stmp_bytes = 0;
@@ -735,7 +736,7 @@ static mt_status check_err_word(mt_scene s) {
 
 // forward render in wavefront form: a pool of paths in device memory
 static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp, const LaunchCfg &cfg, bool dump,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool tangent = false) {
     const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
     const uint32_t P = (uint32_t)std::min<unsigned long long>(total, 1ull << 22);
     if (P > s->wf_cap) {
@@ -756,6 +757,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_TRY(al.alloc(&s->wf_sh_d, P, "shadow queue"));
         MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
         MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sig, P, "path tangent sums"));
         if (!s->wf_counters) {
             MT_TRY(al.alloc(&s->wf_counters, 8, "path queue counters"));
             MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
@@ -823,6 +825,10 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.wide = (cfg.options & MT_OPT_WIDE_BVH) ? 1 : 0;
     w.lambdas = rp.lambdas;
     w.K = rp.lambdas ? rp.K : 0;
+    w.sig = tangent ? s->wf_sig : nullptr;
+    w.dalb = rp.dalb;
+    w.drad = rp.drad;
+    w.dmed = rp.dmed;
     w.sort_rays = sort_rays ? 1 : 0;
     w.sort_keys = s->wf_sk;
     w.sort_keys_out = s->wf_sko;
@@ -904,8 +910,8 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
-    if ((mode == 0 || mode == 1 || mode == 3) && (cfg.options & MT_OPT_WAVEFRONT))
-        return render_wavefront(s, f, p, cfg, mode == 1, st);
+    if ((mode == 0 || mode == 1 || mode == 3 || mode == 4) && (cfg.options & MT_OPT_WAVEFRONT))
+        return render_wavefront(s, f, p, cfg, mode == 1, st, mode == 4);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
     s->launches += 1;
     return mt_launch_render(s->dev, p, cfg, mode, (f->flags & MT_COUNTERS) != 0, st);

@@ -85,6 +85,10 @@ struct WfParams {
     int32_t wide;                  // traverse the 8-wide BVH
     const float *lambdas;          // frequency-space film: K wavelengths (m), the film has T = 2K; K = 0: bins
     int32_t K;
+    // forward-mode derivative: per-path prefix sum of ratio * dtheta over the vertices so far, and the tangent
+    float4 *sig;
+    const float *dalb, *drad;
+    float dmed;
     // ray reordering: extension rays sorted by (direction octant, origin Morton code)
     int32_t sort_rays;
     uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue

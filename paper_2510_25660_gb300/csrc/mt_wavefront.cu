@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
         p.o[slot] = make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f);
         p.d[slot] = make_float4(d.x, d.y, d.z, 0.f);
         p.beta[slot] = make_float4(1.f, 1.f, 1.f, 0.f);
+        if (p.sig) p.sig[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
         p.meta[slot] = make_uint4(pix, smp, 1u, 0u);
         qcur[it.cont + i] = slot;
         paths++;
@@ -382,7 +383,14 @@ __global__ void __launch_bounds__(256) k_wf_trace_dyn(const DevScene s, const Wf
 #define MT_WF_SHADE_MINB 3
 #endif
 
-template <bool DUMP, bool MEDIA>
+__device__ __forceinline__ float3 drad_of(const WfParams &p, int em) {
+    return p.drad ? f3(p.drad[em * 3], p.drad[em * 3 + 1], p.drad[em * 3 + 2]) : f3(0.f, 0.f, 0.f);
+}
+
+// TAN: forward-mode derivative (Sec. 4.4): every contribution C is replaced by
+// C * (sum of ratio * dtheta over its vertices) + Cbar * dLe (the film becomes
+// the tangent film); the prefix sum of a path lives in p.sig
+template <bool DUMP, bool MEDIA, bool TAN>
 __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
                                                   uint32_t *qnext) {
     const uint32_t n = p.counters[C_CUR];
@@ -409,6 +417,8 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             float opl = o4.w;
             float3 beta = xyz(b4);
             const float3 dir = xyz(d4);
+            float3 sig = f3(0.f, 0.f, 0.f);
+            if (TAN) sig = xyz(p.sig[slot]);
             if (MEDIA && h.w) {
                 // scattering in the medium: albedo, next-event estimate through the medium
                 // (phase function, no MIS; the shadow stage applies the transmittance),
@@ -437,8 +447,14 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                             const float ph = hg_eval(s.m_params[1], dot(dir, wi));
                             const float pick = U.v1.w;
                             const float geo = is_pt ? 1.0f / (dist * dist) / pick : cy / (dist * dist) / (pick / U.v0.w);
-                            const float3 c = mul(beta * (ph * geo), xyz(s.em_rad[em])) * p.scale;
-                            if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
+                            const float3 cb = beta * (ph * geo * p.scale);
+                            float3 c = mul(cb, xyz(s.em_rad[em]));
+                            const bool nonzero = c.x != 0.f || c.y != 0.f || c.z != 0.f;
+                            if (TAN) {
+                                const float dr = p.dmed / s.m_params[0];
+                                c = mul(c, sig + f3(dr, dr, dr)) + mul(cb, drad_of(p, em));
+                            }
+                            if (nonzero) {
                                 shadow = true;
                                 sh_o = make_float4(x.x, x.y, x.z, dist - (is_pt ? 0.0f : eps_of(y)));
                                 sh_d = make_float4(wi.x, wi.y, wi.z,
@@ -451,6 +467,11 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     }
                     const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_SCATTER), p.k0, p.k1);
                     const float3 nd = hg_sample(s.m_params[1], dir, u24(R.x), u24(R.y));
+                    if (TAN) {
+                        const float dr = p.dmed / s.m_params[0];
+                        sig = sig + f3(dr, dr, dr);
+                        p.sig[slot] = make_float4(sig.x, sig.y, sig.z, 0.f);
+                    }
                     p.o[slot] = make_float4(x.x, x.y, x.z, opl);
                     p.d[slot] = make_float4(nd.x, nd.y, nd.z, 0.f);
                     p.beta[slot] = make_float4(beta.x, beta.y, beta.z, 0.f);
@@ -476,7 +497,9 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     float w = 1.0f;
                     if (depth > 1) w = mis2w(d4.w, (U.v1.w / U.v0.w) * th * th / cwo);
                     const int em = __float_as_int(U.v2.w);
-                    const float3 c = mul(beta * w, xyz(s.em_rad[em])) * p.scale;
+                    const float3 cb = beta * (w * p.scale);
+                    float3 c = mul(cb, xyz(s.em_rad[em]));
+                    if (TAN) c = mul(c, sig) + mul(cb, drad_of(p, em));
                     const float oc = opl + pulse_time(s, pix, smp, (uint32_t)depth, 0, p.k0, p.k1);
                     wf_splat(p, pix, oc, c);
                     contribs++;
@@ -520,8 +543,17 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                                 geo = cy / (dist * dist) / pA;
                                 if (!MEDIA) w = mis2w(pA * dist * dist / cy, pb);
                             }
-                            const float3 c = mul(mul(beta, f) * (cx * geo * w), xyz(s.em_rad[em])) * p.scale;
-                            if (c.x != 0.f || c.y != 0.f || c.z != 0.f) {
+                            const float3 cb = mul(beta, f) * (cx * geo * w * p.scale);
+                            float3 c = mul(cb, xyz(s.em_rad[em]));
+                            const bool nonzero = c.x != 0.f || c.y != 0.f || c.z != 0.f;
+                            if (TAN) {
+                                const float3 dv = p.dalb ? f3(p.dalb[orig * 3], p.dalb[orig * 3 + 1],
+                                                              p.dalb[orig * 3 + 2])
+                                                         : f3(0.f, 0.f, 0.f);
+                                const float3 own = mul(bsdf_dratio(mat, wol, to_local(wi, tb, bb, nn)), dv);
+                                c = mul(c, sig + own) + mul(cb, drad_of(p, em));
+                            }
+                            if (nonzero) {
                                 shadow = true;
                                 sh_o = make_float4(xo.x, xo.y, xo.z, dist - (is_pt ? 0.0f : eps_of(y)));
                                 sh_d = make_float4(wi.x, wi.y, wi.z,
@@ -541,6 +573,13 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                         bsdf_eval(mat, wol, wil, f, pb);
                         if (pb > 0.f) {
                             beta = mul(beta, f) * (wil.z / pb);
+                            if (TAN) {
+                                const float3 dv = p.dalb ? f3(p.dalb[orig * 3], p.dalb[orig * 3 + 1],
+                                                              p.dalb[orig * 3 + 2])
+                                                         : f3(0.f, 0.f, 0.f);
+                                sig = sig + mul(bsdf_dratio(mat, wol, wil), dv);
+                                p.sig[slot] = make_float4(sig.x, sig.y, sig.z, 0.f);
+                            }
                             const float3 no = x + nn * eps_of(x);
                             const float3 nd = to_world(wil, tb, bb, nn);
                             p.o[slot] = make_float4(no.x, no.y, no.z, opl);
@@ -733,12 +772,15 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_extend<false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
         }
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
-        if (media) {
-            if (dump) k_wf_shade<true, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
-            else k_wf_shade<false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (p.sig) {
+            if (media) k_wf_shade<false, true, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        } else if (media) {
+            if (dump) k_wf_shade<true, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         } else {
-            if (dump) k_wf_shade<true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
-            else k_wf_shade<false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            if (dump) k_wf_shade<true, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         }
         if (p.sh_perm) {
             k_wf_shadow_keys<<<grid, 256, 0, st>>>(s, p);

@@ -80,3 +80,34 @@ def test_medium_tangent_matches_oracle(oracle_mod, scenes_mod):
     ref = osc.render_tangent(H, W, 256, 3.5, 0.01, 4, 3, 6, dmed=1.0, crop=crop)
     assert rel_l2(ts.cpu().numpy()[28:36, 28:36], ref["steady"]) < 0.02
     assert rel_l2(tf.cpu().numpy()[28:36, 28:36].sum(2), ref["film"].sum(2)) < 0.02
+
+
+@pytest.mark.parametrize("which", ["cornell_ggx", "media"])
+def test_wavefront_tangent_equals_megakernel(scenes_mod, which):
+    """The wavefront form carries the same prefix sums per path: equal tangent
+    films up to the order of floating-point additions."""
+    import torch
+    api = build_and_load()
+    if which == "media":
+        sc = scenes_mod.media_scene(res=32)
+        kw = dict(dmedium=0.7)
+    else:
+        sc = scenes_mod.cornell_box()
+        sc.mtype[10:22] = 1
+        sc.roughness[10:22] = 0.3
+        kw = {}
+    s = api.Scene(sc)
+    gen = torch.Generator("cuda").manual_seed(4)
+    da = torch.randn((sc.n_tris, 3), device="cuda", generator=gen)
+    dr = torch.randn((len(sc.emitters), 3), device="cuda", generator=gen)
+    a, sa = api.render_tangent(s, H, W, T, START, WIDTH, SPP, SEED, 6, da, dr, **kw)
+    a, sa = a.clone(), sa.clone()
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    try:
+        b, sb = api.render_tangent(s, H, W, T, START, WIDTH, SPP, SEED, 6, da, dr, **kw)
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
+    assert a.abs().max().item() > 0
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-4
+    assert rel_l2(sb.cpu().numpy(), sa.cpu().numpy()) < 1e-4
