@@ -636,6 +636,7 @@ def secondary(api, autotune, scenes):
     g = torch.randn_like(film)
     outg = (torch.zeros((sc.n_tris, 3), device="cuda"), torch.zeros((len(sc.emitters), 3), device="cuda"),
             torch.zeros(1, device="cuda"))
+    autotune.apply(s, "backward", sc, f, 128, 16)
     bms = _timed(lambda: api.render_backward(s, f.T, f.start_opl, f.bin_width, 128, 1, 16, g, out=outg), 3)
     s.read_counters(reset=True)
     api.render_backward(s, f.T, f.start_opl, f.bin_width, 128, 1, 16, g, out=outg)

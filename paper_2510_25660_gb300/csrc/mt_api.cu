@@ -126,6 +126,10 @@ struct mt_scene_s {
     int4 *wf_hit = nullptr;
     uint32_t *wf_qa = nullptr, *wf_qb = nullptr, *wf_free = nullptr, *wf_counters = nullptr;
     float4 *wf_sig = nullptr;  // forward-mode prefix sums of the path pool
+    float4 *wf_rec = nullptr;   // path replay: vertex records (3 x [max_depth + 1][P])
+    uint32_t *wf_fin = nullptr;
+    float4 *wf_shown = nullptr;
+    size_t wf_rec_cap = 0;      // float4s per record array
     uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr, *wf_shperm = nullptr;  // ray reordering
     char *wf_stmp = nullptr;
     size_t wf_stmp_bytes = 0;
@@ -736,7 +740,7 @@ static mt_status check_err_word(mt_scene s) {
 
 // forward render in wavefront form: a pool of paths in device memory
 static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp, const LaunchCfg &cfg, bool dump,
-                                  cudaStream_t st, bool tangent = false) {
+                                  cudaStream_t st, bool tangent = false, bool backward = false) {
     const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
     const uint32_t P = (uint32_t)std::min<unsigned long long>(total, 1ull << 22);
     if (P > s->wf_cap) {
@@ -764,6 +768,22 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
             MT_TRY(al.alloc((char **)&s->wf_iter, 64, "path queue counters"));
         }
         s->wf_cap = P;
+    }
+    if (backward) {
+        const size_t need = (size_t)(rp.max_depth + 1) * P;
+        if (need > s->wf_rec_cap) {
+            cudaStreamCaptureStatus cs;
+            MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+            MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                         "the first wavefront backward pass of this size must not be captured (it sizes the records)");
+            auto &al = s->al;
+            MT_TRY(al.alloc(&s->wf_rec, 3 * need, "path replay vertex records"));
+            if (!s->wf_fin) {
+                MT_TRY(al.alloc(&s->wf_fin, (size_t)(1u << 22), "path replay queue"));
+                MT_TRY(al.alloc(&s->wf_shown, (size_t)(1u << 22), "path replay shadow records"));
+            }
+            s->wf_rec_cap = need;
+        }
     }
     const bool sort_rays = (cfg.options & MT_OPT_SORT_RAYS) != 0;
     const bool sort_shadow = (cfg.options & MT_OPT_SORT_SHADOW) != 0 && !dump;
@@ -829,6 +849,20 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.dalb = rp.dalb;
     w.drad = rp.drad;
     w.dmed = rp.dmed;
+    w.bwd = backward ? 1 : 0;
+    if (backward) {
+        const size_t cap = s->wf_rec_cap;
+        w.rec_a = s->wf_rec;
+        w.rec_b = s->wf_rec + cap;
+        w.rec_c = s->wf_rec + 2 * cap;
+        w.fin_q = s->wf_fin;
+        w.sh_cb = s->wf_shown;
+        w.gfilm = rp.gfilm;
+        w.gsteady = rp.gsteady;
+        w.galb = rp.galb;
+        w.grad = rp.grad;
+        w.gmed = rp.gmed;
+    }
     w.sort_rays = sort_rays ? 1 : 0;
     w.sort_keys = s->wf_sk;
     w.sort_keys_out = s->wf_sko;
@@ -836,7 +870,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.sort_tmp = s->wf_stmp;
     w.sort_tmp_bytes = s->wf_stmp_bytes;
     w.sh_perm = sort_shadow ? s->wf_shperm : nullptr;
-    if (!(rp.flags & MT_ACCUMULATE)) {
+    if (!(rp.flags & MT_ACCUMULATE) && !backward) {  // a backward pass reads dL/dfilm from the film
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
     }
@@ -910,8 +944,8 @@ static mt_status render_common(mt_scene s, mt_film f, int32_t spp, uint64_t seed
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
     }
     if (dump) MT_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(int64_t), st));
-    if ((mode == 0 || mode == 1 || mode == 3 || mode == 4) && (cfg.options & MT_OPT_WAVEFRONT))
-        return render_wavefront(s, f, p, cfg, mode == 1, st, mode == 4);
+    if ((mode == 0 || mode == 1 || mode == 2 || mode == 3 || mode == 4) && (cfg.options & MT_OPT_WAVEFRONT))
+        return render_wavefront(s, f, p, cfg, mode == 1, st, mode == 4, mode == 2);
     MT_CUDA_TRY(cudaMemsetAsync(s->tile_counter, 0, sizeof(int), st));
     s->launches += 1;
     return mt_launch_render(s->dev, p, cfg, mode, (f->flags & MT_COUNTERS) != 0, st);

@@ -89,6 +89,15 @@ struct WfParams {
     float4 *sig;
     const float *dalb, *drad;
     float dmed;
+    // path replay (backward): vertex records [vertex][slot] (a: ratio of the continuation + triangle bits,
+    // b: sum of g * C of contributions made at the vertex, c: own next-event term), the queue of paths
+    // that ended in this iteration, gradient inputs and outputs
+    int32_t bwd;
+    float4 *rec_a, *rec_b, *rec_c;
+    uint32_t *fin_q;
+    const float *gfilm, *gsteady;
+    float *galb, *grad, *gmed;
+    float4 *sh_cb;                 // backward shadow records: own ratio of the next-event direction
     // ray reordering: extension rays sorted by (direction octant, origin Morton code)
     int32_t sort_rays;
     uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue

@@ -29,7 +29,7 @@ struct WfIter {
 namespace {
 
 // counters[] layout
-enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_PAD = 7 };
+enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_FIN = 7 };
 
 __device__ __forceinline__ float mis2w(float a, float b) { return a * a / (a * a + b * b); }
 
@@ -113,6 +113,80 @@ __device__ __forceinline__ void wf_dump(const WfParams &p, uint32_t pix, uint32_
     }
 }
 
+// dL/dfilm at the bin of a contribution at `opl` plus dL/dsteady (backward)
+__device__ __forceinline__ float3 wf_grad_at(const WfParams &p, uint32_t pix, float opl) {
+    const uint32_t lp = pix - p.pix_base;
+    float3 g = p.gsteady ? f3(p.gsteady[lp * 3], p.gsteady[lp * 3 + 1], p.gsteady[lp * 3 + 2]) : f3(0.f, 0.f, 0.f);
+    const float x = (opl - p.start) / p.width;
+    if (x >= 0.f && x < (float)p.T) {
+        const float *h = p.gfilm + ((size_t)lp * p.T + (int)x) * 3;
+        g = g + f3(h[0], h[1], h[2]);
+    }
+    return g;
+}
+
+#define MT_WF_EM_SMEM 64  // emitters whose radiance gradients a CTA sums in shared memory
+
+__device__ __forceinline__ void em_grad_add(const WfParams &p, float *em_acc, int n_em, int em, float3 v) {
+    if (n_em <= MT_WF_EM_SMEM) {
+        atomicAdd(&em_acc[em * 3], v.x);
+        atomicAdd(&em_acc[em * 3 + 1], v.y);
+        atomicAdd(&em_acc[em * 3 + 2], v.z);
+    } else {
+        atomicAdd(&p.grad[em * 3], v.x);
+        atomicAdd(&p.grad[em * 3 + 1], v.y);
+        atomicAdd(&p.grad[em * 3 + 2], v.z);
+    }
+}
+
+__device__ __forceinline__ void em_grad_flush(const WfParams &p, const float *em_acc, int n_em) {
+    __syncthreads();
+    if (n_em <= MT_WF_EM_SMEM)
+        for (int k = threadIdx.x; k < n_em * 3; k += blockDim.x)
+            if (em_acc[k] != 0.f) atomicAdd(&p.grad[k], em_acc[k]);
+}
+
+// Paths that ended in this iteration (after their shadow rays were traced):
+// suffix sums over the vertex records turn the per-vertex sums of g * C into
+// the albedo and medium-albedo gradients (Sec. 4.4 path replay), then the slot
+// returns to the free stack.
+__global__ void __launch_bounds__(256) k_wf_finalize(const DevScene s, const WfParams p) {
+    const uint32_t n = p.counters[C_FIN];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t n_round = ((n + 31u) / 32u) * 32u;
+    float gm = 0.f;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_round; q += stride) {
+        const bool valid = q < n;
+        uint32_t slot = 0;
+        if (valid) {
+            slot = p.fin_q[q];
+            const int end = (int)p.meta[slot].w;
+            float3 P = f3(0.f, 0.f, 0.f);
+            for (int i = end; i >= 1; --i) {
+                const size_t r = (size_t)i * p.P + slot;
+                const float4 a = p.rec_a[r], b = p.rec_b[r], c = p.rec_c[r];
+                const float3 gi = mul(P, xyz(a)) + xyz(c);
+                const int tri = __float_as_int(a.w);
+                if (tri >= 0) {
+                    if (gi.x != 0.f || gi.y != 0.f || gi.z != 0.f) {
+                        float *g = p.galb + (size_t)tri * 3;
+                        atomicAdd(g, gi.x);
+                        atomicAdd(g + 1, gi.y);
+                        atomicAdd(g + 2, gi.z);
+                    }
+                } else {
+                    gm += gi.x + gi.y + gi.z;
+                }
+                P = P + xyz(b);
+            }
+        }
+        const uint32_t fs = wf_append(&p.counters[C_FREE], valid);
+        if (valid) p.free_q[fs] = slot;
+    }
+    for (int o = 16; o > 0; o >>= 1) gm += __shfl_xor_sync(0xffffffffu, gm, o);
+    if ((threadIdx.x & 31) == 0 && gm != 0.f && p.gmed) atomicAdd(p.gmed, gm);
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_count(unsigned long long *dst, T v) {
     unsigned long long x = v;
@@ -136,6 +210,7 @@ __global__ void k_wf_setup(WfParams p, WfIter *it) {
     c[C_FREE] = freec - n_new;
     c[C_EXT_CUR] = 0;
     c[C_SH_CUR] = 0;
+    c[C_FIN] = 0;
     c[C_DONE] = (cont + n_new == 0) ? 1u : 0u;
     *p.next_path = base + n_new;
 }
@@ -389,10 +464,19 @@ __device__ __forceinline__ float3 drad_of(const WfParams &p, int em) {
 
 // TAN: forward-mode derivative (Sec. 4.4): every contribution C is replaced by
 // C * (sum of ratio * dtheta over its vertices) + Cbar * dLe (the film becomes
-// the tangent film); the prefix sum of a path lives in p.sig
-template <bool DUMP, bool MEDIA, bool TAN>
+// the tangent film); the prefix sum of a path lives in p.sig.
+// BWD: path replay (Sec. 4.4): each vertex records the ratio of its
+// continuation and the sum of g * C of the contributions made there (light found
+// here; the next-event term is added by the shadow stage), paths that end go to
+// the finalize queue; radiance gradients are summed per CTA.
+template <bool DUMP, bool MEDIA, bool TAN, bool BWD>
 __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevScene s, const WfParams p, const uint32_t *qcur,
                                                   uint32_t *qnext) {
+    __shared__ float em_acc[BWD ? MT_WF_EM_SMEM * 3 : 1];
+    if (BWD) {
+        for (int k = threadIdx.x; k < MT_WF_EM_SMEM * 3; k += blockDim.x) em_acc[k] = 0.f;
+        __syncthreads();
+    }
     const uint32_t n = p.counters[C_CUR];
     uint32_t verts = 0, contribs = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -402,7 +486,10 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
         bool valid = i < n;
         const uint32_t slot = valid ? qcur[i] : 0u;
         bool cont = false, shadow = false, done = false;
-        float4 sh_o = make_float4(0, 0, 0, 0), sh_d = sh_o, sh_c = sh_o;
+        float4 sh_o = make_float4(0, 0, 0, 0), sh_d = sh_o, sh_c = sh_o, sh_own = sh_o;
+        int end = 0;  // BWD: the path's last vertex
+        float3 Sv = f3(0.f, 0.f, 0.f), rv = f3(0.f, 0.f, 0.f);  // BWD: record of this vertex
+        int rtri = -2;
         uint4 sh_m = make_uint4(0, 0, 0, 0);
         float4 o4 = sh_o, d4 = sh_o, b4 = sh_o;
         uint4 m = sh_m;
@@ -419,11 +506,14 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             const float3 dir = xyz(d4);
             float3 sig = f3(0.f, 0.f, 0.f);
             if (TAN) sig = xyz(p.sig[slot]);
+            end = depth - 1;
             if (MEDIA && h.w) {
                 // scattering in the medium: albedo, next-event estimate through the medium
                 // (phase function, no MIS; the shadow stage applies the transmittance),
                 // Henyey-Greenstein continuation
                 verts++;
+                rtri = -1;
+                end = depth;
                 const float th = __int_as_float(h.z);
                 const float3 x = xyz(o4) + dir * th;
                 if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
@@ -460,8 +550,15 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                                 sh_d = make_float4(wi.x, wi.y, wi.z,
                                                    opl + dist + pulse_time(s, pix, smp, (uint32_t)depth, 1, p.k0,
                                                                            p.k1));
-                                sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
-                                sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                                if (BWD) {
+                                    const float ia = 1.0f / s.m_params[0];
+                                    sh_c = make_float4(cb.x, cb.y, cb.z, __int_as_float((int)pix));
+                                    sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)em, slot);
+                                    sh_own = make_float4(ia, ia, ia, 0.f);
+                                } else {
+                                    sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
+                                    sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                                }
                             }
                         }
                     }
@@ -471,6 +568,10 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                         const float dr = p.dmed / s.m_params[0];
                         sig = sig + f3(dr, dr, dr);
                         p.sig[slot] = make_float4(sig.x, sig.y, sig.z, 0.f);
+                    }
+                    if (BWD) {
+                        const float ia = 1.0f / s.m_params[0];
+                        rv = f3(ia, ia, ia);
                     }
                     p.o[slot] = make_float4(x.x, x.y, x.z, opl);
                     p.d[slot] = make_float4(nd.x, nd.y, nd.z, 0.f);
@@ -482,6 +583,8 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                 done = true;
             } else {
                 verts++;
+                rtri = h.y;
+                end = depth;
                 const int k = h.x, orig = h.y;
                 const float th = __int_as_float(h.z);
                 const float3 x = xyz(o4) + dir * th;
@@ -501,7 +604,13 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     float3 c = mul(cb, xyz(s.em_rad[em]));
                     if (TAN) c = mul(c, sig) + mul(cb, drad_of(p, em));
                     const float oc = opl + pulse_time(s, pix, smp, (uint32_t)depth, 0, p.k0, p.k1);
-                    wf_splat(p, pix, oc, c);
+                    if (BWD) {
+                        const float3 g = wf_grad_at(p, pix, oc);
+                        Sv = Sv + mul(g, c);
+                        em_grad_add(p, em_acc, s.n_em, em, mul(g, cb));
+                    } else {
+                        wf_splat(p, pix, oc, c);
+                    }
                     contribs++;
                     if (DUMP) wf_dump(p, pix, smp, depth, 0, orig, oc, c);
                 }
@@ -559,8 +668,15 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                                 sh_d = make_float4(wi.x, wi.y, wi.z,
                                                    opl + dist + pulse_time(s, pix, smp, (uint32_t)depth, 1, p.k0,
                                                                            p.k1));
-                                sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
-                                sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                                if (BWD) {
+                                    const float3 own = bsdf_dratio(mat, wol, to_local(wi, tb, bb, nn));
+                                    sh_c = make_float4(cb.x, cb.y, cb.z, __int_as_float((int)pix));
+                                    sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)em, slot);
+                                    sh_own = make_float4(own.x, own.y, own.z, 0.f);
+                                } else {
+                                    sh_c = make_float4(c.x, c.y, c.z, __int_as_float((int)pix));
+                                    sh_m = make_uint4(smp, (uint32_t)depth, (uint32_t)__float_as_int(U.n.w), 0u);
+                                }
                             }
                         }
                     }
@@ -573,6 +689,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                         bsdf_eval(mat, wol, wil, f, pb);
                         if (pb > 0.f) {
                             beta = mul(beta, f) * (wil.z / pb);
+                            if (BWD) rv = bsdf_dratio(mat, wol, wil);
                             if (TAN) {
                                 const float3 dv = p.dalb ? f3(p.dalb[orig * 3], p.dalb[orig * 3 + 1],
                                                               p.dalb[orig * 3 + 2])
@@ -593,25 +710,46 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                 }
             }
         }
+        if (BWD && valid && end >= 1 && end == (int)m.z) {
+            // the record of this vertex (the shadow stage adds its next-event term)
+            const size_t r = (size_t)m.z * p.P + slot;
+            p.rec_a[r] = make_float4(rv.x, rv.y, rv.z, __int_as_float(rtri));
+            p.rec_b[r] = make_float4(Sv.x, Sv.y, Sv.z, 0.f);
+            p.rec_c[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const uint32_t qs = wf_append(&p.counters[C_NEXT], cont);
         if (cont) qnext[qs] = slot;
-        const uint32_t fs = wf_append(&p.counters[C_FREE], done);
-        if (done) p.free_q[fs] = slot;
+        const uint32_t fs = wf_append(&p.counters[BWD ? C_FIN : C_FREE], done);
+        if (done) {
+            if (BWD) {
+                p.fin_q[fs] = slot;
+                p.meta[slot] = make_uint4(m.x, m.y, m.z, (uint32_t)end);
+            } else {
+                p.free_q[fs] = slot;
+            }
+        }
         const uint32_t ss = wf_append(&p.counters[C_SHADOW], shadow);
         if (shadow) {
             p.sh_o[ss] = sh_o;
             p.sh_d[ss] = sh_d;
             p.sh_c[ss] = sh_c;
             p.sh_m[ss] = sh_m;
+            if (BWD) p.sh_cb[ss] = sh_own;
         }
         (void)valid;
     }
     warp_count(&s.counters[0], verts);
     warp_count(&s.counters[2], contribs);
+    if (BWD) em_grad_flush(p, em_acc, s.n_em);
 }
 
-template <bool DUMP, bool CNT, bool WIDE, bool MEDIA>
+template <bool DUMP, bool CNT, bool WIDE, bool MEDIA, bool BWD>
 __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevScene s, const WfParams p) {
+    __shared__ float em_acc[BWD ? MT_WF_EM_SMEM * 3 : 1];
+    if (BWD) {
+        for (int k = threadIdx.x; k < MT_WF_EM_SMEM * 3; k += blockDim.x) em_acc[k] = 0.f;
+        __syncthreads();
+    }
     const uint32_t n = p.counters[C_SHADOW];
     const int lane = threadIdx.x & 31;
     TraceCnt tc{0, 0};
@@ -645,7 +783,21 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
                     keep = ok && Tr != 0.f;
                     cv = cv * Tr;
                 }
-                if (keep) {
+                if (keep && BWD) {
+                    // path replay: the next-event contribution of vertex m.y of the path in slot m.w
+                    // (the record holds Cbar; C = Cbar * L_e)
+                    const uint4 m = p.sh_m[i];
+                    const float3 cc = mul(cv, xyz(s.em_rad[m.z]));
+                    const float3 g = wf_grad_at(p, pix, d.w);
+                    const float3 gc = mul(g, cc);
+                    const size_t r = (size_t)m.y * p.P + m.w;
+                    const float4 b = p.rec_b[r], c2 = p.rec_c[r];
+                    const float3 own = mul(gc, xyz(p.sh_cb[i]));
+                    p.rec_b[r] = make_float4(b.x + gc.x, b.y + gc.y, b.z + gc.z, b.w);
+                    p.rec_c[r] = make_float4(c2.x + own.x, c2.y + own.y, c2.z + own.z, c2.w);
+                    em_grad_add(p, em_acc, s.n_em, (int)m.z, mul(g, cv));
+                    contribs++;
+                } else if (keep) {
                     wf_splat(p, pix, d.w, cv);
                     contribs++;
                     if (DUMP) {
@@ -662,6 +814,7 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
         warp_count(&s.counters[4], tc.nodes);
         warp_count(&s.counters[5], tc.tris);
     }
+    if (BWD) em_grad_flush(p, em_acc, s.n_em);
 }
 
 __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsigned long long *next_path) {
@@ -746,8 +899,8 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
         k_wf_generate<<<grid, 256, 0, st>>>(s, p, p.iter, qa);
         const bool media = s.has_medium != 0;
-        const bool dyn = p.dynamic_fetch && !dump && !media;
-        const bool wide = p.wide && !media;  // the medium forms traverse the binary tree
+        const bool dyn = p.dynamic_fetch && !dump && !media && !p.bwd;
+        const bool wide = p.wide && !media && !p.bwd;  // the medium and replay forms traverse the binary tree
         const uint32_t *qext = qa;
         if (p.sort_rays && !dump) {
             k_wf_sort_keys<<<grid, 256, 0, st>>>(s, p, qa);
@@ -772,15 +925,18 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_extend<false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
         }
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
-        if (p.sig) {
-            if (media) k_wf_shade<false, true, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
-            else k_wf_shade<false, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        if (p.bwd) {
+            if (media) k_wf_shade<false, true, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
+        } else if (p.sig) {
+            if (media) k_wf_shade<false, true, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         } else if (media) {
-            if (dump) k_wf_shade<true, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
-            else k_wf_shade<false, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            if (dump) k_wf_shade<true, true, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, true, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         } else {
-            if (dump) k_wf_shade<true, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
-            else k_wf_shade<false, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            if (dump) k_wf_shade<true, false, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
+            else k_wf_shade<false, false, false, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         }
         if (p.sh_perm) {
             k_wf_shadow_keys<<<grid, 256, 0, st>>>(s, p);
@@ -790,31 +946,41 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             *launches += 1;
         }
         if (timing) MT_TRY(wf_event(timing, iter, 3, st));
-        if (dyn) {
+        if (p.bwd) {
+            if (media) {
+                if (counters) k_wf_shadow<false, true, false, true, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, false, true, true><<<grid, 256, 0, st>>>(s, p);
+            } else {
+                if (counters) k_wf_shadow<false, true, false, false, true><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, false, false, true><<<grid, 256, 0, st>>>(s, p);
+            }
+            k_wf_finalize<<<grid, 256, 0, st>>>(s, p);
+            *launches += 1;
+        } else if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
         } else if (media) {
             if (dump) {
-                if (counters) k_wf_shadow<true, true, false, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<true, false, false, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<true, true, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<true, false, false, true, false><<<grid, 256, 0, st>>>(s, p);
             } else {
-                if (counters) k_wf_shadow<false, true, false, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, false, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, false, true, false><<<grid, 256, 0, st>>>(s, p);
             }
         } else if (wide) {
             if (dump) {
-                if (counters) k_wf_shadow<true, true, true, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<true, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<true, true, true, false, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<true, false, true, false, false><<<grid, 256, 0, st>>>(s, p);
             } else {
-                if (counters) k_wf_shadow<false, true, true, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, true, false, false><<<grid, 256, 0, st>>>(s, p);
+                else k_wf_shadow<false, false, true, false, false><<<grid, 256, 0, st>>>(s, p);
             }
         } else if (dump) {
-            if (counters) k_wf_shadow<true, true, false, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<true, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<true, true, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<true, false, false, false, false><<<grid, 256, 0, st>>>(s, p);
         } else {
-            if (counters) k_wf_shadow<false, true, false, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<false, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<false, true, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            else k_wf_shadow<false, false, false, false, false><<<grid, 256, 0, st>>>(s, p);
         }
         MT_CUDA_TRY(cudaGetLastError());
         if (timing) MT_TRY(wf_event(timing, iter, 4, st));

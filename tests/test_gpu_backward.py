@@ -130,3 +130,35 @@ def test_autograd_function(setup):
     ga, gr, _ = api.render_backward(s, T, START, WIDTH, 4, 9, 4, g.contiguous(), torch.ones_like(steady))
     assert torch.allclose(alb.grad, ga, rtol=1e-4, atol=1e-7)
     assert torch.allclose(rad.grad, gr[:1], rtol=1e-4)
+
+
+@pytest.mark.parametrize("which", ["cornell_ggx", "media"])
+def test_wavefront_backward_equals_megakernel(setup, scenes_mod, which):
+    """The wavefront replay (vertex records in the path pool, suffix sums when a
+    path ends) gives the megakernel's gradients on the same paths."""
+    import torch
+    api = setup[0]
+    if which == "media":
+        sc = scenes_mod.media_scene(res=32)
+        depth = 8
+    else:
+        sc = setup[1]
+        depth = 4
+    s = api.Scene(sc)
+    gen = torch.Generator("cuda").manual_seed(5)
+    gf = torch.randn((H, W, T, 3), device="cuda", generator=gen)
+    gs = torch.randn((H, W, 3), device="cuda", generator=gen)
+    a = api.render_backward(s, T, START, WIDTH, 8, 21, depth, gf, gs)
+    a = [x.clone() for x in a]
+    s.set_launch(api.MT_LAUNCH_BACKWARD, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    try:
+        b = api.render_backward(s, T, START, WIDTH, 8, 21, depth, gf, gs)
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_BACKWARD)
+    ga, gb = a[0].cpu().numpy(), b[0].cpu().numpy()
+    assert np.abs(ga).max() > 0
+    assert np.linalg.norm(gb - ga) < 1e-4 * np.linalg.norm(ga)
+    assert np.linalg.norm(b[1].cpu().numpy() - a[1].cpu().numpy()) < 1e-4 * np.linalg.norm(a[1].cpu().numpy())
+    if which == "media":
+        assert abs(b[2].item() - a[2].item()) < 1e-4 * abs(a[2].item())
