@@ -699,6 +699,7 @@ def secondary(api, autotune, scenes):
     f = scenes.DIFF_FILM
     s = api.Scene(sc)
     autotune.apply(s, "backward", sc, f, 64, 8)
+    autotune.apply(s, "render", sc, f, 64, 8)
     film, steady = api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 64, 1, 8)
     g = torch.randn_like(film)
     gs = torch.randn_like(steady)
