@@ -390,11 +390,10 @@ mt_status mt_microbench(int32_t kind, void *d_buf, int64_t bytes, int32_t iters,
  * cannot allocate device memory at the time they render.  mt_render_nlos
  * allocates (with cudaMalloc) a hidden-surface table the first time it sees a
  * hidden triangle range and grows a per-scene sample buffer the first time it
- * sees a larger exhaustive grid.  That fails or is unwelcome for code recording
- * a CUDA graph (cudaMalloc is not allowed while a stream is being captured),
- * for applications whose device memory is reserved up front by their own
- * allocator or a fixed budget, and for loops that must not stall on an
- * allocation.  mt_render_nlos_noalloc computes the same impulse responses as
+ * sees a larger exhaustive grid.  That fails or is unwelcome for applications
+ * whose device memory is reserved up front by their own allocator or a fixed
+ * budget (a cudaMalloc outside that pool can fail once the budget is taken),
+ * and for render loops that must not stall on an allocation.  mt_render_nlos_noalloc computes the same impulse responses as
  * mt_render_nlos (same arguments, same result up to the order of
  * floating-point additions) but keeps its per-call scratch in one static
  * device array of 4.75 MiB compiled into libmt.so, which every GPU that loads

@@ -130,6 +130,8 @@ struct mt_scene_s {
     uint32_t *wf_fin = nullptr;
     float4 *wf_shown = nullptr;
     size_t wf_rec_cap = 0;      // float4s per record array
+    float4 *wf_mueller = nullptr, *wf_xframe = nullptr, *wf_shs = nullptr;  // polarization state of the pool
+    uint32_t wf_pol_cap = 0;
     uint32_t *wf_sk = nullptr, *wf_sko = nullptr, *wf_sq = nullptr, *wf_shperm = nullptr;  // ray reordering
     char *wf_stmp = nullptr;
     size_t wf_stmp_bytes = 0;
@@ -740,7 +742,8 @@ static mt_status check_err_word(mt_scene s) {
 
 // forward render in wavefront form: a pool of paths in device memory
 static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp, const LaunchCfg &cfg, bool dump,
-                                  cudaStream_t st, bool tangent = false, bool backward = false) {
+                                  cudaStream_t st, bool tangent = false, bool backward = false,
+                                  bool polarized = false) {
     const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
     const uint32_t P = (uint32_t)std::min<unsigned long long>(total, 1ull << 22);
     if (P > s->wf_cap) {
@@ -785,8 +788,20 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
             s->wf_rec_cap = need;
         }
     }
-    const bool sort_rays = (cfg.options & MT_OPT_SORT_RAYS) != 0;
-    const bool sort_shadow = (cfg.options & MT_OPT_SORT_SHADOW) != 0 && !dump;
+    if (polarized && P > s->wf_pol_cap) {
+        cudaStreamCaptureStatus cs;
+        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                     "the first polarized wavefront render of this size must not be captured (it sizes the pool)");
+        auto &al = s->al;
+        MT_TRY(al.alloc(&s->wf_mueller, (size_t)12 * P, "path Mueller matrices"));
+        MT_TRY(al.alloc(&s->wf_xframe, P, "path Stokes frames"));
+        MT_TRY(al.alloc(&s->wf_shs, (size_t)3 * P, "shadow Stokes records"));
+        s->wf_pol_cap = P;
+    }
+    // the polarized stages read neither ray order
+    const bool sort_rays = (cfg.options & MT_OPT_SORT_RAYS) != 0 && !polarized;
+    const bool sort_shadow = (cfg.options & MT_OPT_SORT_SHADOW) != 0 && !dump && !polarized;
     if ((sort_rays || sort_shadow) && P > s->wf_sort_cap) {
         cudaStreamCaptureStatus cs;
         MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
@@ -870,7 +885,13 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.sort_tmp = s->wf_stmp;
     w.sort_tmp_bytes = s->wf_stmp_bytes;
     w.sh_perm = sort_shadow ? s->wf_shperm : nullptr;
-    if (!(rp.flags & MT_ACCUMULATE) && !backward) {  // a backward pass reads dL/dfilm from the film
+    if (polarized) {
+        w.mueller = s->wf_mueller;
+        w.xframe = s->wf_xframe;
+        w.sh_s = s->wf_shs;
+    }
+    // a backward pass reads dL/dfilm from the film; polarized films (C = 12) are cleared by the caller
+    if (!(rp.flags & MT_ACCUMULATE) && !backward && !polarized) {
         MT_CUDA_TRY(cudaMemsetAsync(f->film, 0, (size_t)f->H * f->W * f->T * 3 * sizeof(float), st));
         if (f->steady) MT_CUDA_TRY(cudaMemsetAsync(f->steady, 0, (size_t)f->H * f->W * 3 * sizeof(float), st));
     }
@@ -977,6 +998,28 @@ mt_status mt_render_polarized(mt_scene s, mt_film f, int32_t spp, uint64_t seed,
     }
     uint32_t k0, k1;
     seed_key(seed, k0, k1);
+    const LaunchCfg &cfg = s->cfg[MT_LAUNCH_RENDER];
+    if (cfg.options & MT_OPT_WAVEFRONT) {  // the render configuration selects the form
+        RenderParams p{};
+        p.H = f->H;
+        p.W = f->W;
+        p.H_full = f->H_full;
+        p.row0 = f->row0;
+        p.pix_base = (uint32_t)f->row0 * (uint32_t)f->W;
+        p.T = f->T;
+        p.start = f->start;
+        p.width = f->width;
+        p.scale = acc ? 1.0f : 1.0f / (float)spp;
+        p.flags = f->flags;
+        p.spp = spp;
+        p.max_depth = max_depth;
+        p.sample_offset = (uint32_t)sample_offset;
+        p.k0 = k0;
+        p.k1 = k1;
+        p.film = f->film;
+        p.steady = f->steady;
+        return render_wavefront(s, f, p, cfg, false, st, false, false, true);
+    }
     s->launches += 1;
     return mt_launch_polarized(s->dev, f->H, f->W, f->T, f->H_full, f->row0, f->start, f->width,
                                acc ? 1.0f : 1.0f / (float)spp,

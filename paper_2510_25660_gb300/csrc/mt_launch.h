@@ -98,6 +98,10 @@ struct WfParams {
     const float *gfilm, *gsteady;
     float *galb, *grad, *gmed;
     float4 *sh_cb;                 // backward shadow records: own ratio of the next-event direction
+    // polarization: per path a 4x4 Mueller throughput per colour (12 float4 rows) and the frame vector
+    // of its current segment; shadow records carry a Stokes vector per colour (3 float4); the film is
+    // [H][W][T][4][3]
+    float4 *mueller, *xframe, *sh_s;
     // ray reordering: extension rays sorted by (direction octant, origin Morton code)
     int32_t sort_rays;
     uint32_t *sort_keys, *sort_keys_out, *sort_q;  // [P] each; sort_q = the sorted queue

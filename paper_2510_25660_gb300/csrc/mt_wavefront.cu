@@ -20,6 +20,7 @@
 #include "mt_internal.h"
 #include "mt_launch.h"
 #include "mt_trace.cuh"
+#include "mt_polar.cuh"
 
 struct WfIter {
     uint32_t cont, n_new, free_before;
@@ -237,6 +238,16 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
         p.d[slot] = make_float4(d.x, d.y, d.z, 0.f);
         p.beta[slot] = make_float4(1.f, 1.f, 1.f, 0.f);
         if (p.sig) p.sig[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p.mueller) {  // P = identity per colour, frame = the camera's horizontal axis
+#pragma unroll
+            for (int e = 0; e < 12; ++e) {
+                const int row = e & 3;
+                p.mueller[(size_t)slot * 12 + e] =
+                    make_float4(row == 0 ? 1.f : 0.f, row == 1 ? 1.f : 0.f, row == 2 ? 1.f : 0.f, row == 3 ? 1.f : 0.f);
+            }
+            const float3 xf = normalize(s.cam_r - d * dot(s.cam_r, d));
+            p.xframe[slot] = make_float4(xf.x, xf.y, xf.z, 0.f);
+        }
         p.meta[slot] = make_uint4(pix, smp, 1u, 0u);
         qcur[it.cont + i] = slot;
         paths++;
@@ -340,6 +351,299 @@ __global__ void k_wf_sort_keys(const DevScene s, const WfParams p, const uint32_
             p.sort_keys[i] = 0xFFFFFFFFu;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Transient polarization in wavefront form (Sec. 4.2): the estimator of the
+// path-per-thread kernel k_render_pol (mt_polar.cu) with each path's Mueller
+// throughput (3 colours x 4 rows) and segment frame kept in the path pool.
+// Shade adds emission Stokes vectors and queues next-event rays with their
+// Stokes contributions; the shadow stage splats those that are unoccluded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void wf_splat_stokes(const WfParams &p, uint32_t pix, float opl, const float S[3][4]) {
+    const uint32_t lp = pix - p.pix_base;
+    const float x = (opl - p.start) / p.width;
+    const bool in = x >= 0.f && x < (float)p.T;
+    float *f = in ? p.film + ((size_t)lp * p.T + (int)x) * 12 : nullptr;
+    float *st = p.steady + (size_t)lp * 12;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = S[c][k];
+            if (v != 0.f) {
+                if (in) atomicAdd(f + k * 3 + c, v);
+                atomicAdd(st + k * 3 + c, v);
+            }
+        }
+}
+
+__device__ __forceinline__ void load_mueller(const WfParams &p, uint32_t slot, Mueller &P) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 v = p.mueller[(size_t)slot * 12 + c * 4 + r];
+            P.m[c][4 * r] = v.x;
+            P.m[c][4 * r + 1] = v.y;
+            P.m[c][4 * r + 2] = v.z;
+            P.m[c][4 * r + 3] = v.w;
+        }
+}
+
+__device__ __forceinline__ void store_mueller(const WfParams &p, uint32_t slot, const Mueller &P) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            p.mueller[(size_t)slot * 12 + c * 4 + r] =
+                make_float4(P.m[c][4 * r], P.m[c][4 * r + 1], P.m[c][4 * r + 2], P.m[c][4 * r + 3]);
+}
+
+// GGX microfacet factor D G2 / (4 cos_o cos_i) and the cosine of the microfacet
+// incidence (conductor branch of the Mueller BSDF)
+__device__ __forceinline__ float ggx_factor(float rough, float3 wol, float3 wil, float &cd) {
+    const float a = fmaxf(rough, 1e-4f), a2 = a * a;
+    const float3 hh = normalize(wol + wil);
+    const float kd = (hh.x * hh.x + hh.y * hh.y) + a2 * (hh.z * hh.z);
+    const float D = a2 / (MT_PI * kd * kd);
+    const float G2 = 1.0f / (1.0f + ggx_lambda(a2, wol) + ggx_lambda(a2, wil));
+    cd = dot(wil, hh);
+    return D * G2 / (4.0f * wol.z * wil.z);
+}
+
+__global__ void __launch_bounds__(128) k_wf_shade_pol(const DevScene s, const WfParams p, const uint32_t *qcur,
+                                                     uint32_t *qnext) {
+    const uint32_t n = p.counters[C_CUR];
+    uint32_t verts = 0, contribs = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t n_round = ((n + 31u) / 32u) * 32u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        const uint32_t slot = valid ? qcur[i] : 0u;
+        bool cont = false, shadow = false, done = false;
+        float4 sh_o = make_float4(0, 0, 0, 0), sh_d = sh_o, sh_c = sh_o;
+        float S_nee[3][4];
+        if (valid) {
+            const float4 o4 = p.o[slot], d4 = p.d[slot];
+            const uint4 m = p.meta[slot];
+            const int4 h = p.hit[slot];
+            const uint32_t pix = m.x, smp = m.y;
+            const int depth = (int)m.z;
+            float opl = o4.w;
+            const float3 d = xyz(d4);
+            if (h.x < 0) {
+                done = true;
+            } else {
+                verts++;
+                Mueller P;
+                load_mueller(p, slot, P);
+                const float3 xf = xyz(p.xframe[slot]);
+                const int k = h.x, orig = h.y;
+                const float th = __int_as_float(h.z);
+                const float3 x = xyz(o4) + d * th;
+                if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
+                const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
+                const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+                const float3 wo = -d;
+                const float cwo = dot(ng, wo);
+                const int unit = __ldg(&s.tri_unit[orig]);
+                if (unit >= 0 && cwo > 0.f) {  // emission: column 0 of P (unpolarised emitter)
+                    const LightUnit U = s.units[unit];
+                    float w = 1.0f;
+                    if (depth > 1) w = mis2w(d4.w, (U.v1.w / U.v0.w) * th * th / cwo);
+                    const float4 Le = s.em_rad[__float_as_int(U.v2.w)];
+                    const float le[3] = {Le.x, Le.y, Le.z};
+                    float S[3][4];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) S[c][q] = P.m[c][4 * q] * le[c] * w * p.scale;
+                    wf_splat_stokes(p, pix, opl + pulse_time(s, pix, smp, (uint32_t)depth, 0, p.k0, p.k1), S);
+                    contribs++;
+                }
+                if (depth == p.max_depth) {
+                    done = true;
+                } else {
+                    opl += vertex_delay(s, orig, pix, smp, (uint32_t)depth, p.k0, p.k1);
+                    const float3 nn = cwo >= 0.f ? ng : -ng;
+                    float3 tb, bb;
+                    onb(nn, tb, bb);
+                    const float3 wol = to_local(wo, tb, bb, nn);
+                    const float4 mm = __ldg(&s.mats[orig]);
+                    const Mat mat{xyz(mm), mm.w};
+                    const float alb[3] = {mm.x, mm.y, mm.z};
+                    if (s.n_units > 0) {  // next-event estimate, queued for the shadow stage
+                        const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_NEE), p.k0, p.k1);
+                        const LightUnit U = s.units[pick_unit_wf(s, R.x)];
+                        const int em = __float_as_int(U.v2.w);
+                        const bool is_pt = __float_as_int(U.n.w) < 0;
+                        const float3 y = is_pt ? xyz(U.v0)
+                                               : tri_point(xyz(U.v0), xyz(U.v1), xyz(U.v2), u24(R.y), u24(R.z));
+                        const float3 xo = x + nn * eps_of(x);
+                        const float3 dl = y - xo;
+                        const float dist = sqrtf(dot(dl, dl));
+                        const float3 wi = dl * (1.0f / dist);
+                        const float cx = dot(nn, wi);
+                        const float cy = is_pt ? 1.0f : -dot(xyz(U.n), wi);
+                        if (cx > 0.f && cy > 0.f && dist > 0.f) {
+                            const float3 wil = to_local(wi, tb, bb, nn);
+                            float3 fc;
+                            float pb;
+                            bsdf_eval(mat, wol, wil, fc, pb);
+                            const float pick = U.v1.w;
+                            float geo, w = 1.0f;
+                            if (is_pt) geo = 1.0f / (dist * dist) / pick;
+                            else {
+                                const float pA = pick / U.v0.w;
+                                geo = cy / (dist * dist) / pA;
+                                w = mis2w(pA * dist * dist / cy, pb);
+                            }
+                            const float4 Le = s.em_rad[em];
+                            const float le[3] = {Le.x, Le.y, Le.z};
+                            if (mat.rough < 0.f) {
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const float kk = alb[c] * (1.0f / MT_PI) * cx * geo * w * le[c] * p.scale;
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) S_nee[c][q] = P.m[c][4 * q] * kk;
+                                }
+                            } else {
+                                // column 0 of (P R(t)) M_F, t the turn from the scattering plane to the frame
+                                const float t = frame_angle(wo, plane_normal(wi, d), xf);
+                                float s2, c2;
+                                sincosf(2.0f * t, &s2, &c2);
+                                float cd;
+                                const float kf = ggx_factor(mat.rough, wol, wil, cd) * cx * geo * w * p.scale;
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const float4 F = fresnel_abcd(cd, conductor_kappa(alb[c]));
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) {
+                                        const float q0 = P.m[c][4 * q];
+                                        const float q1 = P.m[c][4 * q + 1] * c2 - P.m[c][4 * q + 2] * s2;
+                                        S_nee[c][q] = (q0 * F.x + q1 * F.y) * kf * le[c];
+                                    }
+                                }
+                            }
+                            bool nonzero = false;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) nonzero |= S_nee[c][q] != 0.f;
+                            if (nonzero) {
+                                shadow = true;
+                                sh_o = make_float4(xo.x, xo.y, xo.z, dist - (is_pt ? 0.0f : eps_of(y)));
+                                sh_d = make_float4(wi.x, wi.y, wi.z,
+                                                   opl + dist + pulse_time(s, pix, smp, (uint32_t)depth, 1, p.k0,
+                                                                           p.k1));
+                                sh_c = make_float4(0.f, 0.f, 0.f, __int_as_float((int)pix));
+                            }
+                        }
+                    }
+                    // continue by sampling the BSDF
+                    const uint4 R = philox4x32_10(make_uint4(pix, smp, (uint32_t)depth, G_SCATTER), p.k0, p.k1);
+                    float3 wil;
+                    if (bsdf_sample(mat, wol, u24(R.x), u24(R.y), wil)) {
+                        float3 f;
+                        float pb;
+                        bsdf_eval(mat, wol, wil, f, pb);
+                        if (pb > 0.f) {
+                            const float3 wi = to_world(wil, tb, bb, nn);
+                            const float3 sv = plane_normal(wi, d);
+                            rotate_columns(P, frame_angle(wo, sv, xf));
+                            if (mat.rough < 0.f) {  // ideal depolariser
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const float kk = alb[c] * (1.0f / MT_PI) * wil.z / pb;
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) {
+                                        P.m[c][4 * q] *= kk;
+                                        P.m[c][4 * q + 1] = 0.f;
+                                        P.m[c][4 * q + 2] = 0.f;
+                                        P.m[c][4 * q + 3] = 0.f;
+                                    }
+                                }
+                            } else {  // P <- P M_F (Fresnel Mueller of the microfacet) x GGX factor / pdf
+                                float cd;
+                                const float kf = ggx_factor(mat.rough, wol, wil, cd) * wil.z / pb;
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const float4 F = fresnel_abcd(cd, conductor_kappa(alb[c]));
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) {
+                                        float *row = &P.m[c][4 * q];
+                                        const float r0 = row[0], r1 = row[1], r2 = row[2], r3 = row[3];
+                                        row[0] = (r0 * F.x + r1 * F.y) * kf;
+                                        row[1] = (r0 * F.y + r1 * F.x) * kf;
+                                        row[2] = (r2 * F.z - r3 * F.w) * kf;
+                                        row[3] = (r2 * F.w + r3 * F.z) * kf;
+                                    }
+                                }
+                            }
+                            store_mueller(p, slot, P);
+                            p.xframe[slot] = make_float4(sv.x, sv.y, sv.z, 0.f);
+                            const float3 no = x + nn * eps_of(x);
+                            p.o[slot] = make_float4(no.x, no.y, no.z, opl);
+                            p.d[slot] = make_float4(wi.x, wi.y, wi.z, pb);
+                            p.meta[slot] = make_uint4(pix, smp, (uint32_t)(depth + 1), 0u);
+                            cont = true;
+                        }
+                    }
+                    if (!cont) done = true;
+                }
+            }
+        }
+        const uint32_t qs = wf_append(&p.counters[C_NEXT], cont);
+        if (cont) qnext[qs] = slot;
+        const uint32_t fs = wf_append(&p.counters[C_FREE], done);
+        if (done) p.free_q[fs] = slot;
+        const uint32_t ss = wf_append(&p.counters[C_SHADOW], shadow);
+        if (shadow) {
+            p.sh_o[ss] = sh_o;
+            p.sh_d[ss] = sh_d;
+            p.sh_c[ss] = sh_c;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                p.sh_s[(size_t)ss * 3 + c] = make_float4(S_nee[c][0], S_nee[c][1], S_nee[c][2], S_nee[c][3]);
+        }
+    }
+    warp_count(&s.counters[0], verts);
+    warp_count(&s.counters[2], contribs);
+}
+
+// unoccluded next-event rays add their Stokes records (warps claim 32 rays at a time)
+__global__ void __launch_bounds__(256, 4) k_wf_shadow_pol(const DevScene s, const WfParams p) {
+    const uint32_t n = p.counters[C_SHADOW];
+    const int lane = threadIdx.x & 31;
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0, contribs = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&p.counters[C_SH_CUR], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i < n) {
+            const float4 o = p.sh_o[i], d = p.sh_d[i];
+            rays++;
+            if (!trace_any<false>(s, make_ray(s, xyz(o), xyz(d)), o.w, tc)) {
+                float S[3][4];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float4 v = p.sh_s[(size_t)i * 3 + c];
+                    S[c][0] = v.x;
+                    S[c][1] = v.y;
+                    S[c][2] = v.z;
+                    S[c][3] = v.w;
+                }
+                wf_splat_stokes(p, (uint32_t)__float_as_int(p.sh_c[i].w), d.w, S);
+                contribs++;
+            }
+        }
+    }
+    warp_count(&s.counters[3], rays);
+    warp_count(&s.counters[2], contribs);
 }
 
 // Sort keys of the queued shadow rays: an octahedral cell of the direction
@@ -925,7 +1229,9 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_extend<false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
         }
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
-        if (p.bwd) {
+        if (p.mueller) {
+            k_wf_shade_pol<<<grid * 2, 128, 0, st>>>(s, p, qa, qb);
+        } else if (p.bwd) {
             if (media) k_wf_shade<false, true, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
             else k_wf_shade<false, false, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
         } else if (p.sig) {
@@ -946,7 +1252,9 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             *launches += 1;
         }
         if (timing) MT_TRY(wf_event(timing, iter, 3, st));
-        if (p.bwd) {
+        if (p.mueller) {
+            k_wf_shadow_pol<<<grid, 256, 0, st>>>(s, p);
+        } else if (p.bwd) {
             if (media) {
                 if (counters) k_wf_shadow<false, true, false, true, true><<<grid, 256, 0, st>>>(s, p);
                 else k_wf_shadow<false, false, false, true, true><<<grid, 256, 0, st>>>(s, p);

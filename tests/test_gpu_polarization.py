@@ -94,3 +94,38 @@ def test_two_reflections_match_oracle(oracle_mod, scenes_mod):
     err = np.abs(ratio_g - ratio_r).max(axis=2)[lit]
     assert np.quantile(err, 0.95) < 1e-3 and err.max() < 2e-2, (np.quantile(err, 0.95), err.max())
     assert rel_l2(g[:, :, 0, :], r[:, :, 0, :]) < 1e-3
+
+
+@pytest.mark.parametrize("which", ["conductor_box", "mirror_corner"])
+def test_wavefront_polarized_equals_path_kernel(scenes_mod, which):
+    """The wavefront form keeps each path's Mueller matrices and frame in the
+    path pool: the same Stokes films as the path-per-thread kernel up to the
+    order of floating-point additions, whole frame and band by band."""
+    import torch
+    api = build_and_load()
+    if which == "mirror_corner":
+        sc = scenes_mod.mirror_corner()
+    else:
+        sc = scenes_mod.cornell_box()
+        sc.mtype[10:34] = 1
+        sc.roughness[10:34] = 0.08
+        sc.albedo[10:34] = np.clip(sc.albedo[10:34] + 0.3, 0, 0.95)
+    s = api.Scene(sc)
+    H = W = 48
+    T, start, width = 160, 3.0, 0.025
+    a, sa = api.render_polarized(s, H, W, T, start, width, 8, 9, 6)
+    a, sa = a.clone(), sa.clone()
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
+    try:
+        b, sb = api.render_polarized(s, H, W, T, start, width, 8, 9, 6)
+        bf = torch.empty_like(b)
+        bs = torch.empty_like(sb)
+        for r0 in range(0, H, 16):
+            api.render_polarized(s, 16, W, T, start, width, 8, 9, 6, out=(bf[r0:r0 + 16], bs[r0:r0 + 16]),
+                                 window=(H, r0))
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
+    assert sa[:, :, 1:].abs().max().item() > 0
+    for x, y in ((b, a), (sb, sa), (bf, a), (bs, sa)):
+        assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) < 1e-4

@@ -1,5 +1,6 @@
 """mt_render_nlos_noalloc: the NLOS capture for callers that cannot allocate
-device memory when they render (graph capture, pre-reserved memory budgets).
+device memory when they render (device memory reserved up front by their own
+allocator or a fixed budget).
 It must give the same impulse responses as mt_render_nlos, through the C ABI,
 on two calls in a row, without changing the device's free memory.
 
