@@ -752,11 +752,21 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
                      "the first wavefront render of this size must not be captured (it sizes the path pool)");
         auto &al = s->al;
+#if MT_WF_AOS
+        MT_TRY(al.alloc(&s->wf_o, (size_t)MT_WF_REC * P, "path pool"));
+        s->wf_d = s->wf_o + 1;
+        s->wf_beta = s->wf_o + 2;
+        s->wf_meta = (uint4 *)(s->wf_o + 3);
+        s->wf_hit = (int4 *)(s->wf_o + 4);
+        s->wf_sig = s->wf_o + 5;
+#else
         MT_TRY(al.alloc(&s->wf_o, P, "path pool"));
         MT_TRY(al.alloc(&s->wf_d, P, "path pool"));
         MT_TRY(al.alloc(&s->wf_beta, P, "path pool"));
         MT_TRY(al.alloc(&s->wf_meta, P, "path pool"));
         MT_TRY(al.alloc(&s->wf_hit, P, "path pool"));
+        MT_TRY(al.alloc(&s->wf_sig, P, "path tangent sums"));
+#endif
         MT_TRY(al.alloc(&s->wf_qa, P, "path queues"));
         MT_TRY(al.alloc(&s->wf_qb, P, "path queues"));
         MT_TRY(al.alloc(&s->wf_free, P, "path queues"));
@@ -764,7 +774,6 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_TRY(al.alloc(&s->wf_sh_d, P, "shadow queue"));
         MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
         MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
-        MT_TRY(al.alloc(&s->wf_sig, P, "path tangent sums"));
         if (!s->wf_counters) {
             MT_TRY(al.alloc(&s->wf_counters, 8, "path queue counters"));
             MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
@@ -836,11 +845,11 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.P = P;
     w.film = rp.film;
     w.steady = rp.steady;
-    w.o = s->wf_o;
-    w.d = s->wf_d;
-    w.beta = s->wf_beta;
-    w.meta = s->wf_meta;
-    w.hit = s->wf_hit;
+    w.o.base = s->wf_o;
+    w.d.base = s->wf_d;
+    w.beta.base = s->wf_beta;
+    w.meta.base = s->wf_meta;
+    w.hit.base = s->wf_hit;
     w.qa = s->wf_qa;
     w.qb = s->wf_qb;
     w.free_q = s->wf_free;
@@ -860,7 +869,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.wide = (cfg.options & MT_OPT_WIDE_BVH) ? 1 : 0;
     w.lambdas = rp.lambdas;
     w.K = rp.lambdas ? rp.K : 0;
-    w.sig = tangent ? s->wf_sig : nullptr;
+    w.sig.base = tangent ? s->wf_sig : nullptr;
     w.dalb = rp.dalb;
     w.drad = rp.drad;
     w.dmed = rp.dmed;

@@ -58,6 +58,23 @@ struct NlosParams {
     int32_t aggregate;         // warp-aggregated splats
 };
 
+// Path pool layout of the wavefront form.  MT_WF_AOS = 1: one 128-byte record
+// per slot, float4 words [o, d, beta, meta, hit, sig, -, -], so the state of a
+// path shares cache lines (a shading step reads two and a half 32-byte sectors
+// and a new path writes two whole sectors); 0: one array per field.
+#ifndef MT_WF_AOS
+#define MT_WF_AOS 1
+#endif
+#define MT_WF_REC (MT_WF_AOS ? 8 : 1)  // float4 words between the fields of consecutive slots
+
+// one field of the path pool, indexed by slot
+template <class T>
+struct PoolField {
+    T *base;
+    __host__ __device__ __forceinline__ T &operator[](size_t slot) const { return base[slot * MT_WF_REC]; }
+    __host__ __device__ __forceinline__ explicit operator bool() const { return base != nullptr; }
+};
+
 struct WfParams {
     int32_t H, W, T;
     int32_t H_full, row0;          // film window in the frame (see RenderParams)
@@ -69,9 +86,9 @@ struct WfParams {
     unsigned long long total_paths;
     uint32_t P;                    // paths in flight (pool size)
     float *film, *steady;
-    float4 *o, *d, *beta;          // path state: origin + OPL, direction + pdf of the last BSDF sample, throughput
-    uint4 *meta;                   // pixel, sample index, depth
-    int4 *hit;                     // leaf-order triangle, original triangle, t bits
+    PoolField<float4> o, d, beta;  // path state: origin + OPL, direction + pdf of the last BSDF sample, throughput
+    PoolField<uint4> meta;         // pixel, sample index, depth
+    PoolField<int4> hit;           // leaf-order triangle, original triangle, t bits
     uint32_t *qa, *qb, *free_q;    // extension queues and the free-slot stack
     float4 *sh_o, *sh_d, *sh_c;    // shadow rays: origin + tmax, direction + OPL, contribution + pixel
     uint4 *sh_m;                   // shadow ray record: sample, depth, emitter triangle
@@ -86,7 +103,7 @@ struct WfParams {
     const float *lambdas;          // frequency-space film: K wavelengths (m), the film has T = 2K; K = 0: bins
     int32_t K;
     // forward-mode derivative: per-path prefix sum of ratio * dtheta over the vertices so far, and the tangent
-    float4 *sig;
+    PoolField<float4> sig;
     const float *dalb, *drad;
     float dmed;
     // path replay (backward): vertex records [vertex][slot] (a: ratio of the continuation + triangle bits,

@@ -84,17 +84,60 @@ __device__ __forceinline__ float q_plane(uint32_t word, uint32_t sel) {
     return __int_as_float(__byte_perm(word, 0x4B000000u, sel));
 }
 
+// Packed arithmetic of sm_100-class GPUs: fma.rn.f32x2 (two independent FMAs,
+// each rounded once, in one instruction) and three-input min/max.  Each lane
+// gets the same values as the scalar forms, so switching MT_SLAB_PACKED off
+// (scalar FMAs and two-input min/max) changes no result, only the count of
+// issued instructions per node.
+#ifndef MT_SLAB_PACKED
+#define MT_SLAB_PACKED 1
+#endif
+
+__device__ __forceinline__ void fma_x2(float ax, float ay, float bx, float by, float cx, float cy, float &dx,
+                                       float &dy) {
+#if MT_SLAB_PACKED
+    asm("{\n\t.reg .b64 a, b, c, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tmov.b64 c, {%6, %7};\n\t"
+        "fma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(dx), "=f"(dy)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by), "f"(cx), "f"(cy));
+#else
+    dx = fmaf(ax, bx, cx);
+    dy = fmaf(ay, by, cy);
+#endif
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+#if MT_SLAB_PACKED
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+#else
+    return fmaxf(fmaxf(a, b), c);
+#endif
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+#if MT_SLAB_PACKED
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+#else
+    return fminf(fminf(a, b), c);
+#endif
+}
+
 // entry / exit distance of one child box; wx, wy, wz are its three axis words
 __device__ __forceinline__ void slab(const RayT &r, uint32_t wx, uint32_t wy, uint32_t wz, float tmax, float &tn,
                                      float &tf) {
-    const float nx = fmaf(q_plane(wx, r.sel_n[0]), r.sa.x, r.sb.x);
-    const float fx = fmaf(q_plane(wx, r.sel_n[0] ^ 0x22u), r.sa.x, r.sb.x);
-    const float ny = fmaf(q_plane(wy, r.sel_n[1]), r.sa.y, r.sb.y);
-    const float fy = fmaf(q_plane(wy, r.sel_n[1] ^ 0x22u), r.sa.y, r.sb.y);
+    float nx, ny, fx, fy;
+    fma_x2(q_plane(wx, r.sel_n[0]), q_plane(wy, r.sel_n[1]), r.sa.x, r.sa.y, r.sb.x, r.sb.y, nx, ny);
+    fma_x2(q_plane(wx, r.sel_n[0] ^ 0x22u), q_plane(wy, r.sel_n[1] ^ 0x22u), r.sa.x, r.sa.y, r.sb.x, r.sb.y, fx,
+           fy);
     const float nz = fmaf(q_plane(wz, r.sel_n[2]), r.sa.z, r.sb.z);
     const float fz = fmaf(q_plane(wz, r.sel_n[2] ^ 0x22u), r.sa.z, r.sb.z);
-    tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.0f));
-    tf = fminf(fminf(fx, fy), fminf(fz, tmax));
+    tn = fmaxf(max3f(nx, ny, nz), 0.0f);
+    tf = fminf(min3f(fx, fy, fz), tmax);
 }
 
 // Watertight ray/triangle test.  The edge functions are evaluated without
