@@ -335,10 +335,13 @@ def main():
     khash = _kernel_hash()
     traffic, _ = _traffic_from_profile(khash, "k_wf_traversal_large_scene" if wavefront else "k_render_large_scene")
     if wavefront:
-        # dominant kernel: the BVH traversal (k_wf_extend + k_wf_shadow), timed by its own events
+        # dominant kernel: the BVH traversal pass k_wf_trace (extension rays, then the shadow rays
+        # of the previous shading pass; the last shading pass's shadow rays in k_wf_shadow),
+        # timed by its own events
         trav_ms = (stages["extend_ms"] + stages["shadow_ms"]) / args.steps
         achieved = trav_bytes / (trav_ms / 1000.0) / 1e9
-        kernel_name = "k_wf_extend + k_wf_shadow (BVH traversal of extension and shadow rays)"
+        kernel_name = ("k_wf_trace (+ k_wf_shadow for the last pass): BVH traversal of extension and "
+                       "shadow rays")
         kernel_bytes = trav_bytes
         per_unit = "per ray: BVH node bytes fetched (32 B per node) + 48 B per triangle tested"
         stage_ms = {k: v / args.steps for k, v in stages.items() if k.endswith("_ms")}

@@ -321,7 +321,11 @@ class Scene:
         mt_scene_set_pulse(self.h, int(shape), float(a), float(b))
 
     def stage_times(self, reset=True) -> dict:
-        """Milliseconds per wavefront stage of renders run with MT_OPT_STAGE_TIMING."""
+        """Milliseconds per wavefront stage of renders run with MT_OPT_STAGE_TIMING:
+        generate (with the extension-ray sort, if on), extend (the traversal pass:
+        extension rays and, in the fused forward form, the shadow rays of the
+        previous shading pass), shade (with the shadow-ray sort, if on), shadow
+        (a shadow pass of its own: replay, polarization, dynamic fetch)."""
         out = (C.c_double * 5)()
         mt_stage_times(self.h, out, int(reset))
         keys = ["generate_ms", "extend_ms", "shade_ms", "shadow_ms", "iterations"]

@@ -775,7 +775,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
         MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
         if (!s->wf_counters) {
-            MT_TRY(al.alloc(&s->wf_counters, 8, "path queue counters"));
+            MT_TRY(al.alloc(&s->wf_counters, 16, "path queue counters"));
             MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
             MT_TRY(al.alloc((char **)&s->wf_iter, 64, "path queue counters"));
         }

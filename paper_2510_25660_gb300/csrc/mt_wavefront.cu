@@ -30,7 +30,13 @@ struct WfIter {
 namespace {
 
 // counters[] layout
-enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_FIN = 7 };
+// C_SH_N: shadow rays queued by the previous iteration's shading, which the
+// fused traversal pass of this iteration traces after its extension rays
+enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_FIN = 7, C_SH_N = 8 };
+#define MT_WF_COUNTERS 16
+#ifndef MT_WF_FUSE
+#define MT_WF_FUSE 1  // 0: a shadow pass of its own after every shading pass
+#endif
 
 __device__ __forceinline__ float mis2w(float a, float b) { return a * a / (a * a + b * b); }
 
@@ -207,6 +213,7 @@ __global__ void k_wf_setup(WfParams p, WfIter *it) {
     it->base = base;
     c[C_CUR] = cont + n_new;
     c[C_NEXT] = 0;
+    c[C_SH_N] = c[C_SHADOW];
     c[C_SHADOW] = 0;
     c[C_FREE] = freec - n_new;
     c[C_EXT_CUR] = 0;
@@ -266,11 +273,10 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
 // hit record: (leaf-order triangle or -1, original triangle, t bits, 1 if the
 // path scatters in the medium at t before reaching that surface)
 template <bool WIDE, bool CNT, bool MEDIA>
-__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
+__device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, const uint32_t *qcur, TraceCnt &tc,
+                                         uint32_t &rays) {
     const uint32_t n = p.counters[C_CUR];
     const int lane = threadIdx.x & 31;
-    TraceCnt tc{0, 0};
-    uint32_t rays = 0;
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&p.counters[C_EXT_CUR], 32u);
@@ -314,6 +320,13 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevSc
             rays++;
         }
     }
+}
+
+template <bool WIDE, bool CNT, bool MEDIA>
+__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_extend(const DevScene s, const WfParams p, const uint32_t *qcur) {
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0;
+    ext_rays<WIDE, CNT, MEDIA>(s, p, qcur, tc, rays);
     warp_count(&s.counters[3], rays);
     if (CNT) {
         warp_count(&s.counters[4], tc.nodes);
@@ -331,22 +344,39 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     return v;
 }
 
+// Key widths of the ray sorts (radix passes of 8 bits each): Morton bits per
+// axis of the extension-ray origin grid, of the shadow-ray origin grid, and
+// bits per octahedral coordinate of the shadow-ray direction.
+#ifndef MT_SORT_EXT_B
+#define MT_SORT_EXT_B 9
+#endif
+#ifndef MT_SORT_SH_B
+#define MT_SORT_SH_B 7
+#endif
+#ifndef MT_SORT_SH_D
+#define MT_SORT_SH_D 4
+#endif
+#define MT_SORT_EXT_BITS (3 + 3 * MT_SORT_EXT_B)
+#define MT_SORT_SH_BITS (3 * MT_SORT_SH_B + 2 * MT_SORT_SH_D)
+
 // Sort keys of the queued extension rays: direction octant (3 bits) above the
-// Morton code of the origin on a 512^3 grid over the scene box (27 bits).
+// Morton code of the origin on a 2^B x 2^B x 2^B grid over the scene box.
 // Entries past the queue's end get the largest key and sort to the back.
 __global__ void k_wf_sort_keys(const DevScene s, const WfParams p, const uint32_t *qcur) {
     const uint32_t n = p.counters[C_CUR];
-    const float gx = 512.0f / (65536.0f * s.q_scale.x), gy = 512.0f / (65536.0f * s.q_scale.y),
-                gz = 512.0f / (65536.0f * s.q_scale.z);
+    constexpr float G = (float)(1 << MT_SORT_EXT_B);
+    const float gx = G / (65536.0f * s.q_scale.x), gy = G / (65536.0f * s.q_scale.y),
+                gz = G / (65536.0f * s.q_scale.z);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
         if (i < n) {
             const uint32_t slot = qcur[i];
             const float4 o = p.o[slot], d = p.d[slot];
-            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), 511.0f);
-            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), 511.0f);
-            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), 511.0f);
+            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), G - 1.0f);
+            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), G - 1.0f);
+            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), G - 1.0f);
             const uint32_t oct = (d.x < 0.0f ? 1u : 0u) | (d.y < 0.0f ? 2u : 0u) | (d.z < 0.0f ? 4u : 0u);
-            p.sort_keys[i] = (oct << 27) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+            p.sort_keys[i] =
+                (oct << (3 * MT_SORT_EXT_B)) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
         } else {
             p.sort_keys[i] = 0xFFFFFFFFu;
         }
@@ -647,19 +677,20 @@ __global__ void __launch_bounds__(256, 4) k_wf_shadow_pol(const DevScene s, cons
 }
 
 // Sort keys of the queued shadow rays: an octahedral cell of the direction
-// (4 + 4 bits) above the Morton code of the origin on a 128^3 grid (21 bits);
-// the values are record indices.
+// (2 x MT_SORT_SH_D bits) above the Morton code of the origin on a 2^B per
+// axis grid (3 x MT_SORT_SH_B bits); the values are record indices.
 __global__ void k_wf_shadow_keys(const DevScene s, const WfParams p) {
     const uint32_t n = p.counters[C_SHADOW];
-    const float gx = 128.0f / (65536.0f * s.q_scale.x), gy = 128.0f / (65536.0f * s.q_scale.y),
-                gz = 128.0f / (65536.0f * s.q_scale.z);
+    constexpr float G = (float)(1 << MT_SORT_SH_B), GD = (float)(1 << MT_SORT_SH_D);
+    const float gx = G / (65536.0f * s.q_scale.x), gy = G / (65536.0f * s.q_scale.y),
+                gz = G / (65536.0f * s.q_scale.z);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
         uint32_t key = 0xFFFFFFFFu;
         if (i < n) {
             const float4 o = p.sh_o[i], d = p.sh_d[i];
-            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), 127.0f);
-            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), 127.0f);
-            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), 127.0f);
+            const uint32_t cx = (uint32_t)fminf(fmaxf((o.x - s.q_lo.x) * gx, 0.0f), G - 1.0f);
+            const uint32_t cy = (uint32_t)fminf(fmaxf((o.y - s.q_lo.y) * gy, 0.0f), G - 1.0f);
+            const uint32_t cz = (uint32_t)fminf(fmaxf((o.z - s.q_lo.z) * gz, 0.0f), G - 1.0f);
             const float l1 = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
             float u = d.x / l1, v = d.y / l1;
             if (d.z < 0.0f) {
@@ -667,9 +698,10 @@ __global__ void k_wf_shadow_keys(const DevScene s, const WfParams p) {
                 v = (1.0f - fabsf(u)) * (v < 0.0f ? -1.0f : 1.0f);
                 u = uu;
             }
-            const uint32_t du = (uint32_t)fminf(fmaxf((u + 1.0f) * 8.0f, 0.0f), 15.0f);
-            const uint32_t dv = (uint32_t)fminf(fmaxf((v + 1.0f) * 8.0f, 0.0f), 15.0f);
-            key = (du << 25) | (dv << 21) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+            const uint32_t du = (uint32_t)fminf(fmaxf((u + 1.0f) * (0.5f * GD), 0.0f), GD - 1.0f);
+            const uint32_t dv = (uint32_t)fminf(fmaxf((v + 1.0f) * (0.5f * GD), 0.0f), GD - 1.0f);
+            key = (du << (3 * MT_SORT_SH_B + MT_SORT_SH_D)) | (dv << (3 * MT_SORT_SH_B)) | spread3(cx) |
+                  (spread3(cy) << 1) | (spread3(cz) << 2);
         }
         p.sort_keys[i] = key;
         p.sort_q[i] = i;
@@ -1048,16 +1080,9 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
 }
 
 template <bool DUMP, bool CNT, bool WIDE, bool MEDIA, bool BWD>
-__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevScene s, const WfParams p) {
-    __shared__ float em_acc[BWD ? MT_WF_EM_SMEM * 3 : 1];
-    if (BWD) {
-        for (int k = threadIdx.x; k < MT_WF_EM_SMEM * 3; k += blockDim.x) em_acc[k] = 0.f;
-        __syncthreads();
-    }
-    const uint32_t n = p.counters[C_SHADOW];
+__device__ __forceinline__ void sh_rays(const DevScene &s, const WfParams &p, uint32_t n, float *em_acc,
+                                        TraceCnt &tc, uint32_t &rays, uint32_t &contribs) {
     const int lane = threadIdx.x & 31;
-    TraceCnt tc{0, 0};
-    uint32_t rays = 0, contribs = 0;
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&p.counters[C_SH_CUR], 32u);
@@ -1112,6 +1137,19 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
             }
         }
     }
+}
+
+// shadow rays of this iteration's shading; n_idx names the counter that holds their number
+template <bool DUMP, bool CNT, bool WIDE, bool MEDIA, bool BWD>
+__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevScene s, const WfParams p, int n_idx) {
+    __shared__ float em_acc[BWD ? MT_WF_EM_SMEM * 3 : 1];
+    if (BWD) {
+        for (int k = threadIdx.x; k < MT_WF_EM_SMEM * 3; k += blockDim.x) em_acc[k] = 0.f;
+        __syncthreads();
+    }
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0, contribs = 0;
+    sh_rays<DUMP, CNT, WIDE, MEDIA, BWD>(s, p, p.counters[n_idx], em_acc, tc, rays, contribs);
     warp_count(&s.counters[3], rays);
     warp_count(&s.counters[2], contribs);
     if (CNT) {
@@ -1121,10 +1159,28 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_shadow(const DevSc
     if (BWD) em_grad_flush(p, em_acc, s.n_em);
 }
 
+// Fused traversal pass: the extension rays of this iteration, then the shadow
+// rays that the previous iteration's shading queued (they are independent of
+// each other), so that warps that find the extension queue drained trace
+// shadow rays instead of idling in the tail of the pass.
+template <bool WIDE, bool CNT, bool MEDIA, bool DUMP>
+__global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_trace(const DevScene s, const WfParams p, const uint32_t *qcur) {
+    TraceCnt tc{0, 0};
+    uint32_t rays = 0, contribs = 0;
+    ext_rays<WIDE, CNT, MEDIA>(s, p, qcur, tc, rays);
+    sh_rays<DUMP, CNT, WIDE, MEDIA, false>(s, p, p.counters[C_SH_N], nullptr, tc, rays, contribs);
+    warp_count(&s.counters[3], rays);
+    warp_count(&s.counters[2], contribs);
+    if (CNT) {
+        warp_count(&s.counters[4], tc.nodes);
+        warp_count(&s.counters[5], tc.tris);
+    }
+}
+
 __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsigned long long *next_path) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) free_q[i] = i;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int k = 0; k < 8; ++k) counters[k] = 0;
+        for (int k = 0; k < MT_WF_COUNTERS; ++k) counters[k] = 0;
         counters[C_FREE] = P;
         *next_path = 0ull;
     }
@@ -1135,7 +1191,7 @@ __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsi
 size_t mt_wf_sort_bytes(uint32_t P) {
     size_t bytes = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const uint32_t *)nullptr, (uint32_t *)nullptr,
-                                    (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)P, 0, 30);
+                                    (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)P, 0, 32);
     return bytes;
 }
 
@@ -1195,6 +1251,26 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
                                                                                     p.next_path);
     MT_CUDA_TRY(cudaGetLastError());
     uint32_t *qa = p.qa, *qb = p.qb;
+    // fused form: trace the shadow rays whose count the last setup moved to C_SH_N
+    auto shadow_tail = [&]() -> mt_status {
+        const bool media = s.has_medium != 0;
+        const bool dyn = p.dynamic_fetch && !dump && !media && !p.bwd;
+        const bool wide = p.wide && !media && !p.bwd;
+        if (!MT_WF_FUSE || p.bwd || p.mueller || dyn || dump) return MT_OK;
+        if (media) {
+            if (counters) k_wf_shadow<false, true, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+            else k_wf_shadow<false, false, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+        } else if (wide) {
+            if (counters) k_wf_shadow<false, true, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+            else k_wf_shadow<false, false, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+        } else {
+            if (counters) k_wf_shadow<false, true, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+            else k_wf_shadow<false, false, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SH_N);
+        }
+        MT_CUDA_TRY(cudaGetLastError());
+        *launches += 2;
+        return MT_OK;
+    };
     // an upper bound on iterations: every path needs at most max_depth extension rays
     const unsigned long long bound =
         (p.total_paths + p.P - 1) / p.P * (unsigned long long)(p.max_depth + 1) + (unsigned long long)p.max_depth + 2;
@@ -1205,12 +1281,15 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         const bool media = s.has_medium != 0;
         const bool dyn = p.dynamic_fetch && !dump && !media && !p.bwd;
         const bool wide = p.wide && !media && !p.bwd;  // the medium and replay forms traverse the binary tree
+        // shadow rays traced in the next iteration's extension pass (the replay needs its shadow
+        // terms before the finalize stage, polarization and dynamic fetch have kernels of their own)
+        const bool fused = MT_WF_FUSE && !p.bwd && !p.mueller && !dyn && !dump;
         const uint32_t *qext = qa;
         if (p.sort_rays && !dump) {
             k_wf_sort_keys<<<grid, 256, 0, st>>>(s, p, qa);
             size_t bytes = p.sort_tmp_bytes;
             MT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(p.sort_tmp, bytes, p.sort_keys, p.sort_keys_out, qa, p.sort_q,
-                                                        (int)p.P, 0, 30, st));
+                                                        (int)p.P, 0, MT_SORT_EXT_BITS, st));
             qext = p.sort_q;
             *launches += 1;
         }
@@ -1218,6 +1297,17 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         if (dyn) {
             if (counters) k_wf_trace_dyn<false, true><<<grid, 256, 0, st>>>(s, p, qa);
             else k_wf_trace_dyn<false, false><<<grid, 256, 0, st>>>(s, p, qa);
+        } else if (fused) {
+            if (media) {
+                if (counters) k_wf_trace<false, true, true, false><<<grid, 256, 0, st>>>(s, p, qext);
+                else k_wf_trace<false, false, true, false><<<grid, 256, 0, st>>>(s, p, qext);
+            } else if (wide) {
+                if (counters) k_wf_trace<true, true, false, false><<<grid, 256, 0, st>>>(s, p, qext);
+                else k_wf_trace<true, false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
+            } else {
+                if (counters) k_wf_trace<false, true, false, false><<<grid, 256, 0, st>>>(s, p, qext);
+                else k_wf_trace<false, false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
+            }
         } else if (media) {
             if (counters) k_wf_extend<false, true, true><<<grid, 256, 0, st>>>(s, p, qext);
             else k_wf_extend<false, false, true><<<grid, 256, 0, st>>>(s, p, qext);
@@ -1248,19 +1338,21 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             k_wf_shadow_keys<<<grid, 256, 0, st>>>(s, p);
             size_t bytes = p.sort_tmp_bytes;
             MT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(p.sort_tmp, bytes, p.sort_keys, p.sort_keys_out, p.sort_q,
-                                                        p.sh_perm, (int)p.P, 0, 29, st));
+                                                        p.sh_perm, (int)p.P, 0, MT_SORT_SH_BITS, st));
             *launches += 1;
         }
         if (timing) MT_TRY(wf_event(timing, iter, 3, st));
-        if (p.mueller) {
+        if (fused) {
+            // traced by the next iteration's extension pass
+        } else if (p.mueller) {
             k_wf_shadow_pol<<<grid, 256, 0, st>>>(s, p);
         } else if (p.bwd) {
             if (media) {
-                if (counters) k_wf_shadow<false, true, false, true, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, false, true, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, false, true, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<false, false, false, true, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             } else {
-                if (counters) k_wf_shadow<false, true, false, false, true><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, false, false, true><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, false, false, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<false, false, false, false, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             }
             k_wf_finalize<<<grid, 256, 0, st>>>(s, p);
             *launches += 1;
@@ -1269,30 +1361,30 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             else k_wf_trace_dyn<true, false><<<grid, 256, 0, st>>>(s, p, qa);
         } else if (media) {
             if (dump) {
-                if (counters) k_wf_shadow<true, true, false, true, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<true, false, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<true, true, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<true, false, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             } else {
-                if (counters) k_wf_shadow<false, true, false, true, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, false, true, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<false, false, false, true, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             }
         } else if (wide) {
             if (dump) {
-                if (counters) k_wf_shadow<true, true, true, false, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<true, false, true, false, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<true, true, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<true, false, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             } else {
-                if (counters) k_wf_shadow<false, true, true, false, false><<<grid, 256, 0, st>>>(s, p);
-                else k_wf_shadow<false, false, true, false, false><<<grid, 256, 0, st>>>(s, p);
+                if (counters) k_wf_shadow<false, true, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+                else k_wf_shadow<false, false, true, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             }
         } else if (dump) {
-            if (counters) k_wf_shadow<true, true, false, false, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<true, false, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<true, true, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+            else k_wf_shadow<true, false, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
         } else {
-            if (counters) k_wf_shadow<false, true, false, false, false><<<grid, 256, 0, st>>>(s, p);
-            else k_wf_shadow<false, false, false, false, false><<<grid, 256, 0, st>>>(s, p);
+            if (counters) k_wf_shadow<false, true, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
+            else k_wf_shadow<false, false, false, false, false><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
         }
         MT_CUDA_TRY(cudaGetLastError());
         if (timing) MT_TRY(wf_event(timing, iter, 4, st));
-        *launches += 5;
+        *launches += fused ? 4 : 5;
         uint32_t *t = qa;
         qa = qb;
         qb = t;
@@ -1301,13 +1393,20 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             uint32_t done = 0;
             MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             MT_CUDA_TRY(cudaStreamSynchronize(st));
-            if (done) return timing ? wf_accumulate(timing, iter + 1) : MT_OK;
+            if (done) {
+                // shadow rays of the last shading pass (none once the queues have drained, but the
+                // fused form never leaves queued rays behind)
+                k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
+                MT_TRY(shadow_tail());
+                return timing ? wf_accumulate(timing, iter + 1) : MT_OK;
+            }
         }
     }
     if (timing) MT_TRY(wf_accumulate(timing, bound));
     // one more setup decides whether anything is left
     k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
     *launches += 1;
+    MT_TRY(shadow_tail());
     uint32_t done = 0;
     MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     MT_CUDA_TRY(cudaStreamSynchronize(st));
