@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             p.sh_o[ss] = sh_o;
             p.sh_d[ss] = sh_d;
             p.sh_c[ss] = sh_c;
-            p.sh_m[ss] = sh_m;
+            if (DUMP || MEDIA || BWD) p.sh_m[ss] = sh_m;  // read only by these forms' shadow stages
             if (BWD) p.sh_cb[ss] = sh_own;
         }
         (void)valid;
