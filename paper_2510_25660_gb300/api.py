@@ -257,15 +257,15 @@ class Scene:
         self.sc = sc
         n = sc.n_tris
         tris = np.ascontiguousarray(sc.tris, np.float32)
-        mats = (mt_material * n)()
-        alb = np.ascontiguousarray(sc.albedo, np.float32)
-        rough = np.ascontiguousarray(sc.roughness, np.float32)
-        mt = np.ascontiguousarray(sc.mtype, np.uint32)
-        arr = np.frombuffer(mats, dtype=np.dtype([("albedo", np.float32, 3), ("roughness", np.float32),
-                                                  ("type", np.uint32)]))
-        arr["albedo"] = alb
-        arr["roughness"] = rough
-        arr["type"] = mt
+        # mt_material rows (albedo[3], roughness, type bits) packed by torch's threaded cat into page-locked
+        # memory from torch's host cache, so that the upload runs at copy-engine speed
+        import torch
+        alb = torch.from_numpy(np.ascontiguousarray(sc.albedo, np.float32))
+        rough = torch.from_numpy(np.ascontiguousarray(sc.roughness, np.float32))
+        mt = torch.from_numpy(np.ascontiguousarray(sc.mtype, np.uint32).view(np.float32))
+        mats_t = torch.empty((n, 5), dtype=torch.float32, pin_memory=torch.cuda.is_available())
+        torch.cat((alb, rough[:, None], mt[:, None]), dim=1, out=mats_t)
+        mats = C.c_void_p(mats_t.data_ptr())  # read before mt_scene_create returns
         ne = len(sc.emitters)
         ems = (mt_emitter * max(ne, 1))()
         for i, e in enumerate(sc.emitters):

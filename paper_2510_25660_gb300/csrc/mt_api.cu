@@ -10,6 +10,8 @@
 #include <mutex>
 
 #include "mt_common.cuh"
+#include <thread>
+
 #include "mt_internal.h"
 #include "mt_launch.h"
 #include "mt_trace.cuh"
@@ -492,24 +494,47 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
 }
 
 // true when no float has an all-ones exponent (no infinity or NaN)
+// Run f(begin, end) over [0, n) on up to 8 host threads (one for small n); true when
+// every part returned true.
+extern "C++" {
+template <class F>
+static bool parallel_all(int64_t n, F f) {
+    const int64_t min_part = 1 << 20;
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(8, n / min_part));
+    if (parts == 1) return f(0, n);
+    std::vector<std::thread> th;
+    std::vector<char> ok((size_t)parts, 1);
+    for (int t = 0; t < parts; ++t)
+        th.emplace_back([&, t] { ok[t] = f(n * t / parts, n * (t + 1) / parts) ? 1 : 0; });
+    for (auto &x : th) x.join();
+    for (char c : ok)
+        if (!c) return false;
+    return true;
+}
+}  // extern "C++"
+
 static bool all_finite(const float *v, size_t n) {
     const uint32_t *b = reinterpret_cast<const uint32_t *>(v);
-    uint32_t bad = 0;
-    for (size_t i = 0; i < n; ++i) bad |= (uint32_t)((b[i] & 0x7F800000u) == 0x7F800000u);
-    return bad == 0;
+    return parallel_all((int64_t)n, [b](int64_t lo, int64_t hi) {
+        uint32_t bad = 0;
+        for (int64_t i = lo; i < hi; ++i) bad |= (uint32_t)((b[i] & 0x7F800000u) == 0x7F800000u);
+        return bad == 0;
+    });
 }
 
 static bool materials_ok(const mt_material *m, int64_t n) {
-    uint32_t bad = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        const mt_material &x = m[i];
-        bad |= (uint32_t)!(x.albedo[0] >= 0.f && x.albedo[0] < INFINITY);
-        bad |= (uint32_t)!(x.albedo[1] >= 0.f && x.albedo[1] < INFINITY);
-        bad |= (uint32_t)!(x.albedo[2] >= 0.f && x.albedo[2] < INFINITY);
-        bad |= (uint32_t)(x.type != MT_LAMBERT && x.type != MT_GGX_CONDUCTOR);
-        bad |= (uint32_t)(x.type == MT_GGX_CONDUCTOR && !(x.roughness > 0.f && x.roughness <= 1.f));
-    }
-    return bad == 0;
+    return parallel_all(n, [m](int64_t lo, int64_t hi) {
+        uint32_t bad = 0;
+        for (int64_t i = lo; i < hi; ++i) {
+            const mt_material &x = m[i];
+            bad |= (uint32_t)!(x.albedo[0] >= 0.f && x.albedo[0] < INFINITY);
+            bad |= (uint32_t)!(x.albedo[1] >= 0.f && x.albedo[1] < INFINITY);
+            bad |= (uint32_t)!(x.albedo[2] >= 0.f && x.albedo[2] < INFINITY);
+            bad |= (uint32_t)(x.type != MT_LAMBERT && x.type != MT_GGX_CONDUCTOR);
+            bad |= (uint32_t)(x.type == MT_GGX_CONDUCTOR && !(x.roughness > 0.f && x.roughness <= 1.f));
+        }
+        return bad == 0;
+    });
 }
 
 mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials, const mt_emitter *emitters,
