@@ -448,7 +448,9 @@ def main():
 
 def profile_case(which):
     """Launches of the hot kernels for ncu captures.  small: the large scene
-    (full geometry) at 128x128 px, 256 spp with the launch configuration of the
+    (full geometry) at 256x256 px, 256 spp (16.7M paths: four fills of the
+    path pool, so mid-render passes run with a full pool; 1.6 GB film) with the
+    launch configuration of the
     benchmark, the differentiable scene's backward at 64x64, a 16x16 confocal
     NLOS grid.  traversal: one full-size render of the benchmark (512x512 px,
     256 spp) with the benchmark's launch configuration, for single-pass
@@ -469,9 +471,9 @@ def profile_case(which):
         s.sync()
         print("profile case done")
         return
-    film, steady = api.new_film(128, 128, f.T)
+    film, steady = api.new_film(256, 256, f.T)
     for _ in range(3):
-        api.render(s, 128, 128, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))
+        api.render(s, 256, 256, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))
     s.sync()
     del s
     sc = scenes.diff_scene()
