@@ -158,10 +158,24 @@ __global__ void k_pack_mats(const mt_material *m, int n, float4 *out) {
     }
 }
 
-__global__ void k_set_albedo(const float *alb, int n, float4 *mats) {
+__global__ void k_set_albedo(const float *alb, int n, float4 *mats, const int32_t *leaf_of, float4 *shrec) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 m = mats[i];
-        mats[i] = make_float4(alb[3 * i], alb[3 * i + 1], alb[3 * i + 2], m.w);
+        const float4 v = make_float4(alb[3 * i], alb[3 * i + 1], alb[3 * i + 2], m.w);
+        mats[i] = v;
+        shrec[2 * (size_t)leaf_of[i] + 1] = v;
+    }
+}
+
+// shading records in leaf order: normal of the winding + light unit, material
+__global__ void k_shading_records(const float4 *tris, const float4 *mats, const int32_t *tri_unit, int n,
+                                  float4 *shrec) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float4 p0 = tris[3 * k], p1 = tris[3 * k + 1], p2 = tris[3 * k + 2];
+        const int orig = __float_as_int(p0.w);
+        const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+        shrec[2 * (size_t)k] = make_float4(ng.x, ng.y, ng.z, __int_as_float(tri_unit[orig]));
+        shrec[2 * (size_t)k + 1] = mats[orig];
     }
 }
 
@@ -429,9 +443,13 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
         MT_CUDA_TRY(cudaMemcpyAsync(tmp, rad.data(), rad.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         k_set_radiance<<<1, 64, 0, st>>>(tmp, std::max(1, n_em), emrad);
     }
+    float4 *shrec;
+    MT_TRY(al.alloc(&shrec, (size_t)2 * n, "shading records"));
+    k_shading_records<<<g, 256, 0, st>>>(sc->bvh.tris, mats4, tri_unit, (int)n, shrec);
     D.mats = mats4;
     D.tri_unit = tri_unit;
     D.leaf_of = leaf_of;
+    D.shrec = shrec;
     D.units = units;
     D.unit_cdf = cdf;
     D.n_units = nu;
@@ -623,8 +641,9 @@ mt_status mt_scene_set_params(mt_scene s, const float *d_albedo, const float *d_
     MT_CHECK_ARG(s != nullptr, "scene is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if (d_albedo)
-        k_set_albedo<<<grid_for(s->n_tris, 256, s->num_sms), 256, 0, st>>>(d_albedo, (int)s->n_tris,
-                                                                           const_cast<float4 *>(s->dev.mats));
+        k_set_albedo<<<grid_for(s->n_tris, 256, s->num_sms), 256, 0, st>>>(
+            d_albedo, (int)s->n_tris, const_cast<float4 *>(s->dev.mats), s->dev.leaf_of,
+            const_cast<float4 *>(s->dev.shrec));
     if (d_radiance && s->n_em > 0)
         k_set_radiance<<<1, 64, 0, st>>>(d_radiance, s->n_em, const_cast<float4 *>(s->dev.em_rad));
     if (d_medium_albedo)

@@ -268,6 +268,9 @@ struct DevScene {
     const float4 *mats;    // per original triangle: albedo, w = GGX roughness or -1 (Lambert)
     const int32_t *tri_unit; // per original triangle: light unit or -1
     const int32_t *leaf_of;  // per original triangle: its leaf-order index
+    // per leaf-ordered triangle, the two float4 a shading step reads (one 32-byte sector):
+    // geometric normal (winding) + light unit (int bits, -1 = none), material as in mats
+    const float4 *shrec;
     const uint32_t *unit_cdf; // ceil(cdf * 2^24)
     const LightUnit *units;
     const float4 *em_rad;  // per emitter: radiance (rgb)

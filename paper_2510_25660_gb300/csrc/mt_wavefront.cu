@@ -473,11 +473,11 @@ __global__ void __launch_bounds__(128) k_wf_shade_pol(const DevScene s, const Wf
                 const float th = __int_as_float(h.z);
                 const float3 x = xyz(o4) + d * th;
                 if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
-                const float4 p0 = __ldg(&s.tris[3 * k]), p1 = __ldg(&s.tris[3 * k + 1]), p2 = __ldg(&s.tris[3 * k + 2]);
-                const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+                const float4 sn = __ldg(&s.shrec[2 * (size_t)k]);  // normal + light unit
+                const float3 ng = xyz(sn);
                 const float3 wo = -d;
                 const float cwo = dot(ng, wo);
-                const int unit = __ldg(&s.tri_unit[orig]);
+                const int unit = __float_as_int(sn.w);
                 if (unit >= 0 && cwo > 0.f) {  // emission: column 0 of P (unpolarised emitter)
                     const LightUnit U = s.units[unit];
                     float w = 1.0f;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(128) k_wf_shade_pol(const DevScene s, const Wf
                     float3 tb, bb;
                     onb(nn, tb, bb);
                     const float3 wol = to_local(wo, tb, bb, nn);
-                    const float4 mm = __ldg(&s.mats[orig]);
+                    const float4 mm = __ldg(&s.shrec[2 * (size_t)k + 1]);
                     const Mat mat{xyz(mm), mm.w};
                     const float alb[3] = {mm.x, mm.y, mm.z};
                     if (s.n_units > 0) {  // next-event estimate, queued for the shadow stage
@@ -925,11 +925,11 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                 const float th = __int_as_float(h.z);
                 const float3 x = xyz(o4) + dir * th;
                 if (!(depth == 1 && (p.flags & MT_UNWARP))) opl += th;
-                const float4 p0 = ldg_keep(&s.tris[3 * k]), p1 = ldg_keep(&s.tris[3 * k + 1]), p2 = ldg_keep(&s.tris[3 * k + 2]);
-                const float3 ng = normalize(cross(xyz(p1) - xyz(p0), xyz(p2) - xyz(p0)));
+                const float4 sn = __ldg(&s.shrec[2 * (size_t)k]);  // normal + light unit
+                const float3 ng = xyz(sn);
                 const float3 wo = -dir;
                 const float cwo = dot(ng, wo);
-                const int unit = __ldg(&s.tri_unit[orig]);
+                const int unit = __float_as_int(sn.w);
                 // with a medium, emission found by the path counts only at the camera vertex
                 if (unit >= 0 && cwo > 0.f && (!MEDIA || depth == 1)) {
                     const LightUnit U = s.units[unit];
@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     float3 tb, bb;
                     onb(nn, tb, bb);
                     const float3 wol = to_local(wo, tb, bb, nn);
-                    const float4 mm = __ldg(&s.mats[orig]);
+                    const float4 mm = __ldg(&s.shrec[2 * (size_t)k + 1]);
                     const Mat mat{xyz(mm), mm.w};
                     // next-event estimate: a shadow ray carrying its contribution
                     if (s.n_units > 0) {
