@@ -3,7 +3,7 @@
 // Visibility V and segment lengths of the path integral (arXiv 2510.25660,
 // Sec. 3 Eqs. 3 and 8) come from these queries.
 //
-// Node layout (32 bytes = one L2 sector, fetched as two 16-byte loads): one
+// Node layout (32 bytes = one L2 sector, fetched by one 256-bit load): one
 // 32-bit word per child and axis holds that axis' lower plane (low half) and
 // upper plane (high half):
 //   a.x = child 0 x   a.y = child 0 y   a.z = child 0 z   a.w = child 1 x
@@ -82,6 +82,22 @@ __device__ __forceinline__ RayT make_ray(const DevScene &s, float3 o, float3 d) 
 // exponent of 2^23 with one byte permute
 __device__ __forceinline__ float q_plane(uint32_t word, uint32_t sel) {
     return __int_as_float(__byte_perm(word, 0x4B000000u, sel));
+}
+
+// One binary node (32 bytes, 32-byte aligned) in one 256-bit read-only load
+// (sm_100-class); MT_NODE_V8 = 0: two 128-bit loads.
+#ifndef MT_NODE_V8
+#define MT_NODE_V8 1
+#endif
+__device__ __forceinline__ void ldg_node(const uint4 *p, uint4 &a, uint4 &b) {
+#if MT_NODE_V8 && !MT_L2_KEEP_BVH
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
+#else
+    a = ldg_keep(p);
+    b = ldg_keep(p + 1);
+#endif
 }
 
 // Packed arithmetic of sm_100-class GPUs: fma.rn.f32x2 (two independent FMAs,
@@ -178,8 +194,8 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
     uint32_t ref = 0;
     for (;;) {
         if (!(ref & 0x80000000u)) {
-            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
-            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
@@ -242,8 +258,8 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
     uint32_t ref = 0;
     for (;;) {
         if (!(ref & 0x80000000u)) {
-            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
-            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
@@ -304,8 +320,8 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
     while (ref != MT_DONE) {
         // internal nodes; the first leaf met is postponed
         while (ref != MT_DONE && !MT_IS_LEAF(ref)) {
-            const uint4 a = ldg_keep(&s.nodes[2 * ref]);
-            const uint4 b = ldg_keep(&s.nodes[2 * ref + 1]);
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
             slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
@@ -424,8 +440,8 @@ template <bool ANY, bool CNT>
 __device__ __forceinline__ bool trav_step(const DevScene &s, const RayT &r, float tmax, TravState &ts, uint2 *st,
                                           TraceCnt &cnt) {
     if (!(ts.ref & 0x80000000u)) {
-        const uint4 a = ldg_keep(&s.nodes[2 * ts.ref]);
-        const uint4 b = ldg_keep(&s.nodes[2 * ts.ref + 1]);
+        uint4 a, b;
+        ldg_node(&s.nodes[2 * ts.ref], a, b);
         if (CNT) cnt.nodes += 32;
         float tn0, tf0, tn1, tf1;
         slab(r, a.x, a.y, a.z, ts.tbest, tn0, tf0);
