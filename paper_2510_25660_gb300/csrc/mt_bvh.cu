@@ -458,7 +458,13 @@ __global__ void k_children(const Task *tasks, int n_tasks, const Decision *decs,
 }
 
 // one CTA builds the whole subtree of a small task
-__global__ void __launch_bounds__(128) k_build_small(const Task *small, BNode *nodes, int *idx, int *tmp,
+// threads of the CTA that builds one small subtree (any multiple of 32): one
+// warp, so the barriers between its node steps cost little (11.0 ms against
+// 12.8 ms at 128 threads for the 1.16M-triangle scene; the same tree)
+#ifndef MT_BVH_SMALL_THREADS
+#define MT_BVH_SMALL_THREADS 32
+#endif
+__global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task *small, BNode *nodes, int *idx, int *tmp,
                                                      const float4 *plo, const float4 *phi, const float4 *cen,
                                                      int *counters) {
     __shared__ int bins[3 * NB * BIN_INTS];
@@ -937,7 +943,7 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
             MT_CUDA_TRY(cudaStreamSynchronize(st));
         }
     }
-    if (hc[2] > 0) k_build_small<<<hc[2], 128, 0, st>>>(small, nodes, idx, tmp, plo, phi, cen, counters);
+    if (hc[2] > 0) k_build_small<<<hc[2], MT_BVH_SMALL_THREADS, 0, st>>>(small, nodes, idx, tmp, plo, phi, cen, counters);
     MT_CUDA_TRY(cudaGetLastError());
     MT_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
     MT_CUDA_TRY(cudaStreamSynchronize(st));
