@@ -369,6 +369,14 @@ def main():
                        "shared-memory atomics into 48 KB per CTA"}
     except Exception as e:  # reported, not fatal
         aux = {"error": str(e)[:200]}
+    if wavefront:
+        # what bounds the pass: issue slots and lane utilisation from the committed ncu capture of the
+        # same kernel sources (the traversal is issue-bound, not DRAM-bound)
+        prof = os.path.join(ROOT, "profiles", "k_wf_traversal_large_scene.json")
+        if os.path.exists(prof):
+            pd = json.load(open(prof))
+            if pd.get("kernel_hash") == khash and "issue" in pd:
+                aux["issue_ncu"] = pd["issue"]
 
     # e2e: host arrays in, film out, through the public API (scene load + render + read-back)
     e2e = None
