@@ -113,6 +113,7 @@ struct mt_scene_s {
     // NLOS state
     int32_t h_first = -1, h_count = -1;
     uint32_t *hcdf = nullptr;
+    uint32_t *hguide = nullptr;  // MT_HGUIDE_N + 1 entries over hcdf
     float h_area = 0.f;
     float4 *ysamp = nullptr;
     int32_t *ysamp_tri = nullptr;
@@ -257,6 +258,20 @@ __global__ void k_setup_units(const float *tris, const int32_t *unit_tri, const 
 }
 
 // hidden-surface area table for NLOS (same construction, weight = area)
+// guide[g] = smallest i with (g << 12) < cdf[i], or n if none (g = 0..MT_HGUIDE_N)
+__global__ void k_hidden_guide(const uint32_t *cdf, int n, uint32_t *guide) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= MT_HGUIDE_N; g += gridDim.x * blockDim.x) {
+        const uint32_t key = (uint32_t)g << 12;
+        int lo = 0, hi = n;  // answer in [0, n]
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (key < cdf[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        guide[g] = (uint32_t)lo;
+    }
+}
+
 __global__ void k_setup_hidden(const float *tris_leaf4, const int32_t *leaf_of, int first, int n, uint32_t *cdf,
                                float *area_out) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -1132,6 +1147,8 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
         MT_TRY(s->al.alloc(&darea, 1, "hidden area"));
         k_setup_hidden<<<1, 1, 0, st>>>(reinterpret_cast<const float *>(s->dev.tris), s->dev.leaf_of,
                                         (int)sc->hidden_first, (int)sc->hidden_count, s->hcdf, darea);
+        if (!s->hguide) MT_TRY(s->al.alloc(&s->hguide, (size_t)MT_HGUIDE_N + 1, "hidden cdf guide"));
+        k_hidden_guide<<<(MT_HGUIDE_N + 256) / 256, 256, 0, st>>>(s->hcdf, (int)sc->hidden_count, s->hguide);
         MT_CUDA_TRY(cudaMemcpyAsync(&s->h_area, darea, sizeof(float), cudaMemcpyDeviceToHost, st));
         MT_CUDA_TRY(cudaStreamSynchronize(st));
         s->h_first = (int32_t)sc->hidden_first;
@@ -1172,6 +1189,7 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
     p.hidden_first = (int32_t)sc->hidden_first;
     p.hidden_n = (int32_t)sc->hidden_count;
     p.hcdf = s->hcdf;
+    p.hguide = s->hguide;
     p.hidden_area = s->h_area;
     p.tile = cfg.tile;
     if (sc->mode == MT_EXHAUSTIVE) p.n_tiles = sc->n_lasers * ((sc->n_sensors + cfg.tile - 1) / cfg.tile);

@@ -46,6 +46,10 @@ struct NlosParams {
     float fw;                  // wall albedo / pi
     int32_t hidden_first, hidden_n;
     const uint32_t *hcdf;      // ceil(cdf * 2^24) over hidden triangles (original order)
+    // optional guide table (MT_HGUIDE_N + 1 entries): hguide[g] = smallest i with (g << 12) < hcdf[i]
+    // (hidden_n if none), so the pick of a 24-bit key lies in [hguide[key >> 12], hguide[(key >> 12) + 1]];
+    // nullptr = search the whole table
+    const uint32_t *hguide;
     float hidden_area;
     int32_t tile, n_tiles;
     float *film, *steady;
@@ -74,6 +78,8 @@ struct PoolField {
     __host__ __device__ __forceinline__ T &operator[](size_t slot) const { return base[slot * MT_WF_REC]; }
     __host__ __device__ __forceinline__ explicit operator bool() const { return base != nullptr; }
 };
+
+#define MT_HGUIDE_N 4096  // guide-table buckets over the 24-bit keys of the hidden-triangle pick
 
 struct WfParams {
     int32_t H, W, T;

@@ -18,9 +18,16 @@
 
 namespace {
 
+// smallest i with key < hcdf[i] (the last index if none); the guide table only
+// narrows the bracket the same search runs in, so the pick is unchanged
 __device__ __forceinline__ int pick_hidden(const NlosParams &p, uint32_t u) {
     int lo = 0, hi = p.hidden_n - 1;
     const uint32_t key = u >> 8;
+    if (p.hguide) {
+        const uint32_t g = key >> 12;
+        lo = min((int)__ldg(&p.hguide[g]), p.hidden_n - 1);
+        hi = min((int)__ldg(&p.hguide[g + 1]), p.hidden_n - 1);
+    }
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (key < __ldg(&p.hcdf[mid])) hi = mid;
