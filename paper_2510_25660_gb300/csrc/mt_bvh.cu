@@ -614,6 +614,77 @@ __global__ void k_emit(const BNode *nodes, int n, const int *map, const int *fla
     }
 }
 
+// Depth-first preorder of the internal nodes (a node, its left subtree, its
+// right subtree), so that a node's left child is stored right after it and a
+// descent into it usually reads the cache line its parent arrived in.  Walks
+// up the tree are bounded by MT_BVH_WALK steps (the tree depth is checked to be
+// below the traversal stack first); a longer walk sets bit 1 of *bad.
+#ifndef MT_BVH_DFS
+#define MT_BVH_DFS 1
+#endif
+#define MT_BVH_WALK 256
+
+__device__ __forceinline__ bool bn_internal(const BNode *nodes, int i) { return nodes[i].left >= 0; }
+
+__global__ void k_parents(const BNode *nodes, int n, int *parent) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const BNode &b = nodes[i];
+        if (b.left >= 0) {
+            parent[b.left] = i;
+            parent[b.right] = i;
+        }
+    }
+}
+
+// internal-node counts of every subtree, bottom-up: a walk starts at each
+// internal node without internal children and climbs while it is the last of
+// its parent's internal children to arrive
+__global__ void k_subtree_sizes(const BNode *nodes, int n, const int *parent, int *cnt, int *arrive, int *bad) {
+    volatile int *vc = cnt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!bn_internal(nodes, i) || bn_internal(nodes, nodes[i].left) || bn_internal(nodes, nodes[i].right)) continue;
+        int node = i;
+        vc[node] = 1;
+        for (int step = 0;; ++step) {
+            if (step >= MT_BVH_WALK) {
+                atomicOr(bad, 2);
+                break;
+            }
+            const int p = parent[node];
+            if (p < 0) break;
+            const int l = nodes[p].left, r = nodes[p].right;
+            const bool il = bn_internal(nodes, l), ir = bn_internal(nodes, r);
+            const int need = (il ? 1 : 0) + (ir ? 1 : 0);
+            __threadfence();
+            if (atomicAdd(&arrive[p], 1) + 1 < need) break;  // the other child's walk finishes p
+            __threadfence();
+            vc[p] = 1 + (il ? vc[l] : 0) + (ir ? vc[r] : 0);
+            node = p;
+        }
+    }
+}
+
+// preorder rank of every internal node: the sum, over its ancestors, of one
+// (the ancestor) plus the left sibling's subtree where the path turns right
+__global__ void k_preorder(const BNode *nodes, int n, const int *parent, const int *cnt, int *map, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!bn_internal(nodes, i)) continue;
+        int pre = 0, node = i;
+        for (int step = 0;; ++step) {
+            if (step >= MT_BVH_WALK) {
+                atomicOr(bad, 2);
+                break;
+            }
+            const int p = parent[node];
+            if (p < 0) break;
+            const int l = nodes[p].left;
+            pre += 1 + ((node != l && bn_internal(nodes, l)) ? cnt[l] : 0);
+            node = p;
+        }
+        map[i] = pre;
+    }
+}
+
 __global__ void k_emit_root_leaf(const BNode *nodes, uint4 *out, float qlx, float qly, float qlz, float qsx, float qsy,
                                  float qsz) {
     const float qlo[3] = {qlx, qly, qlz}, qs[3] = {qsx, qsy, qsz};
@@ -1040,6 +1111,31 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
     int n_int = last_map + last_flag;
     const bool root_leaf = n_int == 0;
     if (root_leaf) n_int = 1;
+#if MT_BVH_DFS
+    if (!root_leaf) {  // renumber the internal nodes in depth-first preorder (root stays 0)
+        int *parent, *cnt, *arrive, *dbad;
+        MT_TRY(tmpal.alloc(&parent, n_build, "bvh parents"));
+        MT_TRY(tmpal.alloc(&cnt, n_build, "bvh subtree sizes"));
+        MT_TRY(tmpal.alloc(&arrive, n_build, "bvh subtree sizes"));
+        MT_TRY(tmpal.alloc(&dbad, 1, "bvh order check"));
+        MT_CUDA_TRY(cudaMemsetAsync(parent, 0xFF, (size_t)n_build * sizeof(int), st));
+        MT_CUDA_TRY(cudaMemsetAsync(arrive, 0, (size_t)n_build * sizeof(int), st));
+        MT_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), st));
+        const int g = std::min(2048, (n_build + 255) / 256);
+        k_parents<<<g, 256, 0, st>>>(nodes, n_build, parent);
+        k_subtree_sizes<<<g, 256, 0, st>>>(nodes, n_build, parent, cnt, arrive, dbad);
+        k_preorder<<<g, 256, 0, st>>>(nodes, n_build, parent, cnt, map, dbad);
+        MT_CUDA_TRY(cudaGetLastError());
+        int hbad = 0, hroot = 0;
+        MT_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(&hroot, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad || hroot != n_int) {
+            mt::set_error("BVH depth-first order failed (flags %d, %d of %d internal nodes)", hbad, hroot, n_int);
+            return MT_ERR_INTERNAL;
+        }
+    }
+#endif
     MT_TRY(al.alloc(&out->nodes, (size_t)2 * n_int, "bvh nodes"));
     MT_TRY(al.alloc(&out->tris, (size_t)3 * n, "bvh triangles"));
     if (root_leaf)
