@@ -27,10 +27,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # row bands of the end-to-end render, as fractions of the frame height: later bands are smaller so
-# that the one copy that cannot overlap a render is short (measured on the 512-row frame: one band
-# 153 ms, 2 equal bands 147 ms, 4 equal bands 130.5 ms, 8 equal bands 130.3 ms, 160/144/128/80 rows
-# 127.5 ms)
-E2E_BANDS = (160 / 512, 144 / 512, 128 / 512, 80 / 512)
+# that the one copy that cannot overlap a render is short (measured on the 512-row frame with a 31-ms
+# scene creation: one band 153 ms, 2 equal bands 147, 4 equal bands 130.5, 8 equal bands 130.3;
+# with the current kernels: 160/144/128/80 rows 111.0 ms, 144/128/112/80/48 108.4,
+# 128/112/96/80/64/32 108.3, 112/96/96/80/64/40/24 108.9)
+E2E_BANDS = (128 / 512, 112 / 512, 96 / 512, 80 / 512, 64 / 512, 32 / 512)
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = "large static scene: 1,164,296-triangle fBm heightfield + 200 icospheres, 4 area lights, " \
            "512x512 px, T=2048 bins x 0.005 m from 12 m, 256 spp, max_depth 8, NEE+MIS, FP32 film"
