@@ -244,9 +244,12 @@ mt_status mt_read_counters(mt_scene scene, uint64_t *out, int32_t reset, void *s
 
 /* Device time of the wavefront stages of renders launched with
  * MT_OPT_STAGE_TIMING since the last reset (out has 5 entries): out[0] ms in
- * queue setup, camera-ray generation (and ray sorting), out[1] ms in
- * extension-ray traversal (k_wf_extend), out[2] ms in shading (k_wf_shade),
- * out[3] ms in shadow-ray traversal (k_wf_shadow), out[4] iterations.  The
+ * queue setup, camera-ray generation (and ray sorting), out[1] ms in the
+ * traversal pass (k_wf_trace: extension rays, then the shadow rays the
+ * previous shading pass queued; k_wf_extend in the backward, polarized and
+ * dump forms), out[2] ms in shading (k_wf_shade), out[3] ms in shadow passes
+ * of their own (k_wf_shadow in the backward, polarized and dump forms, and
+ * for the last shading pass), out[4] iterations.  The
  * values are complete when the renders have returned (they synchronise their
  * stream).  reset != 0 zeroes them afterwards. */
 mt_status mt_stage_times(mt_scene scene, double *out, int32_t reset);
@@ -300,13 +303,18 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * MT_OPT_NO_GRAPH (NLOS) = enqueue the kernels directly instead of replaying
  * the cached CUDA graph.  MT_OPT_REFILL(k) (RENDER/BACKWARD, k = 1..32) = a
  * warp starts new paths only once at least k of its lanes are idle (default 1:
- * every idle lane is refilled at once).  MT_OPT_WAVEFRONT (RENDER, surfaces
- * only) = render in wavefront form: a pool of up to 4M paths in device memory
- * (about 150 B per path, allocated by the first such render of a scene) with
- * separate kernels for camera rays, extension rays, shading and shadow rays,
- * each warp claiming rays of one kind from a queue; films are zeroed and
- * written with global atomics (tile, priv_bins and the refill option do not
- * apply); the call synchronises `stream` every few iterations.
+ * every idle lane is refilled at once).  MT_OPT_WAVEFRONT (RENDER and
+ * BACKWARD; forward, phasor, tangent, polarized and backward renders, with or
+ * without a medium) = render in wavefront form: a pool of up to 4M paths in
+ * device memory (one 128-B record per path plus queues and shadow-ray records,
+ * about 200 B per path; polarized renders add 208 B, backward renders 48 B per
+ * vertex; allocated by the first such render of a scene, which therefore must
+ * not be captured in a graph) with separate kernels for camera rays, the
+ * traversal pass (extension rays, then the previous shading pass's shadow
+ * rays), shading and, for backward and polarized renders, a shadow pass of its
+ * own; each warp claims rays from a queue; films are zeroed and written with
+ * global atomics (tile, priv_bins and the refill option do not apply); the
+ * call synchronises `stream` every few iterations.
  * MT_OPT_DYNAMIC_FETCH (with MT_OPT_WAVEFRONT) = traversal lanes whose ray is
  * done take the next queued ray instead of waiting for their warp, as soon as
  * MT_OPT_REFILL(k) lanes of the warp are idle (k = 0: 8; k > 32: 32).
@@ -317,7 +325,9 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * queued rays are sorted by direction octant and the Morton code of their
  * origin, so that a warp traces similar rays (the film is the same).
  * MT_OPT_STAGE_TIMING (with MT_OPT_WAVEFRONT) = CUDA events on the render
- * stream at every stage boundary; read the totals with mt_stage_times.
+ * stream at every stage boundary; read the totals with mt_stage_times (the
+ * extension stage holds the whole traversal pass, shadow rays included, in the
+ * forms whose shadow rays are traced there).
  * MT_OPT_SORT_SHADOW (with MT_OPT_WAVEFRONT) = shadow rays are traced in the
  * order of (direction cell, origin Morton code) (the film is the same). */
 #define MT_OPT_AGGREGATE 1u
