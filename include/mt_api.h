@@ -165,9 +165,14 @@ mt_status mt_film_set_window(mt_film film, int32_t frame_H, int32_t row0);
  * Philox stream keyed by `seed`, at most max_depth segments each (1 = emitters
  * seen directly), next-event estimation with power-heuristic MIS (no MIS in a
  * medium), every contribution splatted into the bin of its own optical path
- * length and into the steady image.  Asynchronous on `stream`; allocates
- * nothing.  Errors: INVALID_ARGUMENT (spp < 1, max_depth outside [1, 64],
- * film C != 3), CUDA. */
+ * length and into the steady image.  Asynchronous on `stream`.  The persistent
+ * form (the default) allocates nothing.  The wavefront form (MT_OPT_WAVEFRONT
+ * in mt_set_launch) allocates its path pool on the first wavefront render of a
+ * scene that needs a larger pool than the scene holds (a render of more paths,
+ * up to the pool size of mt_set_wavefront_pool), synchronises `stream` every
+ * few iterations, and refuses to run under stream capture when it would
+ * allocate (INVALID_ARGUMENT).  Errors: INVALID_ARGUMENT (spp < 1, max_depth
+ * outside [1, 64], film C != 3), OUT_OF_MEMORY (path pool), CUDA. */
 mt_status mt_render(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, int32_t max_depth,
                     uint64_t sample_offset, void *stream);
 
@@ -232,7 +237,9 @@ mt_status mt_render_backward(mt_scene scene, mt_film film, const float *d_grad_f
                              float *d_grad_medium_albedo, void *stream);
 
 /* Synchronise `stream` and report device-side errors raised since the last
- * call (traversal stack overflow -> INTERNAL, bounded waits -> TIMEOUT). */
+ * call (traversal stack overflow -> INTERNAL, bounded waits -> TIMEOUT).  The
+ * scene names the device error word that the kernels of its renders set (each
+ * scene has its own), so errors of one scene do not surface on another. */
 mt_status mt_sync(mt_scene scene, void *stream);
 
 /* Counters accumulated by launches on this scene since the last reset:
@@ -330,6 +337,20 @@ mt_status mt_set_launch(mt_scene scene, int32_t kind, int32_t threads, int32_t t
  * forms whose shadow rays are traced there).
  * MT_OPT_SORT_SHADOW (with MT_OPT_WAVEFRONT) = shadow rays are traced in the
  * order of (direction cell, origin Morton code) (the film is the same). */
+/* Paths in flight of the wavefront form: its path pool holds at most
+ * max_paths paths (0 = the default 4,194,304; otherwise 32 .. 4,194,304).
+ * A render of more paths than the pool holds starts new paths in the slots
+ * that finished paths free, so every path is traced exactly once and the
+ * result does not depend on the pool size (up to the order of floating-point
+ * additions).  A smaller pool takes less device memory (about 200 B per path,
+ * see MT_OPT_WAVEFRONT) and refills more often.  Takes effect at the next
+ * wavefront render, which allocates a pool of this size if the scene holds a
+ * smaller one (a larger pool already held is reused, only max_paths slots of
+ * it).  Dividing max_paths by the threads of one wavefront launch (8 CTAs of
+ * 256 threads per SM) gives the paths per thread the autotuner searches over.
+ * INVALID_ARGUMENT outside the range. */
+mt_status mt_set_wavefront_pool(mt_scene scene, int64_t max_paths);
+
 #define MT_OPT_AGGREGATE 1u
 #define MT_OPT_NO_GRAPH 2u
 #define MT_OPT_WAVEFRONT 4u
@@ -403,11 +424,12 @@ mt_status mt_microbench(int32_t kind, void *d_buf, int64_t bytes, int32_t iters,
  * sees a larger exhaustive grid.  That fails or is unwelcome for applications
  * whose device memory is reserved up front by their own allocator or a fixed
  * budget (a cudaMalloc outside that pool can fail once the budget is taken),
- * and for render loops that must not stall on an allocation.  mt_render_nlos_noalloc computes the same impulse responses as
- * mt_render_nlos (same arguments, same result up to the order of
- * floating-point additions) but keeps its per-call scratch in one static
- * device array of 4.75 MiB compiled into libmt.so, which every GPU that loads
- * the library holds until the process exits.  It calls no cudaMalloc or
+ * and for render loops that must not stall on an allocation.
+ * mt_render_nlos_noalloc computes the same impulse responses as mt_render_nlos
+ * (same arguments, same launch configuration and options, same result up to
+ * the order of floating-point additions) but keeps its per-call scratch in one
+ * static device array of 5.27 MiB compiled into libmt.so, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc or
  * cudaFree.
  *   - Limits: at most 65,536 hidden triangles and, for EXHAUSTIVE scans,
  *     n_lasers * spp <= 131,072; larger requests return
@@ -415,8 +437,11 @@ mt_status mt_microbench(int32_t kind, void *d_buf, int64_t bytes, int32_t iters,
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) for that device; make that first call before any
  *     stream capture.
- *   - Each call rebuilds the hidden-surface table in the array and reads the
- *     total hidden area back to the host, so it synchronises `stream` once.
+ *   - Each call rebuilds the hidden-surface table (with its guide table) in the
+ *     array with four small kernels on `stream`; the capture kernels read the
+ *     hidden area from the array, so the call does not synchronise `stream`.
+ *     A hidden range of zero total area gives a zero film (mt_render_nlos
+ *     rejects it).
  *   - All calls share the array and leave their contents in it: calls that
  *     overlap on the GPU (for example on two streams, or from two threads)
  *     race and corrupt each other's results; serialise them.

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mt_scene_set_pulse": (C.c_int, [_P, _U32, C.c_float, C.c_float]),
     "mt_scene_stats": (C.c_int, [_P, _P]),
     "mt_set_launch": (C.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _U32]),
+    "mt_set_wavefront_pool": (C.c_int, [_P, _I64]),
     "mt_scene_destroy": (None, [_P]),
     "mt_film_destroy": (None, [_P]),
     "mt_probe_philox": (C.c_int, [_U64, _P, _I64, _P, _P]),
@@ -217,6 +218,10 @@ def mt_set_launch(scene, kind, threads, tile, ctas_per_sm, priv_bins, options):
     return _call("mt_set_launch", scene, kind, threads, tile, ctas_per_sm, priv_bins, options)
 
 
+def mt_set_wavefront_pool(scene, max_paths):
+    return _call("mt_set_wavefront_pool", scene, max_paths)
+
+
 def mt_scene_destroy(scene):
     load().mt_scene_destroy(scene)
 
@@ -342,6 +347,10 @@ class Scene:
 
     def set_launch(self, kind, threads=0, tile=0, ctas_per_sm=0, priv_bins=-1, options=0):
         mt_set_launch(self.h, kind, threads, tile, ctas_per_sm, priv_bins, options)
+
+    def set_wavefront_pool(self, max_paths=0):
+        """Paths in flight of the wavefront form (0 = the default 4,194,304)."""
+        mt_set_wavefront_pool(self.h, int(max_paths))
 
 
 class Film:
@@ -551,6 +560,7 @@ def _autograd():
             scene.set_params(albedo=albedo.detach().contiguous(), radiance=radiance.detach().contiguous())
             film, steady = render(scene, H, W, T, start, width, spp, seed, max_depth)
             ctx.args = (scene, T, start, width, spp, seed, max_depth)
+            ctx.hw = (H, W)
             ctx.save_for_backward(albedo, radiance)
             return film, steady
 
@@ -562,7 +572,8 @@ def _autograd():
             g_film = g_film.contiguous() if g_film is not None else None
             g_steady = g_steady.contiguous() if g_steady is not None else None
             if g_film is None:
-                g_film = torch.zeros((scene.H, scene.W, T, 3), device="cuda")
+                H, W = ctx.hw
+                g_film = torch.zeros((H, W, T, 3), device="cuda")
             ga, gr, _ = render_backward(scene, T, start, width, spp, seed, max_depth, g_film, g_steady)
             return ga, gr[:radiance.shape[0]], None, None, None, None, None, None, None, None, None
 

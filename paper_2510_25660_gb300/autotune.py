@@ -1,10 +1,13 @@
 """Launch-configuration autotuner for the render, backward and NLOS kernels.
 
 Searches over threads per CTA, pixels (scan rows) per tile -- which sets the
-shared-memory histogram size and hence the privatisation depth -- and CTAs per
-SM, timing real launches with CUDA events.  Results are cached in a JSON file
-(MT_AUTOTUNE_CACHE, default ~/.cache/mtr_autotune.json) keyed by device name,
-kind and workload shape, and applied with mt_set_launch.
+shared-memory histogram size and hence the privatisation depth -- CTAs per
+SM, the kernel form and option bits, and, for the wavefront form, the paths
+in flight per thread (the path-pool size divided by the threads of one
+wavefront launch, 8 CTAs of 256 threads per SM), timing real launches with
+CUDA events.  Results are cached in a JSON file (MT_AUTOTUNE_CACHE, default
+~/.cache/mtr_autotune.json) keyed by device name, kind and workload shape,
+and applied with mt_set_launch and mt_set_wavefront_pool.
 """
 from __future__ import annotations
 
@@ -57,12 +60,28 @@ def apply(scene, kind, sc, film, spp, depth) -> dict | None:
     if cfg:
         scene.set_launch(KINDS[kind], cfg["threads"], cfg["tile"], cfg["ctas_per_sm"], cfg.get("priv", -1),
                          cfg.get("options", 0))
+        if kind != "nlos":
+            scene.set_wavefront_pool(pool_paths(cfg.get("paths_per_thread", 0)))
     return cfg
+
+
+WF_CTAS_PER_SM, WF_THREADS = 8, 256  # the grid of every wavefront launch
+
+
+def pool_paths(paths_per_thread) -> int:
+    """Path-pool size for `paths_per_thread` paths per thread of a wavefront
+    launch on this GPU (0 = the library's default pool)."""
+    if not paths_per_thread:
+        return 0
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return int(min(1 << 22, max(32, paths_per_thread * sms * WF_CTAS_PER_SM * WF_THREADS)))
 
 
 def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60.0) -> dict:
     """Time `run()` (one launch of the kernel) under each candidate
-    (threads, tile, ctas_per_sm, priv_bins); keep and cache the fastest."""
+    (threads, tile, ctas_per_sm, priv_bins[, options[, paths_per_thread]]);
+    keep and cache the fastest."""
     import torch
     best = None
     t_end = time.time() + budget_s
@@ -70,15 +89,19 @@ def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60
     for cand in candidates:
         threads, tile, cps, priv = cand[:4]
         opts = cand[4] if len(cand) > 4 else 0
+        ppt = cand[5] if len(cand) > 5 else 0
         if time.time() > t_end:
             break
+        rec = {"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts,
+               "paths_per_thread": ppt}
         scene.set_launch(KINDS[kind], threads, tile, cps, priv, opts)
+        if kind != "nlos":
+            scene.set_wavefront_pool(pool_paths(ppt))
         try:
             run()
             torch.cuda.synchronize()
         except Exception as e:  # a configuration that does not fit is skipped
-            results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts,
-                            "error": str(e)[:80]})
+            results.append(dict(rec, error=str(e)[:80]))
             continue
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -87,19 +110,31 @@ def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        results.append({"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts, "ms": ms})
+        results.append(dict(rec, ms=ms))
         if best is None or ms < best["ms"]:
-            best = {"threads": threads, "tile": tile, "ctas_per_sm": cps, "priv": priv, "options": opts, "ms": ms}
+            best = dict(rec, ms=ms)
     if best is None:
         raise RuntimeError("no launch configuration ran")
     scene.set_launch(KINDS[kind], best["threads"], best["tile"], best["ctas_per_sm"], best["priv"], best["options"])
+    if kind != "nlos":
+        scene.set_wavefront_pool(pool_paths(best["paths_per_thread"]))
     d = _load()
     d[_key(kind, sc, film, spp, depth)] = dict(best, results=results)
     _store(d)
     return best
 
 
-def _candidates(kind, film_T):
+def candidates(kind, film_T, wavefront_only=False):
+    """The search space: for NLOS threads x scan rows per CTA tile x
+    privatisation (all bins / none) x warp-aggregated atomics; for renders
+    the persistent kernel's threads x pixels per warp tile x privatisation
+    depth (all that fit, none, T/4, T/2) x options (aggregation, deferred
+    refill), and the wavefront form at 1, 2, 4 and 8 paths per thread and
+    the default pool."""
+    return _candidates(kind, film_T, wavefront_only)
+
+
+def _candidates(kind, film_T, wavefront_only=False):
     out = []
     if kind == "nlos":
         for threads in (128, 256):
@@ -108,13 +143,14 @@ def _candidates(kind, film_T):
                     for opt in (0, 1):
                         out.append((threads, tile, 0, priv, opt))
         return out
-    for threads in (128, 256):
-        for tile in (1, 2):
-            for priv in (-1, 0, film_T // 4, film_T // 2):
-                for opt in (0, 1, 16 << 8):
-                    out.append((threads, tile, 0, priv, opt))
-    if kind == "render":
-        out.append((256, 1, 0, 0, 4))  # wavefront form
+    if not wavefront_only:
+        for threads in (128, 256):
+            for tile in (1, 2):
+                for priv in (-1, 0, film_T // 4, film_T // 2):
+                    for opt in (0, 1, 16 << 8):
+                        out.append((threads, tile, 0, priv, opt, 0))
+    for ppt in (1, 2, 4, 8, 0):  # wavefront form; 0 = the default pool (about 13 paths per thread)
+        out.append((256, 1, 0, 0, 4, ppt))
     return out
 
 

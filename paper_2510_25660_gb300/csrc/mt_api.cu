@@ -111,9 +111,11 @@ struct mt_scene_s {
     unsigned long long *counters = nullptr;
     float *m_params = nullptr;
     // NLOS state
-    int32_t h_first = -1, h_count = -1;
+    int32_t h_first = -1, h_count = -1, h_cap = 0;
     uint32_t *hcdf = nullptr;
     uint32_t *hguide = nullptr;  // MT_HGUIDE_N + 1 entries over hcdf
+    double *hprefix = nullptr;   // running sums of the hidden areas (table build)
+    float *harea = nullptr;
     float h_area = 0.f;
     float4 *ysamp = nullptr;
     int32_t *ysamp_tri = nullptr;
@@ -123,6 +125,7 @@ struct mt_scene_s {
     // wavefront path pool
     long long launches = 0;  // kernels launched by this scene's render calls
     uint32_t wf_cap = 0;
+    uint32_t wf_pool_max = MT_WF_POOL_DEFAULT;  // paths in flight (mt_set_wavefront_pool)
     float4 *wf_o = nullptr, *wf_d = nullptr, *wf_beta = nullptr, *wf_sh_o = nullptr, *wf_sh_d = nullptr,
            *wf_sh_c = nullptr;
     uint4 *wf_meta = nullptr, *wf_sh_m = nullptr;
@@ -272,29 +275,48 @@ __global__ void k_hidden_guide(const uint32_t *cdf, int n, uint32_t *guide) {
     }
 }
 
-__global__ void k_setup_hidden(const float *tris_leaf4, const int32_t *leaf_of, int first, int n, uint32_t *cdf,
-                               float *area_out) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const float4 *t4 = reinterpret_cast<const float4 *>(tris_leaf4);
-    double tot = 0.0;
-    for (int i = 0; i < n; ++i) {
+// hidden-surface area table in three passes whose result equals one sequential
+// loop in double: the areas in parallel, their running sum in index order by one
+// thread (the only order-dependent step), then the quantised CDF in parallel.
+__global__ void k_hidden_area(const float4 *t4, const int32_t *leaf_of, int first, int n, double *area) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int k = leaf_of[first + i];
         const float4 a = t4[3 * k], b = t4[3 * k + 1], c = t4[3 * k + 2];
         const float v[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
-        tot = __dadd_rn(tot, tri_area_d(v));
+        area[i] = tri_area_d(v);
     }
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const int k = leaf_of[first + i];
-        const float4 a = t4[3 * k], b = t4[3 * k + 1], c = t4[3 * k + 2];
-        const float v[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
-        acc = __dadd_rn(acc, tri_area_d(v));
-        double cc = __ddiv_rn(acc, tot);
-        if (i == n - 1) cc = 1.0;
+}
+
+// in place: area[i] -> area[0] + ... + area[i] (left to right, rounded once per addition)
+__global__ void k_hidden_prefix(double *acc, int n) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double s = 0.0;
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = acc[i + j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            s = __dadd_rn(s, v[j]);
+            acc[i + j] = s;
+        }
+    }
+    for (; i < n; ++i) {
+        s = __dadd_rn(s, acc[i]);
+        acc[i] = s;
+    }
+}
+
+// cdf[i] = ceil(prefix[i] / total * 2^24), the last entry 2^24; total area as float
+__global__ void k_hidden_cdf(const double *prefix, int n, uint32_t *cdf, float *area_out) {
+    const double tot = prefix[n - 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double cc = i == n - 1 ? 1.0 : __ddiv_rn(prefix[i], tot);
         const double q = ceil(cc * 16777216.0);
         cdf[i] = (uint32_t)(q > 16777216.0 ? 16777216.0 : q);
     }
-    *area_out = (float)tot;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *area_out = (float)tot;
 }
 
 struct CamOut {
@@ -804,7 +826,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
                                   cudaStream_t st, bool tangent = false, bool backward = false,
                                   bool polarized = false) {
     const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
-    const uint32_t P = (uint32_t)std::min<unsigned long long>(total, 1ull << 22);
+    const uint32_t P = (uint32_t)std::min<unsigned long long>(total, s->wf_pool_max);
     if (P > s->wf_cap) {
         cudaStreamCaptureStatus cs;
         MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
@@ -850,8 +872,8 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
             auto &al = s->al;
             MT_TRY(al.alloc(&s->wf_rec, 3 * need, "path replay vertex records"));
             if (!s->wf_fin) {
-                MT_TRY(al.alloc(&s->wf_fin, (size_t)(1u << 22), "path replay queue"));
-                MT_TRY(al.alloc(&s->wf_shown, (size_t)(1u << 22), "path replay shadow records"));
+                MT_TRY(al.alloc(&s->wf_fin, (size_t)MT_WF_POOL_DEFAULT, "path replay queue"));
+                MT_TRY(al.alloc(&s->wf_shown, (size_t)MT_WF_POOL_DEFAULT, "path replay shadow records"));
             }
             s->wf_rec_cap = need;
         }
@@ -1121,8 +1143,8 @@ mt_status mt_render_backward(mt_scene s, mt_film f, const float *d_grad_film, co
                          d_grad_radiance, d_grad_medium_albedo, nullptr, 0, nullptr, (cudaStream_t)stream);
 }
 
-static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed,
-                              uint64_t sample_offset, NlosParams &p, LaunchCfg &cfg, cudaStream_t st) {
+// argument checks shared by every NLOS entry point
+static mt_status nlos_check(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t sample_offset) {
     MT_CHECK_ARG(s != nullptr && f != nullptr && sc != nullptr, "scene, film or scan is NULL");
     MT_CHECK_ARG(f->C == 1, "NLOS films have C = 1");
     MT_CHECK_ARG(sc->mode == MT_CONFOCAL || sc->mode == MT_EXHAUSTIVE, "unknown scan mode");
@@ -1137,35 +1159,30 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
     const float nl = std::sqrt(sc->wall_normal[0] * sc->wall_normal[0] + sc->wall_normal[1] * sc->wall_normal[1] +
                                sc->wall_normal[2] * sc->wall_normal[2]);
     MT_CHECK_ARG(std::fabs(nl - 1.0f) < 1e-3f, "wall normal must be a unit vector");
-    if (s->h_first != (int32_t)sc->hidden_first || s->h_count != (int32_t)sc->hidden_count) {
-        cudaStreamCaptureStatus cs;
-        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
-                     "the first NLOS call for a hidden range must not be captured (it builds the sampling table)");
-        if (!s->hcdf || s->h_count < (int32_t)sc->hidden_count) MT_TRY(s->al.alloc(&s->hcdf, sc->hidden_count, "hidden cdf"));
-        float *darea;
-        MT_TRY(s->al.alloc(&darea, 1, "hidden area"));
-        k_setup_hidden<<<1, 1, 0, st>>>(reinterpret_cast<const float *>(s->dev.tris), s->dev.leaf_of,
-                                        (int)sc->hidden_first, (int)sc->hidden_count, s->hcdf, darea);
-        if (!s->hguide) MT_TRY(s->al.alloc(&s->hguide, (size_t)MT_HGUIDE_N + 1, "hidden cdf guide"));
-        k_hidden_guide<<<(MT_HGUIDE_N + 256) / 256, 256, 0, st>>>(s->hcdf, (int)sc->hidden_count, s->hguide);
-        MT_CUDA_TRY(cudaMemcpyAsync(&s->h_area, darea, sizeof(float), cudaMemcpyDeviceToHost, st));
-        MT_CUDA_TRY(cudaStreamSynchronize(st));
-        s->h_first = (int32_t)sc->hidden_first;
-        s->h_count = (int32_t)sc->hidden_count;
-    }
-    if (sc->mode == MT_EXHAUSTIVE) {
-        const long long need = (long long)sc->n_lasers * spp;
-        if (need > s->ysamp_cap) {
-            cudaStreamCaptureStatus cs;
-            MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-            MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
-                         "the first exhaustive NLOS call of this size must not be captured (it sizes its scratch)");
-            MT_TRY(s->al.alloc(&s->ysamp, (size_t)need * 2, "nlos hidden samples"));
-            MT_TRY(s->al.alloc(&s->ysamp_tri, (size_t)need, "nlos hidden samples"));
-            s->ysamp_cap = need;
-        }
-    }
+    return MT_OK;
+}
+
+// Hidden-surface sampling table of triangles [first, first + n) into cdf [n] and
+// guide [MT_HGUIDE_N + 1], with prefix [n] doubles of scratch and the total area
+// (float) written to *area; asynchronous on st.
+static mt_status hidden_table(mt_scene s, int first, int n, uint32_t *cdf, uint32_t *guide, double *prefix,
+                              float *area, cudaStream_t st) {
+    const int g = grid_for(n, 256, s->num_sms);
+    k_hidden_area<<<g, 256, 0, st>>>(s->dev.tris, s->dev.leaf_of, first, n, prefix);
+    k_hidden_prefix<<<1, 1, 0, st>>>(prefix, n);
+    k_hidden_cdf<<<g, 256, 0, st>>>(prefix, n, cdf, area);
+    k_hidden_guide<<<(MT_HGUIDE_N + 256) / 256, 256, 0, st>>>(cdf, n, guide);
+    MT_CUDA_TRY(cudaGetLastError());
+    return MT_OK;
+}
+
+// Launch parameters of an NLOS capture over the given sampling table and scratch
+// (area_dev: device copy of the hidden area read by the kernels, or null to use
+// `area`); shared by the allocating and the allocation-free entry points.
+static void nlos_fill(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed, uint64_t sample_offset,
+                      const uint32_t *cdf, const uint32_t *guide, float area, const float *area_dev, float4 *ysamp,
+                      int32_t *ysamp_tri, int *tile_counter, NlosParams &p, LaunchCfg &cfg) {
+    const long long rows = sc->mode == MT_EXHAUSTIVE ? (long long)sc->n_lasers * sc->n_sensors : sc->n_lasers;
     int D;
     cfg = render_cfg(s, MT_LAUNCH_NLOS, (int)rows, f->T, 1, 0, D);
     p = NlosParams{};
@@ -1188,18 +1205,62 @@ static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t 
     p.fw = sc->wall_albedo / MT_PI;
     p.hidden_first = (int32_t)sc->hidden_first;
     p.hidden_n = (int32_t)sc->hidden_count;
-    p.hcdf = s->hcdf;
-    p.hguide = s->hguide;
-    p.hidden_area = s->h_area;
+    p.hcdf = cdf;
+    p.hguide = guide;
+    p.hidden_area = area;
+    p.hidden_area_dev = area_dev;
     p.tile = cfg.tile;
     if (sc->mode == MT_EXHAUSTIVE) p.n_tiles = sc->n_lasers * ((sc->n_sensors + cfg.tile - 1) / cfg.tile);
     else p.n_tiles = (int)((rows + cfg.tile - 1) / cfg.tile);
     p.film = f->film;
     p.steady = f->steady;
-    p.ysamp = s->ysamp;
-    p.ysamp_tri = s->ysamp_tri;
-    p.tile_counter = s->tile_counter + 1;
+    p.ysamp = ysamp;
+    p.ysamp_tri = ysamp_tri;
+    p.tile_counter = tile_counter;
     p.aggregate = (cfg.options & MT_OPT_AGGREGATE) ? 1 : 0;
+}
+
+static mt_status nlos_prepare(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed,
+                              uint64_t sample_offset, NlosParams &p, LaunchCfg &cfg, cudaStream_t st) {
+    MT_TRY(nlos_check(s, f, sc, spp, sample_offset));
+    if (s->h_first != (int32_t)sc->hidden_first || s->h_count != (int32_t)sc->hidden_count) {
+        cudaStreamCaptureStatus cs;
+        MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                     "the first NLOS call for a hidden range must not be captured (it builds the sampling table)");
+        if (s->h_cap < (int32_t)sc->hidden_count) {
+            s->h_first = -1;
+            MT_TRY(s->al.alloc(&s->hcdf, sc->hidden_count, "hidden cdf"));
+            MT_TRY(s->al.alloc(&s->hprefix, sc->hidden_count, "hidden area sums"));
+            s->h_cap = (int32_t)sc->hidden_count;
+        }
+        if (!s->hguide) MT_TRY(s->al.alloc(&s->hguide, (size_t)MT_HGUIDE_N + 1, "hidden cdf guide"));
+        if (!s->harea) MT_TRY(s->al.alloc(&s->harea, 1, "hidden area"));
+        MT_TRY(hidden_table(s, (int)sc->hidden_first, (int)sc->hidden_count, s->hcdf, s->hguide, s->hprefix,
+                            s->harea, st));
+        float area = 0.f;
+        MT_CUDA_TRY(cudaMemcpyAsync(&area, s->harea, sizeof(float), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        s->h_first = -1;  // a failure below leaves no table behind
+        MT_CHECK_ARG(area > 0.f, "the hidden triangles have no area");
+        s->h_area = area;
+        s->h_first = (int32_t)sc->hidden_first;
+        s->h_count = (int32_t)sc->hidden_count;
+    }
+    if (sc->mode == MT_EXHAUSTIVE) {
+        const long long need = (long long)sc->n_lasers * spp;
+        if (need > s->ysamp_cap) {
+            cudaStreamCaptureStatus cs;
+            MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+            MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
+                         "the first exhaustive NLOS call of this size must not be captured (it sizes its scratch)");
+            MT_TRY(s->al.alloc(&s->ysamp, (size_t)need * 2, "nlos hidden samples"));
+            MT_TRY(s->al.alloc(&s->ysamp_tri, (size_t)need, "nlos hidden samples"));
+            s->ysamp_cap = need;
+        }
+    }
+    nlos_fill(s, f, sc, spp, seed, sample_offset, s->hcdf, s->hguide, s->h_area, nullptr, s->ysamp, s->ysamp_tri,
+              s->tile_counter + 1, p, cfg);
     return MT_OK;
 }
 
@@ -1233,8 +1294,10 @@ mt_status mt_render_nlos(mt_scene s, mt_film f, const mt_scan *scan, int32_t spp
     if (!gc.exec || gc.key != key) {
         if (!s->cap_stream) MT_CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g;
+        const long long launches = s->launches;  // counted when the graph runs
         MT_CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         const mt_status es = nlos_enqueue(s, f, p, cfg, false, s->cap_stream);
+        s->launches = launches;
         const cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
         if (es != MT_OK) {
             if (ce == cudaSuccess) cudaGraphDestroy(g);
@@ -1329,6 +1392,14 @@ mt_status mt_set_launch(mt_scene s, int32_t kind, int32_t threads, int32_t tile,
     return MT_OK;
 }
 
+mt_status mt_set_wavefront_pool(mt_scene s, int64_t max_paths) {
+    MT_CHECK_ARG(s != nullptr, "scene is NULL");
+    MT_CHECK_ARG(max_paths == 0 || (max_paths >= 32 && max_paths <= (int64_t)MT_WF_POOL_DEFAULT),
+                 "max_paths must be 0 or lie in [32, %u]", MT_WF_POOL_DEFAULT);
+    s->wf_pool_max = max_paths == 0 ? MT_WF_POOL_DEFAULT : (uint32_t)max_paths;
+    return MT_OK;
+}
+
 mt_status mt_probe_philox(uint64_t seed, const uint32_t *d_counters, int64_t n, uint32_t *d_out, void *stream) {
     MT_CHECK_ARG(d_counters != nullptr && d_out != nullptr && n >= 0, "bad arguments");
     if (n == 0) return MT_OK;
@@ -1364,17 +1435,21 @@ mt_status mt_probe_bins(const float *d_opl, int64_t n, float start, float width,
 
 // ---------------------------------------------------------------------------
 // NLOS capture that allocates nothing: the per-call scratch (tile counter,
-// hidden-surface table, per-laser hidden samples) lives in one static device
-// array compiled into the library instead of scene-owned buffers.
+// hidden-surface table with its guide table, running area sums, per-laser
+// hidden samples) lives in one static device array compiled into the library
+// instead of scene-owned buffers.
 // ---------------------------------------------------------------------------
 #define MT_NOALLOC_MAX_HIDDEN (1 << 16)
 #define MT_NOALLOC_MAX_SAMPLES (1 << 17)
 namespace {
-constexpr size_t NA_HDR = 256;                                    // tile counter at 0, hidden area at 16
-constexpr size_t NA_CDF = (size_t)MT_NOALLOC_MAX_HIDDEN * 4;      // u32 table per hidden triangle
-constexpr size_t NA_YS = (size_t)MT_NOALLOC_MAX_SAMPLES * 32;     // two float4 per (laser, sample)
-constexpr size_t NA_YT = (size_t)MT_NOALLOC_MAX_SAMPLES * 4;      // hidden triangle per (laser, sample)
-constexpr size_t NA_BYTES = NA_HDR + NA_CDF + NA_YS + NA_YT;     // 4.75 MiB
+constexpr size_t na_up(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t NA_HDR = 256;                                         // tile counter at 0, hidden area at 16
+constexpr size_t NA_CDF = (size_t)MT_NOALLOC_MAX_HIDDEN * 4;           // u32 table per hidden triangle
+constexpr size_t NA_GUIDE = na_up(((size_t)MT_HGUIDE_N + 1) * 4);      // guide table over the u32 table
+constexpr size_t NA_PREFIX = (size_t)MT_NOALLOC_MAX_HIDDEN * 8;        // running area sums (double)
+constexpr size_t NA_YS = (size_t)MT_NOALLOC_MAX_SAMPLES * 32;          // two float4 per (laser, sample)
+constexpr size_t NA_YT = (size_t)MT_NOALLOC_MAX_SAMPLES * 4;           // hidden triangle per (laser, sample)
+constexpr size_t NA_BYTES = NA_HDR + NA_CDF + NA_GUIDE + NA_PREFIX + NA_YS + NA_YT;  // 5.27 MiB
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_mt_noalloc_scratch[NA_BYTES];
@@ -1402,20 +1477,7 @@ static mt_status noalloc_scratch(unsigned char **out) {
 extern "C" mt_status mt_render_nlos_noalloc(mt_scene s, mt_film f, const mt_scan *sc, int32_t spp, uint64_t seed,
                                             uint64_t sample_offset, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    MT_CHECK_ARG(s != nullptr && f != nullptr && sc != nullptr, "scene, film or scan is NULL");
-    MT_CHECK_ARG(f->C == 1, "NLOS films have C = 1");
-    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || sc->mode == MT_EXHAUSTIVE, "unknown scan mode");
-    MT_CHECK_ARG(sc->lasers != nullptr && sc->n_lasers >= 1, "no laser points");
-    MT_CHECK_ARG(sc->mode == MT_CONFOCAL || (sc->sensors != nullptr && sc->n_sensors >= 1), "no sensor points");
-    const long long rows = sc->mode == MT_EXHAUSTIVE ? (long long)sc->n_lasers * sc->n_sensors : sc->n_lasers;
-    MT_CHECK_ARG((long long)f->H * f->W == rows, "film H*W = %lld must equal the number of scan pairs %lld",
-                 (long long)f->H * f->W, rows);
-    MT_CHECK_ARG(sc->hidden_count >= 1 && (int64_t)sc->hidden_first + sc->hidden_count <= s->n_tris,
-                 "hidden triangle range out of bounds");
-    MT_CHECK_ARG(spp >= 1 && sample_offset + (uint64_t)spp <= 0xFFFFFFFFull, "bad spp / sample_offset");
-    const float nl = std::sqrt(sc->wall_normal[0] * sc->wall_normal[0] + sc->wall_normal[1] * sc->wall_normal[1] +
-                               sc->wall_normal[2] * sc->wall_normal[2]);
-    MT_CHECK_ARG(std::fabs(nl - 1.0f) < 1e-3f, "wall normal must be a unit vector");
+    MT_TRY(nlos_check(s, f, sc, spp, sample_offset));
     MT_CHECK_ARG(sc->hidden_count <= (uint32_t)MT_NOALLOC_MAX_HIDDEN,
                  "mt_render_nlos_noalloc: %u hidden triangles exceed the static scratch limit of %d",
                  sc->hidden_count, MT_NOALLOC_MAX_HIDDEN);
@@ -1426,50 +1488,22 @@ extern "C" mt_status mt_render_nlos_noalloc(mt_scene s, mt_film f, const mt_scan
     MT_TRY(noalloc_scratch(&base));
     int *tile_counter = reinterpret_cast<int *>(base);
     float *d_area = reinterpret_cast<float *>(base + 16);
-    uint32_t *cdf = reinterpret_cast<uint32_t *>(base + NA_HDR);
-    float4 *ys = reinterpret_cast<float4 *>(base + NA_HDR + NA_CDF);
-    int32_t *yt = reinterpret_cast<int32_t *>(base + NA_HDR + NA_CDF + NA_YS);
-    // hidden-surface table rebuilt into the static array on every call
-    k_setup_hidden<<<1, 1, 0, st>>>(reinterpret_cast<const float *>(s->dev.tris), s->dev.leaf_of,
-                                    (int)sc->hidden_first, (int)sc->hidden_count, cdf, d_area);
-    MT_CUDA_TRY(cudaGetLastError());
-    float h_area = 0.f;
-    MT_CUDA_TRY(cudaMemcpyAsync(&h_area, d_area, sizeof(float), cudaMemcpyDeviceToHost, st));
-    MT_CUDA_TRY(cudaStreamSynchronize(st));
-    int D;
-    LaunchCfg cfg = render_cfg(s, MT_LAUNCH_NLOS, (int)rows, f->T, 1, 0, D);
-    MT_CHECK_ARG(D >= 1, "film row too long");
-    NlosParams p{};
-    p.T = f->T;
-    p.D = D;
-    p.start = f->start;
-    p.width = f->width;
-    const bool acc = f->flags & MT_ACCUMULATE;
-    p.scale = acc ? 1.0f : 1.0f / (float)spp;
-    p.flags = f->flags;
-    p.spp = spp;
-    p.mode = (int32_t)sc->mode;
-    p.sample_offset = (uint32_t)sample_offset;
-    seed_key(seed, p.k0, p.k1);
-    p.lasers = sc->lasers;
-    p.sensors = sc->sensors;
-    p.n_l = sc->n_lasers;
-    p.n_s = sc->mode == MT_EXHAUSTIVE ? sc->n_sensors : 0;
-    p.nw = make_float3(sc->wall_normal[0], sc->wall_normal[1], sc->wall_normal[2]);
-    p.fw = sc->wall_albedo / MT_PI;
-    p.hidden_first = (int32_t)sc->hidden_first;
-    p.hidden_n = (int32_t)sc->hidden_count;
-    p.hcdf = cdf;
-    p.hidden_area = h_area;
-    p.tile = cfg.tile;
-    if (sc->mode == MT_EXHAUSTIVE) p.n_tiles = sc->n_lasers * ((sc->n_sensors + cfg.tile - 1) / cfg.tile);
-    else p.n_tiles = (int)((rows + cfg.tile - 1) / cfg.tile);
-    p.film = f->film;
-    p.steady = f->steady;
-    p.ysamp = ys;
-    p.ysamp_tri = yt;
-    p.tile_counter = tile_counter;
-    if (p.D < p.T && !acc) MT_CUDA_TRY(cudaMemsetAsync(p.film, 0, (size_t)rows * f->T * sizeof(float), st));
-    MT_CUDA_TRY(cudaMemsetAsync(tile_counter, 0, sizeof(int), st));
-    return mt_launch_nlos(s->dev, p, cfg, false, (f->flags & MT_COUNTERS) != 0, st);
+    size_t off = NA_HDR;
+    uint32_t *cdf = reinterpret_cast<uint32_t *>(base + off);
+    off += NA_CDF;
+    uint32_t *guide = reinterpret_cast<uint32_t *>(base + off);
+    off += NA_GUIDE;
+    double *prefix = reinterpret_cast<double *>(base + off);
+    off += NA_PREFIX;
+    float4 *ys = reinterpret_cast<float4 *>(base + off);
+    off += NA_YS;
+    int32_t *yt = reinterpret_cast<int32_t *>(base + off);
+    // the sampling table is rebuilt in the array on every call; the kernels read
+    // the hidden area from the array, so nothing is read back to the host
+    MT_TRY(hidden_table(s, (int)sc->hidden_first, (int)sc->hidden_count, cdf, guide, prefix, d_area, st));
+    NlosParams p;
+    LaunchCfg cfg;
+    nlos_fill(s, f, sc, spp, seed, sample_offset, cdf, guide, 0.f, d_area, ys, yt, tile_counter, p, cfg);
+    s->launches += 4;  // the table build
+    return nlos_enqueue(s, f, p, cfg, false, st);
 }

@@ -51,6 +51,7 @@ struct NlosParams {
     // nullptr = search the whole table
     const uint32_t *hguide;
     float hidden_area;
+    const float *hidden_area_dev;  // if set, the hidden area is read from here instead of hidden_area
     int32_t tile, n_tiles;
     float *film, *steady;
     float4 *ysamp;             // exhaustive: 2 per (laser, sample): (y, |x_l - y|), (side normal, partial weight or 0)
@@ -78,6 +79,8 @@ struct PoolField {
     __host__ __device__ __forceinline__ T &operator[](size_t slot) const { return base[slot * MT_WF_REC]; }
     __host__ __device__ __forceinline__ explicit operator bool() const { return base != nullptr; }
 };
+
+#define MT_WF_POOL_DEFAULT (1u << 22)  // paths in flight of the wavefront form unless set per scene
 
 #define MT_HGUIDE_N 4096  // guide-table buckets over the 24-bit keys of the hidden-triangle pick
 

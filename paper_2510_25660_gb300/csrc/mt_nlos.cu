@@ -73,7 +73,8 @@ __device__ __forceinline__ HiddenSample sample_hidden(const DevScene &s, const N
     if (trace_any<CNT>(s, ray, l1 - eps_of(h.y), tc)) return h;
     const float4 m = __ldg(&s.mats[tri]);
     const float fh = (m.x + m.y + m.z) * (1.0f / 3.0f) * (1.0f / MT_PI);
-    h.partial = p.fw * cl * fh * cy1 / (h.d1 * h.d1) * p.hidden_area;
+    const float area = p.hidden_area_dev ? __ldg(p.hidden_area_dev) : p.hidden_area;
+    h.partial = p.fw * cl * fh * cy1 / (h.d1 * h.d1) * area;
     return h;
 }
 

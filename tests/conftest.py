@@ -23,3 +23,17 @@ def oracle_mod():
 def scenes_mod():
     from paper_2510_25660_gb300 import scenes
     return scenes
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Divergent-path fractions of the per-contribution parity tests (GPU against
+    the oracle on the same random numbers), one line per comparison."""
+    mod = sys.modules.get("gpu_util")
+    rows = getattr(mod, "PARITY", None) if mod is not None else None
+    if not rows:
+        return
+    tr = terminalreporter
+    tr.write_line("per-contribution parity: test | matched | divergent (fraction) | off > 1e-4 | bin mismatches")
+    for test, nm, div, bad, bin_bad, worst in rows:
+        frac = div / max(nm, 1)
+        tr.write_line(f"  {test.split('::', 1)[-1]} | {nm} | {div} ({frac:.1e}) | {bad} | {bin_bad}")

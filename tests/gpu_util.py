@@ -1,5 +1,11 @@
 """Helpers for the GPU parity tests: load the CUDA path and compare it with the oracle."""
+import os
+
 import numpy as np
+
+# (test id, matched records, divergent records, values off by more than rel, bin mismatches)
+# of every per-contribution comparison in this session; printed at the end of the run
+PARITY = []
 
 
 def build_and_load():
@@ -42,7 +48,27 @@ def match_contribs(gpu, ora, rel=1e-4, start=None, width=None, edge=1e-5):
     x = (o["opl"] - start) / width
     away = np.abs(x - np.round(x)) * width > dopl + edge
     bin_bad = int(((g["bin"] != o["bin"]) & away).sum())
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    PARITY.append((test, len(common), div, bad_val, bin_bad, worst))
     return len(common), div, worst, bad_val, bin_bad, dopl
+
+
+def divergent_pixels(gpu, ora, rel=1e-4):
+    """Pixels with a contribution on one side only, a different triangle, or a
+    value off by more than rel: the pixels whose films may legitimately differ."""
+    def key(r):
+        return (r["pixel"].astype(np.int64) << 32) | (r["sample"].astype(np.int64) << 12) | \
+               (r["depth"].astype(np.int64) << 2) | r["kind"].astype(np.int64)
+
+    kg, ko = key(gpu), key(ora)
+    common, ig, io = np.intersect1d(kg, ko, return_indices=True)
+    only = np.setxor1d(kg, ko)
+    px = set((only >> 32).tolist())
+    g, o = gpu[ig], ora[io]
+    scale = np.maximum(np.abs(o["c"]).max(axis=1), 1e-30)
+    off = (g["tri"] != o["tri"]) | (np.abs(g["c"].astype(np.float64) - o["c"]).max(axis=1) / scale > rel)
+    px |= set(g["pixel"][off].tolist())
+    return px
 
 
 def rel_l2(a, b, mask=None):

@@ -98,6 +98,8 @@ def test_invalid_arguments_without_gpu(lib):
     assert L.mt_render_nlos(None, None, None, 1, 0, 0, None) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_sync(None, None) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_set_launch(None, 0, 0, 0, 0, -1, 0) == api.MT_ERR_INVALID_ARGUMENT
+    assert L.mt_set_wavefront_pool(None, 0) == api.MT_ERR_INVALID_ARGUMENT
+    assert L.mt_render_nlos_noalloc(None, None, None, 1, 0, 0, None) == api.MT_ERR_INVALID_ARGUMENT
     assert L.mt_probe_bins(None, 4, 0.0, 1.0, 4, None, None) == api.MT_ERR_INVALID_ARGUMENT
 
 

@@ -5,7 +5,7 @@ reporting MT_ERR_TIMEOUT instead of hanging."""
 import numpy as np
 import pytest
 
-from gpu_util import build_and_load, match_contribs, rel_l2
+from gpu_util import build_and_load, divergent_pixels, match_contribs, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -17,29 +17,61 @@ def media(oracle_mod, scenes_mod):
     return api, sc, api.Scene(sc), oracle_mod.OracleScene(sc)
 
 
+@pytest.fixture(scope="module")
+def media128(oracle_mod, scenes_mod):
+    """The medium of the volumetric workload: a 128^3 fBm density grid."""
+    api = build_and_load()
+    sc = scenes_mod.media_scene(res=128)
+    return api, sc, api.Scene(sc), oracle_mod.OracleScene(sc)
+
+
 @pytest.mark.parametrize("form", ["megakernel", "wavefront"])
-def test_media_contributions_and_film(media, form):
-    api, sc, s, osc = media
+def test_media_contributions_and_film(media128, scenes_mod, form):
+    """Per contribution (value, time bin) and per time bin of the film, on the
+    128^3 grid with the volumetric workload's window (T = 1024 bins of 5 mm
+    from 3.5 m) and depth 16 (Sec. 4.1 volumetric scattering; time of flight
+    through the medium, Sec. 3 Eq. 3)."""
+    api, sc, s, osc = media128
+    fm = scenes_mod.MEDIA_FILM
     H = W = 64
-    T, start, width = 1024, 3.5, 0.005
-    spp, seed, depth = 4, 25660, 8
+    T, start, width = fm.T, fm.start_opl, fm.bin_width
+    spp, seed, depth = 32, 25660, 16
     if form == "wavefront":
         s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, -1, api.MT_OPT_WAVEFRONT)
     try:
-        film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=3_000_000)
+        film, steady, rec, n = api.render_dump(s, H, W, T, start, width, spp, seed, depth, cap=8_000_000)
+        f2, s2 = api.render(s, H, W, T, start, width, spp, seed, depth)
+        s.sync()
     finally:
         s.set_launch(api.MT_LAUNCH_RENDER)
-    crop = (24, 40, 24, 40)
-    ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=3_000_000)
+    assert n <= 8_000_000
+    crop = (16, 48, 16, 48)
+    ref = osc.render(H, W, T, start, width, spp, seed, depth, crop=crop, dump_cap=8_000_000)
     px = rec["pixel"] % W
     py = rec["pixel"] // W
     sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
     nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"], start=start, width=width)
-    assert nm > 2000
-    assert div <= 5e-3 * nm, (div, nm)
-    assert bad <= 5e-3 * nm, (bad, worst)
-    f = film.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
-    assert rel_l2(f.sum(2), ref["film"].sum(2)) < 0.01
+    assert nm > 20000
+    assert bin_bad == 0, bin_bad
+    assert div <= 5e-3 * nm and bad <= 5e-3 * nm, \
+        f"divergent {div}/{nm} = {div / nm:.1e}, off {bad} (worst {worst:.1e})"
+    for fg, sg in ((film, steady), (f2, s2)):  # dump form and the timed form
+        g = fg.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+        gs = sg.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+        # per bin, on pixels whose paths all agree with the oracle's
+        keep = np.ones(g.shape[:2], bool)
+        for p in divergent_pixels(rec[sel], ref["dump"]):
+            keep[p // W - crop[2], p % W - crop[0]] = False
+        assert keep.mean() > 0.8
+        assert rel_l2(g[keep], ref["film"][keep]) < 1e-3
+        assert rel_l2(gs[keep], ref["steady"][keep]) < 1e-3
+        # per bin of the crop's transient (summed over its pixels) where a bin holds >= 100 samples
+        d = ref["dump"]
+        inb = (d["bin"] >= 0) & (d["bin"] < T)
+        cnt = np.bincount(d["bin"][inb], minlength=T)
+        m = cnt >= 100
+        assert m.sum() > 200
+        assert rel_l2(g.sum((0, 1))[m], ref["film"].sum((0, 1))[m]) < 0.01
 
 
 def test_media_wavefront_equals_megakernel(media):

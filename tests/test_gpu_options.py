@@ -1,0 +1,104 @@
+"""Film-accumulator options and the launch autotuner, against the oracle.
+
+* Warp-aggregated atomics (MT_OPT_AGGREGATE): lanes of a warp that add to the
+  same film bin combine their values first (persistent render; NLOS capture).
+* Partial privatisation: the first D of T bins of each pixel in shared memory,
+  bins >= D added to the film in global memory (0 < D < T).
+* The autotuner: a search over launch configurations, including the wavefront
+  form at several paths per thread, picks one that runs and renders the same
+  film (path reuse into time bins, Sec. 3; the batched NLOS grid, Sec. 4.5).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import build_and_load, divergent_pixels, match_contribs, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+H = W = 64
+T, START, WIDTH = 256, 3.5, 0.01
+
+
+@pytest.fixture(scope="module")
+def cornell(oracle_mod, scenes_mod):
+    api = build_and_load()
+    sc = scenes_mod.cornell_box()
+    return api, sc, api.Scene(sc), oracle_mod.OracleScene(sc)
+
+
+@pytest.mark.parametrize("case", ["aggregate", "priv64", "priv64_aggregate", "priv0"])
+def test_film_accumulator_options_match_oracle(cornell, case):
+    api, sc, s, osc = cornell
+    spp, seed, depth = 16, 25660, 4
+    opts = api.MT_OPT_AGGREGATE if "aggregate" in case else 0
+    priv = {"aggregate": -1, "priv64": 64, "priv64_aggregate": 64, "priv0": 0}[case]
+    ref_f, ref_s = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)  # all bins privatised (D = T)
+    s.set_launch(api.MT_LAUNCH_RENDER, 256, 0, 0, priv, opts)
+    try:
+        film, steady, rec, n = api.render_dump(s, H, W, T, START, WIDTH, spp, seed, depth, cap=4_000_000)
+        f2, s2 = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_RENDER)
+    crop = (16, 48, 16, 48)
+    ref = osc.render(H, W, T, START, WIDTH, spp, seed, depth, crop=crop, dump_cap=4_000_000)
+    px, py = rec["pixel"] % W, rec["pixel"] // W
+    sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
+    nm, div, worst, bad, bin_bad, _ = match_contribs(rec[sel], ref["dump"], start=START, width=WIDTH)
+    assert nm > 20000 and bin_bad == 0 and div <= 1e-3 * nm and bad <= 1e-3 * nm, (nm, div, bad, bin_bad)
+    for fg, sg in ((film, steady), (f2, s2)):
+        g = fg.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+        keep = np.ones(g.shape[:2], bool)
+        for p in divergent_pixels(rec[sel], ref["dump"]):
+            keep[p // W - crop[2], p % W - crop[0]] = False
+        assert keep.mean() > 0.95
+        assert rel_l2(g[keep], ref["film"][keep]) < 1e-4
+        gs = sg.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
+        assert rel_l2(gs[keep], ref["steady"][keep]) < 1e-4
+    # the same film as the fully privatised default, up to the order of additions
+    assert rel_l2(f2.cpu().numpy(), ref_f.cpu().numpy()) < 1e-5
+    assert rel_l2(s2.cpu().numpy(), ref_s.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("case", ["aggregate_global", "aggregate_shared"])
+def test_nlos_aggregate_matches_oracle(oracle_mod, scenes_mod, case):
+    import torch
+    api = build_and_load()
+    sc = scenes_mod.nlos_scene()
+    s = api.Scene(sc)
+    Tn, start, width = 4096, 0.0, 0.003
+    pts = scenes_mod.wall_grid(8, 8)
+    lasers = torch.from_numpy(pts).cuda()
+    s.set_launch(api.MT_LAUNCH_NLOS, 256, 0, 0, 0 if case == "aggregate_global" else -1, api.MT_OPT_AGGREGATE)
+    f, st = api.render_nlos(s, lasers, None, api.MT_CONFOCAL, Tn, start, width, 128, 25660)
+    s.sync()
+    ref = oracle_mod.OracleScene(sc).render_nlos(pts, None, False, Tn, start, width, 128, 25660)
+    assert rel_l2(f.cpu().numpy(), ref["film"]) < 0.01
+    assert rel_l2(st.cpu().numpy(), ref["steady"]) < 1e-3
+
+
+def test_autotune_picks_a_configuration_that_renders_the_same_film(cornell, tmp_path, monkeypatch):
+    import torch
+    api, sc, s, osc = cornell
+    from paper_2510_25660_gb300 import autotune, scenes
+    monkeypatch.setenv("MT_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    spp, seed, depth = 8, 3, 4
+    film0, steady0 = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)
+    out = api.new_film(H, W, T)
+    run = lambda: api.render(s, H, W, T, START, WIDTH, spp, seed, depth, out=out)
+    cands = [c for c in autotune.candidates("render", T) if c[1] == 1 and c[4] in (0, 4)]
+    assert any(c[5] for c in cands)  # paths per thread of the wavefront form are searched
+    best = autotune.tune(s, "render", sc, scenes.CORNELL_FILM, spp, depth, run, cands, reps=1, budget_s=60)
+    assert "ms" in best and best["ms"] > 0
+    # the cache holds every timed candidate and the choice is applied again from it
+    s.set_launch(api.MT_LAUNCH_RENDER)
+    s.set_wavefront_pool(0)
+    cfg = autotune.apply(s, "render", sc, scenes.CORNELL_FILM, spp, depth)
+    assert cfg is not None and cfg["options"] == best["options"] and len(cfg["results"]) >= 5
+    film, steady = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)
+    s.sync()
+    assert rel_l2(film.cpu().numpy(), film0.cpu().numpy()) < 1e-5
+    assert rel_l2(steady.cpu().numpy(), steady0.cpu().numpy()) < 1e-5
+    s.set_launch(api.MT_LAUNCH_RENDER)
+    s.set_wavefront_pool(0)
+    torch.cuda.synchronize()

@@ -25,13 +25,19 @@ def _film(api, rows, T):
     return film, steady, h
 
 
+@pytest.mark.parametrize("launch", ["default", "global_aggregated"])
 @pytest.mark.parametrize("mode", ["exhaustive", "confocal"])
-def test_noalloc_matches_allocating_entry_point(mode):
+def test_noalloc_matches_allocating_entry_point(mode, launch):
+    """Also under a launch configuration that keeps no time bin in shared
+    memory and combines equal-bin atomics across a warp: both entry points
+    take the same configuration and the same kernel path."""
     import torch
     api = build_and_load()
     from paper_2510_25660_gb300 import scenes
     sc = scenes.nlos_scene()
     s = api.Scene(sc)
+    if launch == "global_aggregated":
+        s.set_launch(api.MT_LAUNCH_NLOS, 256, 0, 0, 0, api.MT_OPT_AGGREGATE)
     T, spp, seed = 4096, 256, 25660
     lasers = torch.from_numpy(scenes.wall_grid(4, 4)).cuda()
     if mode == "exhaustive":
