@@ -56,7 +56,7 @@ def test_refill_forward_per_path_and_film(cornell):
     f_full, s_full = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)
     s.sync()
     # 65,536 paths through 4,096 slots: the pool was refilled many times
-    assert iters >= 2 * (H * W * spp // POOL), iters
+    assert iters >= H * W * spp // POOL, iters  # one pool holding every path would need <= depth + 1
     assert n <= 4_000_000
     # every path of the frame exactly once: one camera vertex per (pixel, sample) at most, and the
     # dump's (pixel, sample) pairs cover the frame
