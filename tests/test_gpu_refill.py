@@ -47,7 +47,9 @@ def test_refill_forward_per_path_and_film(cornell):
     _pool(s, POOL)
     try:
         s.stage_times(reset=True)
+        s.read_counters(reset=True)
         film, steady, rec, n = api.render_dump(s, H, W, T, START, WIDTH, spp, seed, depth, cap=4_000_000)
+        paths = s.read_counters(reset=True)["paths"]
         f2, s2 = api.render(s, H, W, T, START, WIDTH, spp, seed, depth)
         s.sync()
         iters = s.stage_times(reset=True)["iterations"]
@@ -58,8 +60,8 @@ def test_refill_forward_per_path_and_film(cornell):
     # 65,536 paths through 4,096 slots: the pool was refilled many times
     assert iters >= H * W * spp // POOL, iters  # one pool holding every path would need <= depth + 1
     assert n <= 4_000_000
-    # every path of the frame exactly once: one camera vertex per (pixel, sample) at most, and the
-    # dump's (pixel, sample) pairs cover the frame
+    # every path of the frame started exactly once, each with a (pixel, sample) of this frame
+    assert paths == H * W * spp, paths
     ps = rec["pixel"].astype(np.int64) * spp + rec["sample"]
     assert ps.min() >= 0 and ps.max() < H * W * spp
     crop = (16, 48, 16, 48)
