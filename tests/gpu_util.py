@@ -54,8 +54,10 @@ def match_contribs(gpu, ora, rel=1e-4, start=None, width=None, edge=1e-5):
 
 
 def divergent_pixels(gpu, ora, rel=1e-4):
-    """Pixels with a contribution on one side only, a different triangle, or a
-    value off by more than rel: the pixels whose films may legitimately differ."""
+    """Pixels with a contribution on one side only, a different triangle, a
+    value off by more than rel, or a different time bin (allowed only within
+    FP32 rounding of a bin edge, which match_contribs checks): the pixels whose
+    films may legitimately differ by more than rounding."""
     def key(r):
         return (r["pixel"].astype(np.int64) << 32) | (r["sample"].astype(np.int64) << 12) | \
                (r["depth"].astype(np.int64) << 2) | r["kind"].astype(np.int64)
@@ -66,7 +68,8 @@ def divergent_pixels(gpu, ora, rel=1e-4):
     px = set((only >> 32).tolist())
     g, o = gpu[ig], ora[io]
     scale = np.maximum(np.abs(o["c"]).max(axis=1), 1e-30)
-    off = (g["tri"] != o["tri"]) | (np.abs(g["c"].astype(np.float64) - o["c"]).max(axis=1) / scale > rel)
+    off = (g["tri"] != o["tri"]) | (g["bin"] != o["bin"]) | \
+        (np.abs(g["c"].astype(np.float64) - o["c"]).max(axis=1) / scale > rel)
     px |= set(g["pixel"][off].tolist())
     return px
 

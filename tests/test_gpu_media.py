@@ -60,9 +60,9 @@ def test_media_contributions_and_film(media128, scenes_mod, form):
         gs = sg.cpu().numpy()[crop[2]:crop[3], crop[0]:crop[1]]
         # per bin, on pixels whose paths all agree with the oracle's
         keep = np.ones(g.shape[:2], bool)
-        for p in divergent_pixels(rec[sel], ref["dump"]):
+        for p in divergent_pixels(rec[sel], ref["dump"], rel=1e-3):
             keep[p // W - crop[2], p % W - crop[0]] = False
-        assert keep.mean() > 0.8
+        assert keep.mean() > 0.8, keep.mean()
         assert rel_l2(g[keep], ref["film"][keep]) < 1e-3
         assert rel_l2(gs[keep], ref["steady"][keep]) < 1e-3
         # per bin of the crop's transient (summed over its pixels) where a bin holds >= 100 samples
