@@ -107,17 +107,14 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile(kernel_hash, name):
-    """DRAM bytes per render of the dominant kernel(s) from the committed ncu
-    summary profiles/<name>.json, or None if the kernel sources changed since it
-    was captured."""
+def _profile(kernel_hash, name):
+    """The committed ncu summary profiles/<name>.json, or None if the kernel
+    sources changed since it was captured."""
     p = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(p):
-        return None, None
+        return None
     d = json.load(open(p))
-    if d.get("kernel_hash") != kernel_hash:
-        return None, d.get("kernel_hash")
-    return d.get("dram_bytes_per_render"), d.get("kernel_hash")
+    return d if d.get("kernel_hash") == kernel_hash else None
 
 
 def _peaks():
@@ -254,12 +251,17 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile", default="", help="small: a few launches of each kernel on reduced sizes (for ncu)")
+    ap.add_argument("--profile", default="", help="small | trace: launches of the hot kernels on reduced sizes (for ncu)")
+    ap.add_argument("--profile-summary", nargs=2, metavar=("CSV", "LOG"),
+                    help="write profiles/k_wf_trace_large_scene.json from the ncu CSV and log of --profile trace")
     ap.add_argument("--compare", action="store_true",
                     help="batched NLOS vs per-scan-point launches; adjoint vs finite differences")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_summary:
+        return profile_summary(args.profile_summary[0], args.profile_summary[1],
+                               os.path.join(ROOT, "profiles", "k_wf_trace_large_scene.json"))
     if args.profile:
         return profile_case(args.profile)
     if args.compare:
@@ -337,48 +339,65 @@ def main():
     total_s, total_vertices = aggregate_ranks(sum(step_ms) / 1000.0, float(run_cnt["vertices"]), ws, "cuda")
     value = total_vertices / total_s
     mean_ms = 1000.0 * total_s / args.steps
-    peak, peak_kind = _peaks()
+    hbm_peak, hbm_kind = _peaks()
     render_achieved = alg_bytes / (mean_ms / 1000.0) / 1e9
     khash = _kernel_hash()
-    traffic, _ = _traffic_from_profile(khash, "k_wf_traversal_large_scene" if wavefront else "k_render_large_scene")
+    # measured rates of the traversal pass's own access patterns on this GPU (the roofline's denominators)
+    l2_gbs = api.microbench(api.MT_MICRO_GATHER32, 64 << 20, 256)
+    red_gops = api.microbench(api.MT_MICRO_RED_GLOBAL, 1 << 30, 64)
+    red_shared_gops = api.microbench(api.MT_MICRO_RED_SHARED, 1 << 20, 1024)
+    prof = _profile(khash, "k_wf_trace_large_scene") if wavefront else None
     if wavefront:
         # dominant kernel: the BVH traversal pass k_wf_trace (extension rays, then the shadow rays
         # of the previous shading pass; the last shading pass's shadow rays in k_wf_shadow),
-        # timed by its own events
+        # timed by its own events on the render stream
         trav_ms = (stages["extend_ms"] + stages["shadow_ms"]) / args.steps
         achieved = trav_bytes / (trav_ms / 1000.0) / 1e9
         kernel_name = ("k_wf_trace (+ k_wf_shadow for the last pass): BVH traversal of extension and "
-                       "shadow rays")
-        kernel_bytes = trav_bytes
+                       "shadow rays, with the film splats of unoccluded shadow rays")
         per_unit = "per ray: BVH node bytes fetched (32 B per node) + 48 B per triangle tested"
         stage_ms = {k: v / args.steps for k, v in stages.items() if k.endswith("_ms")}
         stage_ms["share_of_step"] = {k: v / mean_ms for k, v in stage_ms.items()}
+        # DRAM bytes per render: the ncu capture of every k_wf_trace launch of one 256x256-px render
+        # of the same scene, scaled by rays to this render (null once the kernels changed)
+        traffic = None
+        if prof:
+            traffic = prof["dram_bytes_per_ray"] * cnt["rays"]
+        n_atom = cnt["gmem_splats"] * 3  # three colour channels per splat
+        terms = {"l2_gather_ms": trav_bytes / (l2_gbs * 1e9) * 1e3,
+                 "atomic_ms": n_atom / (red_gops * 1e9) * 1e3,
+                 "hbm_ms": (traffic if traffic is not None else film_bytes) / (hbm_peak * 1e9) * 1e3}
+        binding = max(terms, key=terms.get)
+        t_star = terms[binding]
+        roofline = {
+            "bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+            "traffic": traffic,
+            "peak_kind": "measured in this run: mt_microbench random 32-B loads from a 64 MB (L2-resident) "
+                         "buffer on this GPU",
+            "kernel": kernel_name, "algorithmic_bytes_per_launch": trav_bytes,
+            "launch": "one render's traversal pass (all its k_wf_trace launches); bytes and time per render",
+            "per_unit": per_unit, "units_per_launch": cnt["rays"],
+            "time_ms_per_launch": trav_ms,
+            "terms_ms": terms, "binding_term": binding, "t_star_ms": t_star, "t_star_frac": t_star / trav_ms,
+            "terms_note": "T* = max(B_L2 / measured L2 gather rate, N_atomic / measured red.global rate, "
+                          "B_DRAM / measured HBM copy rate); N_atomic counts every film and steady-image "
+                          "splat of the render (3 atomics each, an upper bound for this pass); B_DRAM from "
+                          "the ncu capture (film bytes when it is stale)",
+            "hbm": {"dram_bytes_per_launch": traffic,
+                    "achieved": traffic / (trav_ms / 1000.0) / 1e9 if traffic is not None else None,
+                    "peak": hbm_peak, "peak_kind": hbm_kind + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind ==
+                    "measured" else hbm_kind, "unit": "GB/s",
+                    "frac": traffic / (trav_ms / 1000.0) / 1e9 / hbm_peak if traffic is not None else None},
+            "alu_issue": prof.get("issue") if prof else None,
+            "rates": {"l2_gather32_gbs": l2_gbs, "red_global_gops": red_gops, "red_shared_gops": red_shared_gops},
+            "stage_ms_per_step": stage_ms,
+            "whole_render": {"algorithmic_bytes": alg_bytes, "achieved_gbs": render_achieved},
+            "counts": cnt, "kernel_hash": khash,
+        }
     else:
-        achieved = render_achieved
-        kernel_name = "k_render (forward megakernel)"
-        kernel_bytes = alg_bytes
-        per_unit = ("node bytes fetched + triangle tests x 48 B + 32 B material/emitter per vertex "
-                    "+ film and steady image written once")
-        stage_ms = None
-    # measured rates of the render kernel's own access patterns on this GPU
-    aux = {}
-    try:
-        l2 = api.microbench(api.MT_MICRO_GATHER32, 64 << 20, 256)
-        aux = {"l2_gather32_gbs": l2, "frac_of_l2_gather": achieved / l2,
-               "red_global_gops": api.microbench(api.MT_MICRO_RED_GLOBAL, 1 << 30, 64),
-               "red_shared_gops": api.microbench(api.MT_MICRO_RED_SHARED, 1 << 20, 1024),
-               "note": "random 32-B loads from a 64 MB (L2-resident) buffer; red.add.f32 into 1 GB; "
-                       "shared-memory atomics into 48 KB per CTA"}
-    except Exception as e:  # reported, not fatal
-        aux = {"error": str(e)[:200]}
-    if wavefront:
-        # what bounds the pass: issue slots and lane utilisation from the committed ncu capture of the
-        # same kernel sources (the traversal is issue-bound, not DRAM-bound)
-        prof = os.path.join(ROOT, "profiles", "k_wf_traversal_large_scene.json")
-        if os.path.exists(prof):
-            pd = json.load(open(prof))
-            if pd.get("kernel_hash") == khash and "issue" in pd:
-                aux["issue_ncu"] = pd["issue"]
+        roofline = {"bound": "l2", "achieved": render_achieved, "peak": l2_gbs, "unit": "GB/s",
+                    "frac": render_achieved / l2_gbs, "traffic": None, "kernel": "k_render (forward megakernel)",
+                    "algorithmic_bytes_per_launch": alg_bytes, "counts": cnt, "kernel_hash": khash}
 
     # e2e: host arrays in, film out, through the public API (scene load + render + read-back)
     e2e = None
@@ -425,6 +444,7 @@ def main():
     extras = {}
     if not args.no_extras and (rank == 0 or ws == 1):
         extras = secondary(api, autotune, scenes)
+        extras["comparisons"] = comparisons(api, autotune, scenes)
 
     line = {
         "metric": METRIC,
@@ -435,13 +455,7 @@ def main():
                    "l2": f"{L2_FLUSH_BYTES >> 20} MB buffer written between timed steps; film output "
                          f"{film_bytes / 1e9:.2f} GB per step",
                    "bvh": s.stats()},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
-                     "algorithmic_bytes_per_launch": kernel_bytes, "per_unit": per_unit,
-                     "stage_ms_per_step": stage_ms,
-                     "whole_render": {"algorithmic_bytes": alg_bytes, "achieved_gbs": render_achieved,
-                                      "frac": render_achieved / peak},
-                     "counts": cnt, "kernel_hash": khash, "aux": aux},
+        "roofline": roofline,
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": e2e,
@@ -457,14 +471,15 @@ def main():
 
 
 def profile_case(which):
-    """Launches of the hot kernels for ncu captures.  small: the large scene
-    (full geometry) at 256x256 px, 256 spp (16.7M paths: four fills of the
-    path pool, so mid-render passes run with a full pool; 1.6 GB film) with the
-    launch configuration of the
-    benchmark, the differentiable scene's backward at 64x64, a 16x16 confocal
-    NLOS grid.  traversal: one full-size render of the benchmark (512x512 px,
-    256 spp) with the benchmark's launch configuration, for single-pass
-    counters of every traversal launch of one render."""
+    """Launches of the hot kernels for ncu captures (small cases only).
+    small: the large scene (full geometry) at 256x256 px, 256 spp (16.7M paths:
+    four fills of the path pool, so mid-render passes run with a full pool;
+    1.6 GB film) with the launch configuration of the benchmark, three times;
+    the differentiable scene's backward at 64x64; a 16x16 confocal NLOS grid.
+    trace: one 256x256-px, 256-spp render of the large scene in the
+    benchmark's configuration (every k_wf_trace launch of it, for one-pass DRAM
+    counters), then the same render with MT_COUNTERS, whose ray count it
+    prints for scaling the bytes to other renders."""
     import torch
     from paper_2510_25660_gb300 import api, scenes
     from paper_2510_25660_gb300 import build as b
@@ -475,13 +490,17 @@ def profile_case(which):
     f = scenes.LARGE_FILM
     s = api.Scene(sc)
     autotune.apply(s, "render", sc, f, 256, 8)
-    if which == "traversal":
-        film, steady = api.new_film(f.H, f.W, f.T)
-        api.render(s, f.H, f.W, f.T, f.start_opl, f.bin_width, 256, scenes.RENDER_SEED, 8, out=(film, steady))
-        s.sync()
-        print("profile case done")
-        return
     film, steady = api.new_film(256, 256, f.T)
+    if which == "trace":
+        api.render(s, 256, 256, f.T, f.start_opl, f.bin_width, 256, scenes.RENDER_SEED, 8, out=(film, steady))
+        s.sync()
+        s.read_counters(reset=True)
+        api.render(s, 256, 256, f.T, f.start_opl, f.bin_width, 256, scenes.RENDER_SEED, 8, flags=api.MT_COUNTERS,
+                   out=(film, steady))
+        c = s.read_counters(reset=True)
+        print(json.dumps({"profile_case": "trace", "rays": c["rays"], "paths": c["paths"],
+                          "node_bytes": c["node_bytes"], "tri_tests": c["tri_tests"]}), flush=True)
+        return
     for _ in range(3):
         api.render(s, 256, 256, f.T, f.start_opl, f.bin_width, 256, 1, 8, out=(film, steady))
     s.sync()
@@ -503,61 +522,122 @@ def profile_case(which):
     print("profile case done")
 
 
-def compare():
-    """(1) All 4096 confocal scan points in one graph launch against one launch
-    per scan point, at equal spp (equal film error: same estimator, same spp).
-    (2) Path-replay gradients of 32 albedo parameters against central finite
-    differences of forward renders (two launches per parameter), with the error
-    of each against the exact oracle-checked gradient on the same samples."""
+def profile_summary(csv_path, log_path, out_path):
+    """profiles/k_wf_trace_large_scene.json from the ncu CSV of the `trace`
+    profile case (dram__bytes_read.sum, dram__bytes_write.sum and
+    gpu__time_duration.sum of every k_wf_trace launch) and that run's log (ray
+    count of the render).  Only the launches of the timed form (no counters)
+    are summed."""
+    import csv
+    rows = [r for r in csv.reader(l for l in open(csv_path) if not l.startswith("=="))]
+    head = rows[0]
+    ki, mi, vi = head.index("Kernel Name"), head.index("Metric Name"), head.index("Metric Value")
+    idi = head.index("ID")
+    launches = {}
+    for r in rows[1:]:
+        if len(r) <= vi or "k_wf_trace<" not in r[ki]:
+            continue
+        targs = r[ki].split("k_wf_trace<", 1)[1].split(">", 1)[0].replace(" ", "")
+        if targs.split(",")[1] not in ("0", "false"):  # CNT = true: the counting render
+            continue
+        v = float(r[vi].replace(",", ""))
+        unit = r[head.index("Metric Unit")] if "Metric Unit" in head else ""
+        if r[mi].startswith("dram__bytes"):
+            v *= {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1)
+        elif r[mi] == "gpu__time_duration.sum":
+            v *= {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0}.get(unit, 1e-6)
+        launches.setdefault(r[idi], {})[r[mi]] = v
+    info = None
+    for l in open(log_path):
+        if l.startswith("{") and "profile_case" in l:
+            info = json.loads(l)
+    rd = sum(x.get("dram__bytes_read.sum", 0) for x in launches.values())
+    wr = sum(x.get("dram__bytes_write.sum", 0) for x in launches.values())
+    ms = sum(x.get("gpu__time_duration.sum", 0) for x in launches.values())
+    d = {"kernel": "k_wf_trace (timed form)", "kernel_hash": _kernel_hash(),
+         "workload": "one render of the 1,164,296-triangle scene, 256x256 px, 256 spp, max_depth 8, T = 2048, "
+                     "benchmark launch configuration (16.7 M paths, 4 fills of the path pool)",
+         "command": "python bench.py --profile trace > gpurun_out/trace.log && ncu --metrics "
+                    "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
+                    "-k regex:k_wf_trace --csv --log-file gpurun_out/trace_dram.csv python bench.py --profile trace",
+         "launches": len(launches), "rays": info["rays"], "dram_bytes_read": rd, "dram_bytes_write": wr,
+         "gpu_time_ms_serialised": ms, "dram_bytes_per_ray": (rd + wr) / info["rays"]}
+    old = json.load(open(out_path)) if os.path.exists(out_path) else {}
+    if "issue" in old:
+        d["issue"] = old["issue"]
+    json.dump(d, open(out_path, "w"), indent=1)
+    print(json.dumps(d))
+
+
+def comparisons(api, autotune, scenes, per_point=256):
+    """The two comparisons the method's own claims set up, at equal sample
+    counts.  (1) Batched NLOS (Sec. 4.5): all 4096 confocal scan points of the
+    64x64 grid in one graph launch against one launch per scan point, timed
+    over `per_point` points and scaled to 4096, with the film error of each
+    against a 16x-spp reference over those points.  (2) Adjoint (Sec. 4.4):
+    one path-replay backward pass (every albedo's gradient) against central
+    differences of forward renders for 32 parameters (two renders each), with
+    the relative difference of the two gradients."""
     import numpy as np
     import torch
-    from paper_2510_25660_gb300 import api, autotune, scenes
-    from paper_2510_25660_gb300 import build as b
-    b.build()
-    api.load()
     out = {}
     sc = scenes.nlos_scene()
     s = api.Scene(sc)
-    autotune.apply(s, "nlos", sc, None, 1024, 0)
+    cfg = autotune.apply(s, "nlos", sc, None, 1024, 0) or {}
     pts = torch.from_numpy(scenes.wall_grid(64, 64)).cuda()
     T, W0, spp = scenes.NLOS_T, scenes.NLOS_W, 1024
     film = torch.empty((4096, T), device="cuda")
     steady = torch.empty(4096, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(2):
         api.render_nlos(s, pts, None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=(film, steady))
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     api.render_nlos(s, pts, None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=(film, steady))
     e1.record()
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1)
-    # one plain launch per scan point through the same API (row views of the same film)
-    cfg = autotune.apply(s, "nlos", sc, None, 1024, 0) or {}
+    # reference for the error: the same points at 16x the samples (another seed)
+    sub = pts[:per_point].contiguous()
+    ref, ref_s = api.render_nlos(s, sub, None, api.MT_CONFOCAL, T, 0.0, W0, 16 * spp, 99)
+    # one plain launch per scan point through the same API, same kernel and launch configuration
     s.set_launch(api.MT_LAUNCH_NLOS, cfg.get("threads", 0), cfg.get("tile", 0), 0, cfg.get("priv", -1),
                  cfg.get("options", 0) | api.MT_OPT_NO_GRAPH)
-    rows = [(film[i:i + 1], steady[i:i + 1]) for i in range(4096)]
-    pt_rows = [pts[i:i + 1].contiguous() for i in range(4096)]
-    for i in range(64):
+    pf = torch.empty((per_point, T), device="cuda")
+    ps = torch.empty(per_point, device="cuda")
+    rows = [(pf[i:i + 1], ps[i:i + 1]) for i in range(per_point)]
+    pt_rows = [pts[i:i + 1].contiguous() for i in range(per_point)]
+    for i in range(min(32, per_point)):
         api.render_nlos(s, pt_rows[i], None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=rows[i])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e0.record()
-    for i in range(4096):
+    for i in range(per_point):
         api.render_nlos(s, pt_rows[i], None, api.MT_CONFOCAL, T, 0.0, W0, spp, 1, out=rows[i])
     e1.record()
     torch.cuda.synchronize()
     loop_wall_ms = 1000 * (time.perf_counter() - t0)
+    loop_ms = e0.elapsed_time(e1)
+
+    def err(a, b):
+        return float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+
     out["nlos_batched_vs_per_point"] = {
-        "workload": "64x64 confocal scan, 1024 spp, T=4096, 49.4k hidden triangles; per point: one direct "
-                    "launch per scan point, same kernel and launch configuration",
-        "batched_ms": batched_ms, "per_point_loop_gpu_ms": e0.elapsed_time(e1), "per_point_loop_wall_ms": loop_wall_ms,
-        "speedup": e0.elapsed_time(e1) / batched_ms}
-    del s
+        "workload": "64x64 confocal scan, 1024 spp, T=4096 x 3 mm, 49.4k hidden triangles; per point: one "
+                    f"direct launch per scan point (timed over the first {per_point} points, scaled to 4096), "
+                    "same kernel and launch configuration",
+        "batched_ms_4096_points": batched_ms, "per_point_loop_ms_4096_points": loop_ms * 4096 / per_point,
+        "per_point_loop_wall_ms_4096_points": loop_wall_ms * 4096 / per_point,
+        "speedup": loop_ms * 4096 / per_point / batched_ms,
+        "film_rel_err_batched": err(film[:per_point], ref), "film_rel_err_per_point": err(pf, ref),
+        "error_reference": f"the first {per_point} points at 16384 spp (another seed)"}
+    del s, film, steady, ref, pf, ps
     # adjoint vs finite differences on the differentiable scene, 32 parameters
     sc = scenes.diff_scene()
     f = scenes.DIFF_FILM
     s = api.Scene(sc)
+    autotune.apply(s, "backward", sc, f, 64, 8)
+    autotune.apply(s, "render", sc, f, 64, 8)
     spp, depth = 64, 8
     alb0 = torch.from_numpy(sc.albedo).cuda()
     s.set_params(albedo=torch.from_numpy(scenes.perturbed_albedo(sc)).cuda())
@@ -589,7 +669,6 @@ def compare():
     pick = rng.choice(cand, 32, replace=False)
     h = 1e-3
     fd = []
-    t0 = time.perf_counter()
     e0.record()
     for k in pick:
         t, c = divmod(int(k), 3)
@@ -608,13 +687,23 @@ def compare():
     fd = np.array(fd)
     rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-30)
     out["adjoint_vs_finite_differences"] = {
-        "workload": "97k-triangle scene, 256x256x512 film, 64 spp, depth 8, L2 loss vs a target with albedos x U[0.8,1.2]",
+        "workload": "97k-triangle scene, 256x256x512 film, 64 spp, depth 8, L2 loss vs a target with albedos "
+                    "x U[0.8,1.2]; finite differences: step 1e-3, common random numbers, 32 parameters",
         "adjoint_ms_all_params": adj_ms, "n_params_adjoint": int(sc.n_tris * 3),
         "fd_ms_32_params": fd_ms, "fd_launches": 64, "loss": L0,
         "adjoint_vs_fd_rel_err_median": float(np.median(rel)), "adjoint_vs_fd_rel_err_max": float(rel.max()),
         "speedup_per_param": (fd_ms / 32) / (adj_ms / (sc.n_tris * 3)),
         "speedup_for_32_params": fd_ms / adj_ms}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def compare():
+    """The comparisons of the default run with the per-point loop over all 4096 points."""
+    from paper_2510_25660_gb300 import api, autotune, scenes
+    from paper_2510_25660_gb300 import build as b
+    b.build()
+    api.load()
+    print(json.dumps(comparisons(api, autotune, scenes, per_point=4096)), flush=True)
 
 
 def _timed(fn, reps):

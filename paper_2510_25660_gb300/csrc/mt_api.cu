@@ -944,6 +944,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.dump = rp.dump;
     w.dump_cap = rp.dump_cap;
     w.dump_count = rp.dump_count;
+    w.splat_count = (f->flags & MT_COUNTERS) ? s->counters + 7 : nullptr;
     // the refill field of the options word doubles as the fetch threshold
     const int fetch_k = (int)((cfg.options >> 8) & 0xFFu);
     w.dynamic_fetch = (cfg.options & MT_OPT_DYNAMIC_FETCH) ? (fetch_k ? std::min(fetch_k, 32) : 8) : 0;

@@ -107,6 +107,7 @@ struct WfParams {
     mt_contrib *dump;
     long long dump_cap;
     unsigned long long *dump_count;
+    unsigned long long *splat_count;  // MT_COUNTERS: film and steady-image splats (each C atomics), else null
     int32_t dynamic_fetch;         // 0: off; else idle lanes of a warp that trigger a fetch (1..32)
     int32_t wide;                  // traverse the 8-wide BVH
     const float *lambdas;          // frequency-space film: K wavelengths (m), the film has T = 2K; K = 0: bins

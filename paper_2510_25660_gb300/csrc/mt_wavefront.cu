@@ -134,6 +134,9 @@ __device__ __noinline__ void wf_splat_phasor(const WfParams &p, uint32_t lp, flo
 __device__ __forceinline__ void wf_splat(const WfParams &p, uint32_t pix, float opl, float3 c) {
     const uint32_t lp = pix - p.pix_base;
     const float x = (opl - p.start) / p.width;
+    if (p.splat_count)  // counting pass only: splats of this contribution into global memory
+        atomicAdd(p.splat_count, (unsigned long long)((p.K > 0 ? 2 * p.K : (x >= 0.f && x < (float)p.T ? 1 : 0)) +
+                                                      (p.steady ? 1 : 0)));
     if (p.K > 0) {
         wf_splat_phasor(p, lp, opl, c);
     } else if (x >= 0.f && x < (float)p.T) {
