@@ -124,7 +124,10 @@ struct mt_scene_s {
     cudaStream_t cap_stream = nullptr;  // private stream the NLOS graph is captured on
     // wavefront path pool
     long long launches = 0;  // kernels launched by this scene's render calls
-    uint32_t wf_cap = 0;
+    uint32_t wf_cap = 0;       // slots of the shadow-ray records and queue counters
+    uint32_t wf_slot_cap = 0;  // slots of the slot-indexed path pool and its queues
+    uint32_t wf_q_cap = 0;     // entries of the queue-ordered path state
+    float4 *wf_qs = nullptr;   // queue-ordered state: 2 x (o, d, beta, meta, tangent sums) + hits
     uint32_t wf_pool_max = MT_WF_POOL_DEFAULT;  // paths in flight (mt_set_wavefront_pool)
     float4 *wf_o = nullptr, *wf_d = nullptr, *wf_beta = nullptr, *wf_sh_o = nullptr, *wf_sh_d = nullptr,
            *wf_sh_c = nullptr;
@@ -827,11 +830,34 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
                                   bool polarized = false) {
     const unsigned long long total = (unsigned long long)f->H * f->W * rp.spp;
     const uint32_t P = (uint32_t)std::min<unsigned long long>(total, s->wf_pool_max);
-    if (P > s->wf_cap) {
+    // path state in queue order unless a form keeps per-path records by slot (replay, polarization)
+    // or reorders the queue (ray sorting, dynamic fetch)
+    const bool dyn = (cfg.options & MT_OPT_DYNAMIC_FETCH) && !dump && !s->dev.has_medium && !backward;
+    const bool qmode = !backward && !polarized && !dyn && !((cfg.options & MT_OPT_SORT_RAYS) && !dump);
+    if (P > s->wf_cap || (qmode ? P > s->wf_q_cap : P > s->wf_slot_cap)) {
         cudaStreamCaptureStatus cs;
         MT_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
         MT_CHECK_ARG(cs == cudaStreamCaptureStatusNone,
                      "the first wavefront render of this size must not be captured (it sizes the path pool)");
+    }
+    if (P > s->wf_cap) {
+        auto &al = s->al;
+        MT_TRY(al.alloc(&s->wf_sh_o, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_d, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
+        MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
+        if (!s->wf_counters) {
+            MT_TRY(al.alloc(&s->wf_counters, 16, "path queue counters"));
+            MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
+            MT_TRY(al.alloc((char **)&s->wf_iter, 64, "path queue counters"));
+        }
+        s->wf_cap = P;
+    }
+    if (qmode && P > s->wf_q_cap) {
+        MT_TRY(s->al.alloc(&s->wf_qs, (size_t)11 * P, "queue-ordered path state"));
+        s->wf_q_cap = P;
+    }
+    if (!qmode && P > s->wf_slot_cap) {
         auto &al = s->al;
 #if MT_WF_AOS
         MT_TRY(al.alloc(&s->wf_o, (size_t)MT_WF_REC * P, "path pool"));
@@ -851,16 +877,7 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
         MT_TRY(al.alloc(&s->wf_qa, P, "path queues"));
         MT_TRY(al.alloc(&s->wf_qb, P, "path queues"));
         MT_TRY(al.alloc(&s->wf_free, P, "path queues"));
-        MT_TRY(al.alloc(&s->wf_sh_o, P, "shadow queue"));
-        MT_TRY(al.alloc(&s->wf_sh_d, P, "shadow queue"));
-        MT_TRY(al.alloc(&s->wf_sh_c, P, "shadow queue"));
-        MT_TRY(al.alloc(&s->wf_sh_m, P, "shadow queue"));
-        if (!s->wf_counters) {
-            MT_TRY(al.alloc(&s->wf_counters, 16, "path queue counters"));
-            MT_TRY(al.alloc(&s->wf_next, 1, "path queue counters"));
-            MT_TRY(al.alloc((char **)&s->wf_iter, 64, "path queue counters"));
-        }
-        s->wf_cap = P;
+        s->wf_slot_cap = P;
     }
     if (backward) {
         const size_t need = (size_t)(rp.max_depth + 1) * P;
@@ -934,6 +951,21 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     w.qa = s->wf_qa;
     w.qb = s->wf_qb;
     w.free_q = s->wf_free;
+    w.qmode = qmode ? 1 : 0;
+    if (qmode) {
+        float4 *q = s->wf_qs;  // 11 arrays of P float4: o, d, beta, meta, sig (current), the same (next), hits
+        w.ps_o = q;
+        w.ps_d = q + (size_t)P;
+        w.ps_b = q + (size_t)2 * P;
+        w.ps_m = (uint4 *)(q + (size_t)3 * P);
+        w.ps_sig = tangent ? q + (size_t)4 * P : nullptr;
+        w.ps_o_n = q + (size_t)5 * P;
+        w.ps_d_n = q + (size_t)6 * P;
+        w.ps_b_n = q + (size_t)7 * P;
+        w.ps_m_n = (uint4 *)(q + (size_t)8 * P);
+        w.ps_sig_n = tangent ? q + (size_t)9 * P : nullptr;
+        w.ps_h = (int4 *)(q + (size_t)10 * P);
+    }
     w.sh_o = s->wf_sh_o;
     w.sh_d = s->wf_sh_d;
     w.sh_c = s->wf_sh_c;

@@ -99,6 +99,17 @@ struct WfParams {
     PoolField<uint4> meta;         // pixel, sample index, depth
     PoolField<int4> hit;           // leaf-order triangle, original triangle, t bits
     uint32_t *qa, *qb, *free_q;    // extension queues and the free-slot stack
+    // Queue-ordered path state (qmode = 1; the forward forms without ray sorting or dynamic fetch): the
+    // path at position i of this iteration's extension queue has its state at ps_o[i], ps_d[i], ps_b[i],
+    // ps_m[i] (ps_sig[i] for the forward-mode derivative) and its hit at ps_h[i]; shading writes each continuing
+    // path to the next iteration's arrays (_n) at its position in the next queue, so every stage reads
+    // and writes the state in queue order and no slot index or free-slot stack is involved.
+    int32_t qmode;
+    float4 *ps_o, *ps_d, *ps_b, *ps_sig;
+    uint4 *ps_m;
+    float4 *ps_o_n, *ps_d_n, *ps_b_n, *ps_sig_n;
+    uint4 *ps_m_n;
+    int4 *ps_h;
     float4 *sh_o, *sh_d, *sh_c;    // shadow rays: origin + tmax, direction + OPL, contribution + pixel
     uint4 *sh_m;                   // shadow ray record: sample, depth, emitter triangle
     uint32_t *counters;            // queue counts and cursors

@@ -156,6 +156,33 @@ __device__ __forceinline__ void slab(const RayT &r, uint32_t wx, uint32_t wy, ui
     tf = fminf(min3f(fx, fy, fz), tmax);
 }
 
+// entry / exit distances of both child boxes of a binary node (a, b = its two
+// 128-bit halves); with MT_SLAB_PAIR_Z the z planes of the two children share
+// packed FMAs as the x and y planes of one child do (same results)
+#ifndef MT_SLAB_PAIR_Z
+#define MT_SLAB_PAIR_Z 0
+#endif
+__device__ __forceinline__ void slab2(const RayT &r, const uint4 &a, const uint4 &b, float tmax, float &tn0,
+                                      float &tf0, float &tn1, float &tf1) {
+#if MT_SLAB_PAIR_Z
+    const uint32_t sx = r.sel_n[0], sy = r.sel_n[1], sz = r.sel_n[2];
+    float nx0, ny0, fx0, fy0, nx1, ny1, fx1, fy1, nz0, nz1, fz0, fz1;
+    fma_x2(q_plane(a.x, sx), q_plane(a.y, sy), r.sa.x, r.sa.y, r.sb.x, r.sb.y, nx0, ny0);
+    fma_x2(q_plane(a.x, sx ^ 0x22u), q_plane(a.y, sy ^ 0x22u), r.sa.x, r.sa.y, r.sb.x, r.sb.y, fx0, fy0);
+    fma_x2(q_plane(a.w, sx), q_plane(b.x, sy), r.sa.x, r.sa.y, r.sb.x, r.sb.y, nx1, ny1);
+    fma_x2(q_plane(a.w, sx ^ 0x22u), q_plane(b.x, sy ^ 0x22u), r.sa.x, r.sa.y, r.sb.x, r.sb.y, fx1, fy1);
+    fma_x2(q_plane(a.z, sz), q_plane(b.y, sz), r.sa.z, r.sa.z, r.sb.z, r.sb.z, nz0, nz1);
+    fma_x2(q_plane(a.z, sz ^ 0x22u), q_plane(b.y, sz ^ 0x22u), r.sa.z, r.sa.z, r.sb.z, r.sb.z, fz0, fz1);
+    tn0 = fmaxf(max3f(nx0, ny0, nz0), 0.0f);
+    tf0 = fminf(min3f(fx0, fy0, fz0), tmax);
+    tn1 = fmaxf(max3f(nx1, ny1, nz1), 0.0f);
+    tf1 = fminf(min3f(fx1, fy1, fz1), tmax);
+#else
+    slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
+    slab(r, a.w, b.x, b.y, tmax, tn1, tf1);
+#endif
+}
+
 // Watertight ray/triangle test.  The edge functions are evaluated without
 // contraction so that a shared edge gives exactly opposite values in its two
 // triangles (no gaps).  Returns true with t = T/det when the ray crosses the
@@ -198,8 +225,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
             ldg_node(&s.nodes[2 * ref], a, b);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
-            slab(r, a.x, a.y, a.z, tbest, tn0, tf0);
-            slab(r, a.w, b.x, b.y, tbest, tn1, tf1);
+            slab2(r, a, b, tbest, tn0, tf0, tn1, tf1);
             const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
             const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
@@ -262,8 +288,7 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             ldg_node(&s.nodes[2 * ref], a, b);
             if (CNT) cnt.nodes += 32;
             float tn0, tf0, tn1, tf1;
-            slab(r, a.x, a.y, a.z, tmax, tn0, tf0);
-            slab(r, a.w, b.x, b.y, tmax, tn1, tf1);
+            slab2(r, a, b, tmax, tn0, tf0, tn1, tf1);
             const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
             const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
@@ -387,10 +412,116 @@ __device__ __forceinline__ int trace_ww(const DevScene &s, const RayT &r, float 
     return best_k;
 }
 
+// ---------------------------------------------------------------------------
+// Single-loop traversal with batched leaves: a lane that reaches a leaf keeps
+// it pending and goes on with the next node from its stack; the pending leaves
+// of a warp are tested together once at least MT_PP_K lanes hold one (or no
+// lane has a node left to visit), so that the triangle tests of a few lanes do
+// not stall the node tests of the others in every iteration.  Only the visiting
+// order changes (closest hit: the smallest (t, original index) over all tested
+// triangles; the pop test against a not yet lowered best distance only visits
+// more nodes), so the hits are those of trace_closest_simple / trace_any_simple.
+// ---------------------------------------------------------------------------
+#ifndef MT_PP_K
+#define MT_PP_K 16
+#endif
+
+template <bool ANY, bool CNT>
+__device__ __forceinline__ int trace_pp(const DevScene &s, const RayT &r, float tmax, float &t_out, int &orig_out,
+                                        TraceCnt &cnt) {
+    float tbest = tmax;
+    int best_k = -1, best_id = 0x7fffffff;
+    uint2 st[MT_STACK];  // (reference, entry distance bits)
+    int sp = 0;
+    uint32_t ref = 0, leaf = MT_DONE;
+    for (;;) {
+        if (ref != MT_DONE && !MT_IS_LEAF(ref)) {
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
+            if (CNT) cnt.nodes += 32;
+            float tn0, tf0, tn1, tf1;
+            slab2(r, a, b, tbest, tn0, tf0, tn1, tf1);
+            const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
+            if (h0 && h1) {
+                const bool f0 = tn0 <= tn1;
+                if (sp < MT_STACK) {
+                    st[sp] = make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0));
+                    ++sp;
+                } else {
+                    raise_err(s, MT_EFLAG_STACK);
+                }
+                ref = f0 ? b.z : b.w;
+            } else if (h0) {
+                ref = b.z;
+            } else if (h1) {
+                ref = b.w;
+            } else {
+                ref = MT_DONE;
+                while (sp > 0) {
+                    --sp;
+                    const uint2 e = st[sp];
+                    if (ANY || __uint_as_float(e.y) <= tbest) {
+                        ref = e.x;
+                        break;
+                    }
+                }
+            }
+        }
+        if (leaf == MT_DONE && ref != MT_DONE && MT_IS_LEAF(ref)) {  // keep the leaf pending
+            leaf = ref;
+            ref = MT_DONE;
+            while (sp > 0) {
+                --sp;
+                const uint2 e = st[sp];
+                if (ANY || __uint_as_float(e.y) <= tbest) {
+                    ref = e.x;
+                    break;
+                }
+            }
+        }
+        const unsigned act = __activemask();
+        const unsigned pend = __ballot_sync(act, leaf != MT_DONE);
+        const unsigned busy = __ballot_sync(act, ref != MT_DONE && !MT_IS_LEAF(ref));
+        if (__popc(pend) >= MT_PP_K || busy == 0u) {
+            if (leaf != MT_DONE) {
+                const int first = (int)(leaf & 0x1FFFFFFFu), n = (int)((leaf >> 29) & 3u) + 1;
+                leaf = MT_DONE;
+                for (int k = first; k < first + n; ++k) {
+                    const float4 p0 = ldg_keep(&s.tris[3 * k]);
+                    const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+                    const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
+                    if (CNT) cnt.tris++;
+                    float t;
+                    if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                        if (ANY) return 1;
+                        const int id = __float_as_int(p0.w);
+                        if (t < tbest || (t == tbest && id < best_id)) {
+                            tbest = t;
+                            best_k = k;
+                            best_id = id;
+                        }
+                    }
+                }
+            }
+        }
+        if (ref == MT_DONE && leaf == MT_DONE) break;
+    }
+    if (ANY) return -1;
+    t_out = tbest;
+    orig_out = best_id;
+    return best_k;
+}
+
 // while-while traversal measured slower than the single loop on GB300 for the
 // large scene (269 ms against 244 ms per render), so it is off by default
 #ifndef MT_TRAVERSAL_WW
 #define MT_TRAVERSAL_WW 0
+#endif
+
+// 1: closest-hit queries with batched leaves (trace_pp), 2: any-hit queries too
+#ifndef MT_TRAVERSAL_PP
+#define MT_TRAVERSAL_PP 0
 #endif
 
 template <bool CNT>
@@ -398,6 +529,8 @@ __device__ __forceinline__ int trace_closest(const DevScene &s, const RayT &r, f
                                              int &orig_out, TraceCnt &cnt) {
 #if MT_TRAVERSAL_WW
     return trace_ww<false, CNT>(s, r, tmax, t_out, orig_out, cnt);
+#elif MT_TRAVERSAL_PP
+    return trace_pp<false, CNT>(s, r, tmax, t_out, orig_out, cnt);
 #else
     return trace_closest_simple<CNT>(s, r, tmax, t_out, orig_out, cnt);
 #endif
@@ -409,6 +542,10 @@ __device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, floa
     float t;
     int id;
     return trace_ww<true, CNT>(s, r, tmax, t, id, cnt) != 0;
+#elif MT_TRAVERSAL_PP >= 2
+    float t;
+    int id;
+    return trace_pp<true, CNT>(s, r, tmax, t, id, cnt) > 0;
 #else
     return trace_any_simple<CNT>(s, r, tmax, cnt);
 #endif

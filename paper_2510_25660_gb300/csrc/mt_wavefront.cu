@@ -3,16 +3,23 @@
 // The same estimator as k_render (arXiv 2510.25660 Sec. 3: paths, optical
 // path length, next-event estimation with power-heuristic MIS, path reuse into
 // time bins), reorganised so that every traversal kernel sees only one kind of
-// ray: a pool of P paths lives in device memory and each iteration runs
+// ray: up to P paths are in flight in device memory and each iteration runs
 //   k_wf_setup     bookkeeping of queue counts, how many new paths to start
-//   k_wf_generate  camera rays for new paths in free pool slots
-//   k_wf_extend    closest hits of all queued extension rays
+//   k_wf_generate  camera rays for new paths behind the continuing ones
+//   k_wf_trace     closest hits of all queued extension rays, then the shadow
+//                  rays of the previous shading pass (k_wf_extend and
+//                  k_wf_shadow separately in the replay, polarized and dump
+//                  forms)
 //   k_wf_shade     emission found by the path, next-event sample (a shadow ray
 //                  carrying its contribution), BSDF sample, continuation
-//   k_wf_shadow    any-hit test of the shadow rays, splat of unoccluded ones
 // Warps claim rays 32 at a time from a queue cursor, so lanes stay busy until
 // the queue drains; appends to the queues are warp-aggregated.  New paths get
 // consecutive ids (pixel-major), so camera rays of a warp share a pixel.
+// The state of the forward forms is kept in queue order (the path at queue
+// position i has its record at index i of per-field arrays, and shading
+// writes a continuing path to its position in the next queue), so every stage
+// streams it; the path replay and polarization keep per-slot records in a
+// pool indexed through the queues, with a stack of free slots.
 // Contributions go to the film with global atomics (no per-tile ownership).
 #include <cub/cub.cuh>
 
@@ -256,7 +263,7 @@ __device__ __forceinline__ void warp_count(unsigned long long *dst, T v) {
 
 __global__ void k_wf_setup(WfParams p, WfIter *it) {
     uint32_t *c = p.counters;
-    const uint32_t cont = c[C_NEXT], freec = c[C_FREE];
+    const uint32_t cont = c[C_NEXT], freec = p.qmode ? p.P - cont : c[C_FREE];
     const unsigned long long base = *p.next_path;
     const unsigned long long remain = base < p.total_paths ? p.total_paths - base : 0ull;
     const uint32_t n_new = (uint32_t)min((unsigned long long)freec, remain);
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
     const WfIter it = *itp;
     uint32_t paths = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < it.n_new; i += gridDim.x * blockDim.x) {
-        const uint32_t slot = p.free_q[it.free_before - 1 - i];
+        const uint32_t slot = p.qmode ? 0u : p.free_q[it.free_before - 1 - i];
         const unsigned long long j = it.base + i;
         const uint32_t lpix = (uint32_t)(j / p.spp);
         const uint32_t smp = p.sample_offset + (uint32_t)(j - (unsigned long long)lpix * p.spp);
@@ -294,6 +301,16 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
         const float sy =
             (1.0f - 2.0f * ((float)py + jy) / (float)p.H_full) * s.tan_half * ((float)p.H_full / (float)p.W);
         const float3 d = normalize(s.cam_f + s.cam_r * sx + s.cam_u * sy);
+        if (p.qmode) {  // the new path's state at its position in this iteration's queue
+            const uint32_t q = it.cont + i;
+            p.ps_o[q] = make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f);
+            p.ps_d[q] = make_float4(d.x, d.y, d.z, 0.f);
+            p.ps_b[q] = make_float4(1.f, 1.f, 1.f, 0.f);
+            p.ps_m[q] = make_uint4(pix, smp, 1u, 0u);
+            if (p.ps_sig) p.ps_sig[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            paths++;
+            continue;
+        }
         st_pair<MT_WF_V8_GEN>(&p.o[slot], &p.d[slot], make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f),
                 make_float4(d.x, d.y, d.z, 0.f));
         if (p.sig) p.sig[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -337,9 +354,14 @@ __device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, c
         if (base >= n) break;
         const uint32_t i = base + lane;
         if (i < n) {
-            const uint32_t slot = qcur[i];
+            const uint32_t slot = p.qmode ? i : qcur[i];
             float4 o, d;
-            ld_pair<MT_WF_V8_EXT>(&p.o[slot], &p.d[slot], o, d);
+            if (p.qmode) {
+                o = p.ps_o[i];
+                d = p.ps_d[i];
+            } else {
+                ld_pair<MT_WF_V8_EXT>(&p.o[slot], &p.d[slot], o, d);
+            }
             const RayT r = make_ray(s, xyz(o), xyz(d));
             float t;
             int orig;
@@ -350,7 +372,7 @@ __device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, c
                 // delta tracking over the part of the segment inside the medium (Sec. 4.1)
                 float ma, mb;
                 if (medium_span(s, xyz(o), xyz(d), k >= 0 ? t : 1e30f, ma, mb)) {
-                    const uint4 m = p.meta[slot];
+                    const uint4 m = p.qmode ? p.ps_m[i] : p.meta[slot];
                     const float inv = 1.0f / s.m_major;
                     float tt = ma;
                     for (uint32_t j = 0;; ++j) {
@@ -370,7 +392,8 @@ __device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, c
                     }
                 }
             }
-            p.hit[slot] = make_int4(k, orig, __float_as_int(t), collided);
+            if (p.qmode) p.ps_h[i] = make_int4(k, orig, __float_as_int(t), collided);
+            else p.hit[slot] = make_int4(k, orig, __float_as_int(t), collided);
             rays++;
         }
     }
@@ -854,7 +877,8 @@ __device__ __forceinline__ float3 drad_of(const WfParams &p, int em) {
 
 // TAN: forward-mode derivative (Sec. 4.4): every contribution C is replaced by
 // C * (sum of ratio * dtheta over its vertices) + Cbar * dLe (the film becomes
-// the tangent film); the prefix sum of a path lives in p.sig.
+// the tangent film); the prefix sum of a path lives in p.sig (slot-indexed pool) or
+// p.ps_sig (queue-ordered state).
 // BWD: path replay (Sec. 4.4): each vertex records the ratio of its
 // continuation and the sum of g * C of the contributions made there (light found
 // here; the next-event term is added by the shadow stage), paths that end go to
@@ -872,9 +896,10 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
     const uint32_t stride = gridDim.x * blockDim.x;
     // every lane of a warp runs the same number of iterations (warp-level appends)
     const uint32_t n_round = ((n + 31u) / 32u) * 32u;
+    const bool qord = !BWD && p.qmode;  // queue-ordered state (the replay keeps its records per slot)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         bool valid = i < n;
-        const uint32_t slot = valid ? qcur[i] : 0u;
+        const uint32_t slot = valid && !qord ? qcur[i] : 0u;
         bool cont = false, shadow = false, done = false;
         float4 sh_o = make_float4(0, 0, 0, 0), sh_d = sh_o, sh_c = sh_o, sh_own = sh_o;
         int end = 0;  // BWD: the path's last vertex
@@ -883,21 +908,32 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
         uint4 sh_m = make_uint4(0, 0, 0, 0);
         float4 o4 = sh_o, d4 = sh_o, b4 = sh_o;
         uint4 m = sh_m;
+        // state of the continuing path, written once its position in the next queue is known
+        float4 n_o = sh_o, n_d = sh_o, n_b = sh_o;
+        uint4 n_m = sh_m;
+        float3 n_sig = f3(0.f, 0.f, 0.f);
         if (valid) {
-            ld_pair<MT_WF_V8_SHADE_LD>(&p.o[slot], &p.d[slot], o4, d4);
-            {
+            int4 h;
+            if (qord) {
+                o4 = p.ps_o[i];
+                d4 = p.ps_d[i];
+                b4 = p.ps_b[i];
+                m = p.ps_m[i];
+                h = p.ps_h[i];
+            } else {
+                ld_pair<MT_WF_V8_SHADE_LD>(&p.o[slot], &p.d[slot], o4, d4);
                 float4 mf;
                 ld_pair<MT_WF_V8_SHADE_LD>(&p.beta[slot], (const float4 *)&p.meta[slot], b4, mf);
                 m = f4u(mf);
+                h = p.hit[slot];
             }
-            const int4 h = p.hit[slot];
             const uint32_t pix = m.x, smp = m.y;
             const int depth = (int)m.z;
             float opl = o4.w;
             float3 beta = xyz(b4);
             const float3 dir = xyz(d4);
             float3 sig = f3(0.f, 0.f, 0.f);
-            if (TAN) sig = xyz(p.sig[slot]);
+            if (TAN) sig = xyz(qord ? p.ps_sig[i] : p.sig[slot]);
             end = depth - 1;
             if (MEDIA && h.w) {
                 // scattering in the medium: albedo, next-event estimate through the medium
@@ -959,15 +995,16 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                     if (TAN) {
                         const float dr = p.dmed / s.m_params[0];
                         sig = sig + f3(dr, dr, dr);
-                        p.sig[slot] = make_float4(sig.x, sig.y, sig.z, 0.f);
+                        n_sig = sig;
                     }
                     if (BWD) {
                         const float ia = 1.0f / s.m_params[0];
                         rv = f3(ia, ia, ia);
                     }
-                    st_pair<MT_WF_V8_SHADE_ST>(&p.o[slot], &p.d[slot], make_float4(x.x, x.y, x.z, opl), make_float4(nd.x, nd.y, nd.z, 0.f));
-                    st_pair<MT_WF_V8_SHADE_ST>(&p.beta[slot], (float4 *)&p.meta[slot], make_float4(beta.x, beta.y, beta.z, 0.f),
-                            u4f(make_uint4(pix, smp, (uint32_t)(depth + 1), 0u)));
+                    n_o = make_float4(x.x, x.y, x.z, opl);
+                    n_d = make_float4(nd.x, nd.y, nd.z, 0.f);
+                    n_b = make_float4(beta.x, beta.y, beta.z, 0.f);
+                    n_m = make_uint4(pix, smp, (uint32_t)(depth + 1), 0u);
                     cont = true;
                 }
             } else if (h.x < 0) {
@@ -1086,14 +1123,14 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
                                                               p.dalb[orig * 3 + 2])
                                                          : f3(0.f, 0.f, 0.f);
                                 sig = sig + mul(bsdf_dratio(mat, wol, wil), dv);
-                                p.sig[slot] = make_float4(sig.x, sig.y, sig.z, 0.f);
+                                n_sig = sig;
                             }
                             const float3 no = x + nn * eps_of(x);
                             const float3 nd = to_world(wil, tb, bb, nn);
-                            st_pair<MT_WF_V8_SHADE_ST>(&p.o[slot], &p.d[slot], make_float4(no.x, no.y, no.z, opl),
-                                    make_float4(nd.x, nd.y, nd.z, pb));
-                            st_pair<MT_WF_V8_SHADE_ST>(&p.beta[slot], (float4 *)&p.meta[slot], make_float4(beta.x, beta.y, beta.z, 0.f),
-                                    u4f(make_uint4(pix, smp, (uint32_t)(depth + 1), 0u)));
+                            n_o = make_float4(no.x, no.y, no.z, opl);
+                            n_d = make_float4(nd.x, nd.y, nd.z, pb);
+                            n_b = make_float4(beta.x, beta.y, beta.z, 0.f);
+                            n_m = make_uint4(pix, smp, (uint32_t)(depth + 1), 0u);
                             cont = true;
                         }
                     }
@@ -1109,14 +1146,29 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             p.rec_c[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const uint32_t qs = wf_append(&p.counters[C_NEXT], cont);
-        if (cont) qnext[qs] = slot;
-        const uint32_t fs = wf_append(&p.counters[BWD ? C_FIN : C_FREE], done);
-        if (done) {
-            if (BWD) {
-                p.fin_q[fs] = slot;
-                p.meta[slot] = make_uint4(m.x, m.y, m.z, (uint32_t)end);
+        if (cont) {
+            if (qord) {
+                p.ps_o_n[qs] = n_o;
+                p.ps_d_n[qs] = n_d;
+                p.ps_b_n[qs] = n_b;
+                p.ps_m_n[qs] = n_m;
+                if (TAN) p.ps_sig_n[qs] = make_float4(n_sig.x, n_sig.y, n_sig.z, 0.f);
             } else {
-                p.free_q[fs] = slot;
+                qnext[qs] = slot;
+                st_pair<MT_WF_V8_SHADE_ST>(&p.o[slot], &p.d[slot], n_o, n_d);
+                st_pair<MT_WF_V8_SHADE_ST>(&p.beta[slot], (float4 *)&p.meta[slot], n_b, u4f(n_m));
+                if (TAN) p.sig[slot] = make_float4(n_sig.x, n_sig.y, n_sig.z, 0.f);
+            }
+        }
+        if (!qord) {  // the slot of a finished path returns to the free stack (replay: to the finalize queue)
+            const uint32_t fs = wf_append(&p.counters[BWD ? C_FIN : C_FREE], done);
+            if (done) {
+                if (BWD) {
+                    p.fin_q[fs] = slot;
+                    p.meta[slot] = make_uint4(m.x, m.y, m.z, (uint32_t)end);
+                } else {
+                    p.free_q[fs] = slot;
+                }
             }
         }
         const uint32_t ss = wf_append(&p.counters[C_SHADOW], shadow);
@@ -1233,7 +1285,8 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_trace(const DevSce
 }
 
 __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsigned long long *next_path) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) free_q[i] = i;
+    if (free_q)  // slot-indexed pool only
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) free_q[i] = i;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int k = 0; k < MT_WF_COUNTERS; ++k) counters[k] = 0;
         counters[C_FREE] = P;
@@ -1302,7 +1355,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
                               cudaStream_t st, long long *launches, WfTiming *timing) {
     WfParams p = p0;
     const int grid = num_sms * 8;
-    k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.free_q, p.P, p.counters,
+    k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.qmode ? nullptr : p.free_q, p.P, p.counters,
                                                                                     p.next_path);
     MT_CUDA_TRY(cudaGetLastError());
     uint32_t *qa = p.qa, *qb = p.qb;
@@ -1379,7 +1432,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         } else if (p.bwd) {
             if (media) k_wf_shade<false, true, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
             else k_wf_shade<false, false, false, true><<<grid, 256, 0, st>>>(s, p, qa, qb);
-        } else if (p.sig) {
+        } else if (p.sig || p.ps_sig) {  // forward-mode derivative
             if (media) k_wf_shade<false, true, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
             else k_wf_shade<false, false, true, false><<<grid, 256, 0, st>>>(s, p, qa, qb);
         } else if (media) {
@@ -1443,6 +1496,13 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         uint32_t *t = qa;
         qa = qb;
         qb = t;
+        if (p.qmode) {  // the next iteration reads the state shading wrote
+            std::swap(p.ps_o, p.ps_o_n);
+            std::swap(p.ps_d, p.ps_d_n);
+            std::swap(p.ps_b, p.ps_b_n);
+            std::swap(p.ps_m, p.ps_m_n);
+            std::swap(p.ps_sig, p.ps_sig_n);
+        }
         // check for completion every few iterations (one small read-back)
         if ((iter & 3) == 3 || iter + 1 == bound) {
             uint32_t done = 0;
