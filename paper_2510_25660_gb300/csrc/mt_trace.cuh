@@ -209,6 +209,13 @@ struct TraceCnt {
     uint32_t nodes, tris;  // bytes of BVH nodes fetched, triangle records tested
 };
 
+// MT_SMEM_STACK > 0: the first MT_SMEM_STACK entries of each thread's traversal
+// stack live in shared memory (CTAs of at most 256 threads), deeper ones in
+// local memory
+#ifndef MT_SMEM_STACK
+#define MT_SMEM_STACK 0
+#endif
+
 // Closest hit with t in (0, tmax); ties in t go to the smaller original index.
 // Returns the leaf-order triangle index (or -1) and writes t and the original index.
 template <bool CNT>
@@ -217,6 +224,14 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
     float tbest = tmax;
     int best_k = -1, best_id = 0x7fffffff;
     uint2 st[MT_STACK];  // (reference, entry distance bits)
+#if MT_SMEM_STACK
+    __shared__ uint2 s_st[MT_SMEM_STACK][256];
+#define MT_ST_PUT(i, v) do { if ((i) < MT_SMEM_STACK) s_st[i][threadIdx.x] = (v); else st[i] = (v); } while (0)
+#define MT_ST_GET(i) ((i) < MT_SMEM_STACK ? s_st[i][threadIdx.x] : st[i])
+#else
+#define MT_ST_PUT(i, v) (st[i] = (v))
+#define MT_ST_GET(i) (st[i])
+#endif
     int sp = 0;
     uint32_t ref = 0;
     for (;;) {
@@ -231,7 +246,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
                 if (sp < MT_STACK) {
-                    st[sp] = make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0));
+                    MT_ST_PUT(sp, make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0)));
                     ++sp;
                 } else {
                     raise_err(s, MT_EFLAG_STACK);
@@ -267,7 +282,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
                 return best_k;
             }
             --sp;
-            const uint2 e = st[sp];
+            const uint2 e = MT_ST_GET(sp);
             if (__uint_as_float(e.y) <= tbest) {
                 ref = e.x;
                 break;
@@ -276,10 +291,16 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
     }
 }
 
+#undef MT_ST_PUT
+#undef MT_ST_GET
+
 // Any hit with t in (0, tmax).
 template <bool CNT>
 __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &r, float tmax, TraceCnt &cnt) {
     uint32_t st_ref[MT_STACK];
+#if MT_SMEM_STACK
+    __shared__ uint32_t s_st1[MT_SMEM_STACK][256];
+#endif
     int sp = 0;
     uint32_t ref = 0;
     for (;;) {
@@ -293,8 +314,17 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
             if (h0 && h1) {
                 const bool f0 = tn0 <= tn1;
-                if (sp < MT_STACK) st_ref[sp++] = f0 ? b.w : b.z;
-                else raise_err(s, MT_EFLAG_STACK);
+                if (sp < MT_STACK) {
+#if MT_SMEM_STACK
+                    if (sp < MT_SMEM_STACK) s_st1[sp][threadIdx.x] = f0 ? b.w : b.z;
+                    else st_ref[sp] = f0 ? b.w : b.z;
+#else
+                    st_ref[sp] = f0 ? b.w : b.z;
+#endif
+                    ++sp;
+                } else {
+                    raise_err(s, MT_EFLAG_STACK);
+                }
                 ref = f0 ? b.z : b.w;
                 continue;
             }
@@ -312,7 +342,12 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             }
         }
         if (sp == 0) return false;
-        ref = st_ref[--sp];
+        --sp;
+#if MT_SMEM_STACK
+        ref = sp < MT_SMEM_STACK ? s_st1[sp][threadIdx.x] : st_ref[sp];
+#else
+        ref = st_ref[sp];
+#endif
     }
 }
 
