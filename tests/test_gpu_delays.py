@@ -44,7 +44,7 @@ def test_delayed_contributions_match_oracle(cornell, form):
     px, py = rec["pixel"] % W, rec["pixel"] // W
     sel = (px >= crop[0]) & (px < crop[1]) & (py >= crop[2]) & (py < crop[3])
     nm, div, worst, bad, bin_bad, dopl = match_contribs(rec[sel], ref["dump"], start=start, width=width)
-    assert nm > 3000 and div <= 1e-3 * nm and bad <= 1e-3 * nm and bin_bad == 0, (nm, div, bad, bin_bad)
+    assert nm > 3000 and div <= 1e-4 * nm and bad <= 1e-3 * nm and bin_bad == 0, (nm, div, bad, bin_bad)
     assert np.quantile(dopl, 0.999) < 2e-5
     ref16 = osc.render(H, W, T, start, width, 16, seed, depth, crop=(24, 40, 24, 40))
     g = f2.cpu().numpy()[24:40, 24:40]
