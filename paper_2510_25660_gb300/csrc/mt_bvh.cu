@@ -570,15 +570,17 @@ __global__ void k_internal_flags(const BNode *nodes, int n, int *flags) {
         flags[i] = nodes[i].left >= 0 ? 1 : 0;
 }
 
-// planes rounded outward and padded by two quantisation steps
-__device__ __forceinline__ uint32_t qfloor(float v, double lo, double sc) {
-    double q = floor(((double)v - lo) / sc) - 2.0;
-    q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
+// planes rounded outward and padded by two quantisation steps: (v - lo) / sc evaluated in
+// float with directed rounding (toward -inf for a lower plane, +inf for an upper one, with
+// the reciprocal of sc rounded the same way), so the plane never moves inward
+__device__ __forceinline__ uint32_t qfloor(float v, float lo, float sc) {
+    float q = floorf(__fmul_rd(__fsub_rd(v, lo), __frcp_rd(sc))) - 2.0f;
+    q = q < 0.0f ? 0.0f : (q > 65535.0f ? 65535.0f : q);
     return (uint32_t)q;
 }
-__device__ __forceinline__ uint32_t qceil(float v, double lo, double sc) {
-    double q = ceil(((double)v - lo) / sc) + 2.0;
-    q = q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q);
+__device__ __forceinline__ uint32_t qceil(float v, float lo, float sc) {
+    float q = ceilf(__fmul_ru(__fsub_ru(v, lo), __frcp_ru(sc))) + 2.0f;
+    q = q < 0.0f ? 0.0f : (q > 65535.0f ? 65535.0f : q);
     return (uint32_t)q;
 }
 
@@ -731,25 +733,30 @@ __global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end
             ch[n++] = nodes[c].right;
         }
         double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        double cc[8][3];
+        float cc[8][3];  // child centroids relative to the node centre (only rank the slot choices)
         for (int i = 0; i < n; ++i) {
             const BNode &c = nodes[ch[i]];
             for (int k = 0; k < 3; ++k) {
                 lo[k] = fmin(lo[k], (double)c.lo[k]);
                 hi[k] = fmax(hi[k], (double)c.hi[k]);
-                cc[i][k] = 0.5 * ((double)c.lo[k] + (double)c.hi[k]);
             }
+        }
+        for (int i = 0; i < n; ++i) {
+            const BNode &c = nodes[ch[i]];
+            for (int k = 0; k < 3; ++k) cc[i][k] = 0.5f * (c.lo[k] + c.hi[k]) - (float)(0.5 * (lo[k] + hi[k]));
         }
         // per-axis step 2^e >= extent / 250 (and >= 2^e_min); origin two steps below
         int e[3];
-        double step[3];
+        double inv_step[3];
         float p[3];
         for (int k = 0; k < 3; ++k) {
+            const double ext = hi[k] - lo[k];
             int ek = e_min;
-            while (ek < 127 && ldexp(250.0, ek) < hi[k] - lo[k]) ++ek;
+            if (ext > 0.0) ek = max(e_min, ilogb(ext / 250.0) - 1);  // at most the answer: the loop ends it
+            while (ek < 127 && ldexp(250.0, ek) < ext) ++ek;
             e[k] = ek;
-            step[k] = ldexp(1.0, ek);
-            p[k] = (float)(lo[k] - 2.0 * step[k]);
+            inv_step[k] = ldexp(1.0, -ek);  // exact: the planes below divide by a power of two
+            p[k] = (float)(lo[k] - 2.0 * ldexp(1.0, ek));
         }
         // slots: greedily pair the child and corner whose centroid offset
         // points most toward that corner
@@ -757,15 +764,15 @@ __global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end
         for (int q = 0; q < 8; ++q) slot_child[q] = -1;
         bool used[8] = {false, false, false, false, false, false, false, false};
         for (int round = 0; round < n; ++round) {
-            double bestc = INFINITY;
+            float bestc = INFINITY;
             int bi = -1, bq = -1;
             for (int i = 0; i < n; ++i) {
                 if (used[i]) continue;
                 for (int q = 0; q < 8; ++q) {
                     if (slot_child[q] >= 0) continue;
-                    double c = 0.0;
+                    float c = 0.0f;
                     for (int k = 0; k < 3; ++k) {
-                        const double off = cc[i][k] - 0.5 * (lo[k] + hi[k]);
+                        const float off = cc[i][k];
                         c -= ((q >> k) & 1) ? off : -off;
                     }
                     if (c < bestc) {
@@ -800,8 +807,8 @@ __global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end
                 continue;
             }
             for (int k = 0; k < 3; ++k) {
-                double a = floor(((double)cn.lo[k] - (double)p[k]) / step[k]) - 2.0;
-                double z = ceil(((double)cn.hi[k] - (double)p[k]) / step[k]) + 2.0;
+                double a = floor(((double)cn.lo[k] - (double)p[k]) * inv_step[k]) - 2.0;
+                double z = ceil(((double)cn.hi[k] - (double)p[k]) * inv_step[k]) + 2.0;
                 a = a < 0.0 ? 0.0 : a;
                 z = z > 255.0 ? 255.0 : z;  // unreachable: extent / step <= 250
                 ql[k][h] |= (uint32_t)a << sh;
