@@ -587,6 +587,162 @@ __device__ __forceinline__ bool trace_any(const DevScene &s, const RayT &r, floa
 }
 
 // ---------------------------------------------------------------------------
+// Warp-cooperative traversal: the 32 rays of a warp walk the top of the tree
+// as one packet and the rest one ray per lane (hybrid packet / single-ray
+// traversal, Benthin, Wald, Woop, Ernst and Mark, IEEE TVCG 2012).  While at
+// least MT_HYBRID_MIN of the warp's rays enter the current node, the warp
+// visits it together: one node load serves every lane, the stack index is the
+// same in every lane (so stack entries are coalesced in local memory), and the
+// warp descends first into the child that more of its rays reach first, with
+// each lane's own entry distance kept on the stack for culling.  A node that
+// fewer rays enter is handed to their lanes, which traverse its subtree alone
+// on top of the warp's stack; then the warp pops its next entry.  Only the
+// visiting order differs from trace_closest_simple / trace_any_simple: the
+// closest hit is the smallest (t, original index) all the same, and the any-hit
+// answer is the same.  All 32 lanes call it together, converged; a lane with
+// live = false carries no ray and gets -1.  It is an option (MT_HYBRID_EXT,
+// MT_HYBRID_SH, MT_PACKET_CAMERA in the wavefront passes): on the 1.16M-triangle
+// scene it was slower than one ray per lane at every threshold, even for warps
+// of camera rays through one pixel (the packet's visiting order culls less,
+// and the votes cost more than the shared node loads save).
+// ---------------------------------------------------------------------------
+#ifndef MT_HYBRID_MIN
+#define MT_HYBRID_MIN 8
+#endif
+
+// the triangles of one leaf against one ray; ANY: true on the first hit
+template <bool ANY, bool CNT>
+__device__ __forceinline__ bool leaf_tris(const DevScene &s, const RayT &r, uint32_t ref, float tmax, float &tbest,
+                                          int &best_k, int &best_id, TraceCnt &cnt) {
+    const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
+    for (int k = first; k < first + n; ++k) {
+        const float4 p0 = ldg_keep(&s.tris[3 * k]);
+        const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+        const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
+        if (CNT) cnt.tris++;
+        float t;
+        if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+            if (ANY) return true;
+            const int id = __float_as_int(p0.w);
+            if (t < tbest || (t == tbest && id < best_id)) {
+                tbest = t;
+                best_k = k;
+                best_id = id;
+            }
+        }
+    }
+    return false;
+}
+
+// one ray through the subtree at `ref`, its stack entries above index sp0;
+// ANY: true on the first hit
+template <bool ANY, bool CNT>
+__device__ __forceinline__ bool trav_subtree(const DevScene &s, const RayT &r, uint32_t ref, uint2 *st, const int sp0,
+                                             float tmax, float &tbest, int &best_k, int &best_id, TraceCnt &cnt) {
+    int sp = sp0;
+    for (;;) {
+        if (!(ref & 0x80000000u)) {
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
+            if (CNT) cnt.nodes += 32;
+            float tn0, tf0, tn1, tf1;
+            slab2(r, a, b, tbest, tn0, tf0, tn1, tf1);
+            const bool h0 = tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = tn1 <= tf1 && MT_LIVE(b.w);
+            if (h0 && h1) {
+                const bool f0 = tn0 <= tn1;
+                if (sp < MT_STACK) {
+                    st[sp] = make_uint2(f0 ? b.w : b.z, __float_as_uint(f0 ? tn1 : tn0));
+                    ++sp;
+                } else {
+                    raise_err(s, MT_EFLAG_STACK);
+                }
+                ref = f0 ? b.z : b.w;
+                continue;
+            }
+            if (h0) { ref = b.z; continue; }
+            if (h1) { ref = b.w; continue; }
+        } else if (leaf_tris<ANY, CNT>(s, r, ref, tmax, tbest, best_k, best_id, cnt)) {
+            return true;
+        }
+        for (;;) {
+            if (sp == sp0) return false;
+            --sp;
+            const uint2 e = st[sp];
+            if (__uint_as_float(e.y) <= tbest) {
+                ref = e.x;
+                break;
+            }
+        }
+    }
+}
+
+template <bool ANY, bool CNT>
+__device__ __forceinline__ int trace_hybrid(const DevScene &s, const RayT &r, const bool live, float tmax,
+                                            float &t_out, int &orig_out, TraceCnt &cnt,
+                                            const int min_rays = MT_HYBRID_MIN) {
+    float tbest = tmax;
+    int best_k = -1, best_id = 0x7fffffff;
+    bool found = false;  // ANY: this lane's ray is occluded
+    uint2 st[MT_STACK];  // (reference, this lane's entry distance bits; +inf: its ray misses the node)
+    int sp = 0;          // the same in every lane
+    uint32_t ref = 0;    // the same in every lane
+    bool act = live;     // this lane's ray enters node `ref`
+    for (;;) {
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (__popc(m) < min_rays) {
+            // few rays (or none) enter the node: each traverses its subtree alone
+            if (act && trav_subtree<ANY, CNT>(s, r, ref, st, sp, tmax, tbest, best_k, best_id, cnt)) found = true;
+        } else if (!(ref & 0x80000000u)) {
+            uint4 a, b;
+            ldg_node(&s.nodes[2 * ref], a, b);
+            if (CNT && act) cnt.nodes += 32;
+            float tn0, tf0, tn1, tf1;
+            slab2(r, a, b, tbest, tn0, tf0, tn1, tf1);
+            const bool h0 = act && tn0 <= tf0 && MT_LIVE(b.z);
+            const bool h1 = act && tn1 <= tf1 && MT_LIVE(b.w);
+            const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+            if (m0 | m1) {
+                // child 0 first if it is the nearer (or only) child for at least half of the rays entering either
+                const unsigned n0 = __ballot_sync(0xffffffffu, h0 && !(h1 && tn1 < tn0));
+                const bool go0 = m0 && (!m1 || 2 * __popc(n0) >= __popc(m0 | m1));
+                if (m0 && m1) {
+                    if (sp < MT_STACK) {
+                        const bool ho = go0 ? h1 : h0;
+                        st[sp] = make_uint2(go0 ? b.w : b.z, ho ? __float_as_uint(go0 ? tn1 : tn0) : 0x7F800000u);
+                        ++sp;
+                    } else {
+                        raise_err(s, MT_EFLAG_STACK);
+                    }
+                }
+                ref = go0 ? b.z : b.w;
+                act = go0 ? h0 : h1;
+                continue;
+            }
+        } else if (act && leaf_tris<ANY, CNT>(s, r, ref, tmax, tbest, best_k, best_id, cnt)) {
+            found = true;
+        }
+        // the warp's next entry that one of its rays still enters
+        if (ANY && !__any_sync(0xffffffffu, live && !found)) break;
+        bool more = false;
+        while (sp > 0) {
+            --sp;
+            const uint2 e = st[sp];
+            act = !found && __uint_as_float(e.y) <= tbest;
+            if (__any_sync(0xffffffffu, act)) {
+                ref = e.x;
+                more = true;
+                break;
+            }
+        }
+        if (!more) break;
+    }
+    t_out = tbest;
+    orig_out = best_id;
+    return ANY ? (found ? 1 : -1) : best_k;
+}
+
+// ---------------------------------------------------------------------------
 // Traversal as a per-lane state machine, one node or leaf per call, for
 // kernels whose lanes fetch a new ray as soon as their current one is done
 // (persistent threads with dynamic ray fetch, Aila & Laine, HPG 2009).

@@ -39,8 +39,23 @@ namespace {
 // counters[] layout
 // C_SH_N: shadow rays queued by the previous iteration's shading, which the
 // fused traversal pass of this iteration traces after its extension rays
-enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_FIN = 7, C_SH_N = 8 };
+// C_CONT: continuing paths at the head of this iteration's queue (new paths follow)
+enum { C_CUR = 0, C_NEXT = 1, C_SHADOW = 2, C_FREE = 3, C_EXT_CUR = 4, C_SH_CUR = 5, C_DONE = 6, C_FIN = 7, C_SH_N = 8,
+       C_CONT = 9 };
 #define MT_WF_COUNTERS 16
+// 1: extension (closest-hit) and shadow (any-hit) rays of the wavefront
+// passes traced by the warp-cooperative hybrid traversal (trace_hybrid)
+#ifndef MT_HYBRID_EXT
+#define MT_HYBRID_EXT 0
+#endif
+#ifndef MT_HYBRID_SH
+#define MT_HYBRID_SH 0
+#endif
+// > 0: warps whose 32 queue positions all hold camera rays of new paths
+// traverse as a packet while at least this many of their rays enter a node
+#ifndef MT_PACKET_CAMERA
+#define MT_PACKET_CAMERA 0
+#endif
 #ifndef MT_WF_FUSE
 #define MT_WF_FUSE 1  // 0: a shadow pass of its own after every shading pass
 #endif
@@ -268,6 +283,7 @@ __global__ void k_wf_setup(WfParams p, WfIter *it) {
     const unsigned long long remain = base < p.total_paths ? p.total_paths - base : 0ull;
     const uint32_t n_new = (uint32_t)min((unsigned long long)freec, remain);
     it->cont = cont;
+    c[C_CONT] = cont;
     it->n_new = n_new;
     it->free_before = freec;
     it->base = base;
@@ -345,7 +361,7 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
 template <bool WIDE, bool CNT, bool MEDIA>
 __device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, const uint32_t *qcur, TraceCnt &tc,
                                          uint32_t &rays) {
-    const uint32_t n = p.counters[C_CUR];
+    const uint32_t n = p.counters[C_CUR], cont = p.counters[C_CONT];
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t base = 0;
@@ -353,20 +369,32 @@ __device__ __forceinline__ void ext_rays(const DevScene &s, const WfParams &p, c
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) break;
         const uint32_t i = base + lane;
-        if (i < n) {
-            const uint32_t slot = p.qmode ? i : qcur[i];
-            float4 o, d;
+        const bool live = i < n;
+        const uint32_t slot = !live ? 0u : (p.qmode ? i : qcur[i]);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f), d = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (live) {
             if (p.qmode) {
                 o = p.ps_o[i];
                 d = p.ps_d[i];
             } else {
                 ld_pair<MT_WF_V8_EXT>(&p.o[slot], &p.d[slot], o, d);
             }
-            const RayT r = make_ray(s, xyz(o), xyz(d));
-            float t;
-            int orig;
-            int k = WIDE ? trace_wide<false, CNT>(s, r, INFINITY, t, orig, tc)
-                         : trace_closest<CNT>(s, r, INFINITY, t, orig, tc);
+        }
+        const RayT r = make_ray(s, xyz(o), xyz(d));
+        float t;
+        int orig;
+        int k;
+        if (WIDE) {
+            k = live ? trace_wide<false, CNT>(s, r, INFINITY, t, orig, tc) : -1;
+        } else if (MT_HYBRID_EXT || (MT_PACKET_CAMERA && p.qmode && base >= cont)) {
+            // the whole warp traverses together (in queue order, positions from `cont` on hold the
+            // camera rays of new paths, consecutive samples of one pixel)
+            k = trace_hybrid<false, CNT>(s, r, live, INFINITY, t, orig, tc,
+                                         MT_HYBRID_EXT ? MT_HYBRID_MIN : MT_PACKET_CAMERA);
+        } else {
+            k = live ? trace_closest<CNT>(s, r, INFINITY, t, orig, tc) : -1;
+        }
+        if (live) {
             int collided = 0;
             if (MEDIA) {
                 // delta tracking over the part of the segment inside the medium (Sec. 4.1)
@@ -1196,6 +1224,23 @@ __device__ __forceinline__ void sh_rays(const DevScene &s, const WfParams &p, ui
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) break;
         const uint32_t q = base + lane;
+#if MT_HYBRID_SH
+        // the warp traverses together (lanes past the queue's end carry no ray)
+        const bool live = q < n;
+        const uint32_t i = !live ? 0u : (p.sh_perm ? __ldg(&p.sh_perm[q]) : q);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f), d = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (live) {
+            o = p.sh_o[i];
+            d = p.sh_d[i];
+        }
+        const RayT r = make_ray(s, xyz(o), xyz(d));
+        float t_unused;
+        int id_unused;
+        const bool occluded = WIDE ? (live && trace_wide<true, CNT>(s, r, o.w, t_unused, id_unused, tc) >= 0)
+                                   : trace_hybrid<true, CNT>(s, r, live, o.w, t_unused, id_unused, tc) >= 0;
+        if (live) {
+            rays++;
+#else
         if (q < n) {
             const uint32_t i = p.sh_perm ? __ldg(&p.sh_perm[q]) : q;
             const float4 o = p.sh_o[i], d = p.sh_d[i];
@@ -1205,6 +1250,7 @@ __device__ __forceinline__ void sh_rays(const DevScene &s, const WfParams &p, ui
             int id_unused;
             const bool occluded = WIDE ? trace_wide<true, CNT>(s, r, o.w, t_unused, id_unused, tc) >= 0
                                        : trace_any<CNT>(s, r, o.w, tc);
+#endif
             if (!occluded) {
                 const float4 c = p.sh_c[i];
                 const uint32_t pix = (uint32_t)__float_as_int(c.w);
