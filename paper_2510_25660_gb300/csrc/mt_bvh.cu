@@ -77,9 +77,19 @@ __device__ __forceinline__ int f2o(float f) {
 }
 __device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
+// surface area of a box with every operation rounded on its own (no contraction), so that
+// each caller gets the same value for the same box
 __device__ __forceinline__ float area_of(const float *lo, const float *hi) {
-    const float dx = fmaxf(0.f, hi[0] - lo[0]), dy = fmaxf(0.f, hi[1] - lo[1]), dz = fmaxf(0.f, hi[2] - lo[2]);
-    return 2.0f * (dx * dy + dy * dz + dz * dx);
+    const float dx = fmaxf(0.f, __fsub_rn(hi[0], lo[0])), dy = fmaxf(0.f, __fsub_rn(hi[1], lo[1])),
+                dz = fmaxf(0.f, __fsub_rn(hi[2], lo[2]));
+    return __fmul_rn(2.0f, __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx)));
+}
+
+// SAH cost of a split, SA_L n_L + SA_R n_R (no contraction: binned and per-triangle
+// evaluations of the same split agree to the bit)
+__device__ __forceinline__ float split_sah(const float *llo, const float *lhi, int nl, const float *rlo,
+                                           const float *rhi, int nr) {
+    return __fadd_rn(__fmul_rn(area_of(llo, lhi), (float)nl), __fmul_rn(area_of(rlo, rhi), (float)nr));
 }
 
 // bin of a centroid coordinate; identical in the binning and partition passes
@@ -177,7 +187,7 @@ __device__ __forceinline__ void sweep_axis(const int *bins_axis, float &best_cos
         rhi[k] = __shfl_down_sync(0xffffffffu, shi[k], 1);
     }
     float cost = INFINITY;
-    if (lane < 31 && pc > 0 && rc > 0) cost = area_of(plo, phi) * pc + area_of(rlo, rhi) * rc;
+    if (lane < 31 && pc > 0 && rc > 0) cost = split_sah(plo, phi, pc, rlo, rhi, rc);
     int split = lane;
     for (int o = 16; o > 0; o >>= 1) {
         const float c2 = __shfl_xor_sync(0xffffffffu, cost, o);
@@ -191,24 +201,13 @@ __device__ __forceinline__ void sweep_axis(const int *bins_axis, float &best_cos
     best_split = split;
 }
 
-// union of bins [b0, b1] of an axis into box / centroid bounds
-__device__ void bins_union(const int *bins_axis, int b0, int b1, float *lo, float *hi, float *clo, float *chi) {
-    for (int k = 0; k < 3; ++k) {
-        lo[k] = INFINITY;
-        hi[k] = -INFINITY;
-        clo[k] = INFINITY;
-        chi[k] = -INFINITY;
-    }
-    for (int i = b0; i <= b1; ++i) {
-        const int *b = bins_axis + i * BIN_INTS;
-        if (b[0] == 0) continue;
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = fminf(lo[k], o2f(b[1 + k]));
-            hi[k] = fmaxf(hi[k], o2f(b[4 + k]));
-            clo[k] = fminf(clo[k], o2f(b[7 + k]));
-            chi[k] = fmaxf(chi[k], o2f(b[10 + k]));
-        }
-    }
+__device__ __forceinline__ float warp_minf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // block-wide exclusive scan of one int per thread; returns the total
@@ -339,32 +338,44 @@ __device__ void decide(const int *bins, const Task &tk, Decision *dec) {
             bs = s;
         }
     }
-    if (lane == 0) {
-        Decision d;
-        d.cntL = 0;
-        d.cntR = 0;
-        if (ba < 0) {
-            d.axis = -1;
-            d.split = 0;
-            d.nL = tk.count / 2;
-            for (int k = 0; k < 3; ++k) {
-                d.llo[k] = d.rlo[k] = tk.box_lo[k];
-                d.lhi[k] = d.rhi[k] = tk.box_hi[k];
-                d.lclo[k] = d.rclo[k] = tk.clo[k];
-                d.lchi[k] = d.rchi[k] = tk.chi[k];
-            }
-        } else {
-            const int *ab = bins + ba * NB * BIN_INTS;
-            int nL = 0;
-            for (int i = 0; i <= bs; ++i) nL += ab[i * BIN_INTS];
-            d.axis = ba;
-            d.split = bs;
-            d.nL = nL;
-            bins_union(ab, 0, bs, d.llo, d.lhi, d.lclo, d.lchi);
-            bins_union(ab, bs + 1, NB - 1, d.rlo, d.rhi, d.rclo, d.rchi);
+    Decision d;
+    d.cntL = 0;
+    d.cntR = 0;
+    if (ba < 0) {
+        d.axis = -1;
+        d.split = 0;
+        d.nL = tk.count / 2;
+        for (int k = 0; k < 3; ++k) {
+            d.llo[k] = d.rlo[k] = tk.box_lo[k];
+            d.lhi[k] = d.rhi[k] = tk.box_hi[k];
+            d.lclo[k] = d.rclo[k] = tk.clo[k];
+            d.lchi[k] = d.rchi[k] = tk.chi[k];
         }
-        *dec = d;
+    } else {
+        // lane i holds bin i of the split axis: the children's counts, boxes and centroid bounds
+        // are warp reductions over the bins on either side (min / max, so the same values as a
+        // sequential union)
+        static_assert(NB == 32, "one bin per lane");
+        const int *b = bins + (ba * NB + lane) * BIN_INTS;
+        const int cnt = b[0];
+        const bool left = lane <= bs, has = cnt > 0;
+        d.axis = ba;
+        d.split = bs;
+        d.nL = __reduce_add_sync(0xffffffffu, left ? cnt : 0);
+        for (int k = 0; k < 3; ++k) {
+            const float blo = has ? o2f(b[1 + k]) : INFINITY, bhi = has ? o2f(b[4 + k]) : -INFINITY;
+            const float bclo = has ? o2f(b[7 + k]) : INFINITY, bchi = has ? o2f(b[10 + k]) : -INFINITY;
+            d.llo[k] = warp_minf(left ? blo : INFINITY);
+            d.lhi[k] = warp_maxf(left ? bhi : -INFINITY);
+            d.lclo[k] = warp_minf(left ? bclo : INFINITY);
+            d.lchi[k] = warp_maxf(left ? bchi : -INFINITY);
+            d.rlo[k] = warp_minf(left ? INFINITY : blo);
+            d.rhi[k] = warp_maxf(left ? -INFINITY : bhi);
+            d.rclo[k] = warp_minf(left ? INFINITY : bclo);
+            d.rchi[k] = warp_maxf(left ? -INFINITY : bchi);
+        }
     }
+    if (lane == 0) *dec = d;
 }
 
 __global__ void k_choose(const Task *tasks, const int *gbins, Decision *decs) {
@@ -457,6 +468,98 @@ __global__ void k_children(const Task *tasks, int n_tasks, const Decision *decs,
     }
 }
 
+// a task of at most four triangles becomes a leaf when that costs no more than its split
+__device__ __forceinline__ bool leaf_better(const Task &tk, const Decision &d) {
+    const float sa = area_of(tk.box_lo, tk.box_hi);
+    const float split_cost =
+        __fadd_rn(__fmul_rn(MT_SAH_CT, sa), split_sah(d.llo, d.lhi, d.nL, d.rlo, d.rhi, tk.count - d.nL));
+    return tk.count <= 4 && __fmul_rn(sa, (float)tk.count) <= split_cost;
+}
+
+// The binned SAH decision (bins_add, then decide) of a task of at most 32
+// triangles, one triangle per lane of a warp, without bins.  Every split that
+// binning can choose is the largest occupied bin of its left side (equal-cost
+// splits between two occupied bins go to the smallest index), i.e. the bin of
+// some triangle: each lane prices the split at its triangle's bin from the
+// same box unions and in the same operations, and the warp takes the smallest
+// (cost, split), then the first axis of smallest cost, as decide does.  bb
+// returns this lane's bins, side its side of the chosen split (1: left).
+__device__ void decide_small(const Task &tk, const float lo[3], const float hi[3], const float cc[3], bool v,
+                             int bb[3], Decision &d, bool &side) {
+    const int lane = threadIdx.x & 31;
+    for (int a = 0; a < 3; ++a) bb[a] = v ? bin_of(cc[a], tk.clo[a], tk.chi[a]) : NB;
+    float bc = INFINITY;
+    int ba = -1, bs = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int s = bb[a];
+        int nl = 0;
+        float Ll[3] = {INFINITY, INFINITY, INFINITY}, Lh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float Rl[3] = {INFINITY, INFINITY, INFINITY}, Rh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int j = 0; j < tk.count; ++j) {
+            const bool inl = __shfl_sync(0xffffffffu, bb[a], j) <= s;
+            nl += inl ? 1 : 0;
+            for (int k = 0; k < 3; ++k) {
+                const float lj = __shfl_sync(0xffffffffu, lo[k], j), hj = __shfl_sync(0xffffffffu, hi[k], j);
+                if (inl) {
+                    Ll[k] = fminf(Ll[k], lj);
+                    Lh[k] = fmaxf(Lh[k], hj);
+                } else {
+                    Rl[k] = fminf(Rl[k], lj);
+                    Rh[k] = fmaxf(Rh[k], hj);
+                }
+            }
+        }
+        float cost = INFINITY;
+        int split = v ? s : NB;
+        if (v && s < NB - 1 && nl > 0 && tk.count - nl > 0) cost = split_sah(Ll, Lh, nl, Rl, Rh, tk.count - nl);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float c2 = __shfl_xor_sync(0xffffffffu, cost, o);
+            const int s2 = __shfl_xor_sync(0xffffffffu, split, o);
+            if (c2 < cost || (c2 == cost && s2 < split)) {
+                cost = c2;
+                split = s2;
+            }
+        }
+        if (cost < bc) {
+            bc = cost;
+            ba = a;
+            bs = split;
+        }
+    }
+    d.cntL = 0;
+    d.cntR = 0;
+    if (ba < 0) {
+        d.axis = -1;
+        d.split = 0;
+        d.nL = tk.count / 2;
+        side = false;
+        for (int k = 0; k < 3; ++k) {
+            d.llo[k] = d.rlo[k] = tk.box_lo[k];
+            d.lhi[k] = d.rhi[k] = tk.box_hi[k];
+            d.lclo[k] = d.rclo[k] = tk.clo[k];
+            d.lchi[k] = d.rchi[k] = tk.chi[k];
+        }
+        return;
+    }
+    const int bsel = ba == 0 ? bb[0] : (ba == 1 ? bb[1] : bb[2]);
+    const bool left = v && bsel <= bs, right = v && !left;
+    side = left;
+    d.axis = ba;
+    d.split = bs;
+    d.nL = __popc(__ballot_sync(0xffffffffu, left));
+    for (int k = 0; k < 3; ++k) {
+        d.llo[k] = warp_minf(left ? lo[k] : INFINITY);
+        d.lhi[k] = warp_maxf(left ? hi[k] : -INFINITY);
+        d.lclo[k] = warp_minf(left ? cc[k] : INFINITY);
+        d.lchi[k] = warp_maxf(left ? cc[k] : -INFINITY);
+        d.rlo[k] = warp_minf(right ? lo[k] : INFINITY);
+        d.rhi[k] = warp_maxf(right ? hi[k] : -INFINITY);
+        d.rclo[k] = warp_minf(right ? cc[k] : INFINITY);
+        d.rchi[k] = warp_maxf(right ? cc[k] : -INFINITY);
+    }
+    (void)lane;
+}
+
 // one CTA builds the whole subtree of a small task
 // threads of the CTA that builds one small subtree (any multiple of 32): one
 // warp, so the barriers between its node steps cost little (11.0 ms against
@@ -484,7 +587,6 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
         __syncthreads();
         if (sp_now == 0) break;
         if (threadIdx.x == 0) s_tk = stack[--s_sp];
-        bins_init(bins);
         __syncthreads();
         const Task tk = s_tk;
         if (tk.count <= 1) {
@@ -496,6 +598,56 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
             __syncthreads();
             continue;
         }
+        if (MT_BVH_SMALL_THREADS == 32 && tk.count <= 32) {
+            // a triangle per lane: the same decision as binning, without bins or barriers
+            const bool v = threadIdx.x < tk.count;
+            const int p = v ? idx[tk.first + threadIdx.x] : 0;
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, cc[3] = {0.f, 0.f, 0.f};
+            if (v) {
+                const float4 l4 = plo[p], h4 = phi[p], c4 = cen[p];
+                lo[0] = l4.x, lo[1] = l4.y, lo[2] = l4.z;
+                hi[0] = h4.x, hi[1] = h4.y, hi[2] = h4.z;
+                cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z;
+            }
+            int bb[3];
+            Decision d;
+            bool side;
+            decide_small(tk, lo, hi, cc, v, bb, d, side);
+            if (leaf_better(tk, d)) {
+                if (threadIdx.x == 0) {
+                    nodes[tk.node].left = -1;
+                    nodes[tk.node].right = -1;
+                    atomicMax(&counters[3], tk.depth);
+                }
+                continue;
+            }
+            if (d.axis >= 0) {  // stable partition in place: left triangles first, each side in order
+                const unsigned ml = __ballot_sync(0xffffffffu, side), mr = __ballot_sync(0xffffffffu, v && !side);
+                const unsigned lt = (1u << threadIdx.x) - 1u;
+                const int dst = side ? tk.first + __popc(ml & lt) : tk.first + d.nL + __popc(mr & lt);
+                __syncwarp();
+                if (v) idx[dst] = p;
+                __syncwarp();
+            }
+            if (threadIdx.x == 0) {
+                const int base = atomicAdd(&counters[0], 2);
+                Task c[2];
+                make_child_tasks(tk, d, base, nodes, c);
+                if (s_sp + 2 <= SMALL_STACK) {
+                    stack[s_sp++] = c[1];
+                    stack[s_sp++] = c[0];
+                } else {
+                    atomicOr(&counters[4], 1);  // stack overflow: children stay leaves
+                    for (int q = 0; q < 2; ++q) {
+                        nodes[c[q].node].left = -1;
+                        nodes[c[q].node].right = -1;
+                    }
+                }
+            }
+            continue;
+        }
+        bins_init(bins);
+        __syncthreads();
         for (int i = tk.first + threadIdx.x; i < tk.first + tk.count; i += blockDim.x) {
             const int p = idx[i];
             bins_add(bins, plo[p], phi[p], cen[p], tk.clo, tk.chi);
@@ -505,11 +657,7 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
         __syncthreads();
         if (threadIdx.x == 0) {
             const Decision &d = s_dec;
-            const float sa = area_of(tk.box_lo, tk.box_hi);
-            const float split_cost =
-                MT_SAH_CT * sa + area_of(d.llo, d.lhi) * d.nL + area_of(d.rlo, d.rhi) * (tk.count - d.nL);
-            const float leaf_cost = sa * tk.count;
-            s_leaf = tk.count <= 4 && leaf_cost <= split_cost;
+            s_leaf = leaf_better(tk, d);
             if (s_leaf) {
                 nodes[tk.node].left = -1;
                 nodes[tk.node].right = -1;
