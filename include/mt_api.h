@@ -129,8 +129,11 @@ const char *mt_last_error(void);
  * emitter sampling table on the device, and returns a handle in *out.  The
  * emitter table weights triangles by area * mean radiance at creation time and
  * is kept fixed by mt_scene_set_params.  Errors: INVALID_ARGUMENT (NULL
- * pointers, n_tris < 1, non-finite vertices, emitter ranges out of bounds),
- * OUT_OF_MEMORY, CUDA.  Synchronises `stream`. */
+ * pointers, n_tris < 1, non-finite vertices, invalid materials, emitter ranges
+ * out of bounds), OUT_OF_MEMORY, CUDA.  The vertices and materials of scenes
+ * of more than 65,536 triangles are checked on the device after the upload
+ * (the same errors and messages; nothing stays allocated), smaller ones on the
+ * host before any device work.  Synchronises `stream`. */
 mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials,
                           const mt_emitter *emitters, int32_t n_emitters, const mt_camera *camera,
                           const mt_medium *medium, void *stream, mt_scene *out);

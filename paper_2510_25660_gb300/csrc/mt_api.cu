@@ -158,6 +158,22 @@ struct mt_scene_s {
 // ---------------------------------------------------------------------------
 namespace {
 
+// non-finite vertex coordinates and invalid materials (the host checks, on the
+// device): sets *bad
+__global__ void k_check_inputs(const uint32_t *tri_bits, size_t n_floats, const mt_material *m, int n, int *bad) {
+    bool ok = true;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_floats; i += stride)
+        ok &= (__ldg(&tri_bits[i]) & 0x7F800000u) != 0x7F800000u;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n; i += stride) {
+        const mt_material x = m[i];
+        for (int k = 0; k < 3; ++k) ok &= x.albedo[k] >= 0.f && x.albedo[k] < INFINITY;
+        ok &= x.type == MT_LAMBERT || x.type == MT_GGX_CONDUCTOR;
+        ok &= x.type != MT_GGX_CONDUCTOR || (x.roughness > 0.f && x.roughness <= 1.f);
+    }
+    if (!ok) atomicOr(bad, 1);
+}
+
 __global__ void k_pack_mats(const mt_material *m, int n, float4 *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const mt_material a = m[i];
@@ -410,7 +426,7 @@ const char *mt_last_error(void) { return mt::get_error(); }
 
 static mt_status scene_create_impl(const float *tris, int64_t n, const mt_material *mats, const mt_emitter *ems,
                                    int32_t n_em, const mt_camera *cam, const mt_medium *med, cudaStream_t st,
-                                   mt_scene_s *sc) {
+                                   mt_scene_s *sc, bool check_on_device) {
     int dev = 0;
     MT_CUDA_TRY(cudaGetDevice(&dev));
     MT_CUDA_TRY(cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -427,6 +443,20 @@ static mt_status scene_create_impl(const float *tris, int64_t n, const mt_materi
     MT_CUDA_TRY(cudaMemcpyAsync(d_tris, tris, (size_t)n * 9 * sizeof(float), cudaMemcpyHostToDevice, st));
     MT_CUDA_TRY(cudaMemcpyAsync(d_mats, mats, (size_t)n * sizeof(mt_material), cudaMemcpyHostToDevice, st));
     if (n_em > 0) MT_CUDA_TRY(cudaMemcpyAsync(d_em, ems, (size_t)n_em * sizeof(mt_emitter), cudaMemcpyHostToDevice, st));
+    if (check_on_device) {  // the triangles and materials are checked where they now are, before the build
+        int *dbad, hbad = 0;
+        MT_TRY(al.alloc(&dbad, 1, "input check"));
+        MT_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), st));
+        k_check_inputs<<<grid_for(n * 9, 256, sc->num_sms), 256, 0, st>>>(
+            reinterpret_cast<const uint32_t *>(d_tris), (size_t)n * 9, d_mats, (int)n, dbad);
+        MT_CUDA_TRY(cudaGetLastError());
+        MT_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad) {
+            mt::set_error("non-finite vertex coordinates or invalid materials");
+            return MT_ERR_INVALID_ARGUMENT;
+        }
+    }
     MT_TRY(mt_build_bvh(d_tris, (int32_t)n, st, al, &sc->bvh));
     DevScene &D = sc->dev;
     D.nodes = sc->bvh.nodes;
@@ -571,6 +601,10 @@ static bool parallel_all(int64_t n, F f) {
 }
 }  // extern "C++"
 
+#ifndef MT_HOST_CHECK_TRIS
+#define MT_HOST_CHECK_TRIS (1 << 16)
+#endif
+
 static bool all_finite(const float *v, size_t n) {
     const uint32_t *b = reinterpret_cast<const uint32_t *>(v);
     return parallel_all((int64_t)n, [b](int64_t lo, int64_t hi) {
@@ -595,14 +629,8 @@ static bool materials_ok(const mt_material *m, int64_t n) {
     });
 }
 
-mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials, const mt_emitter *emitters,
-                          int32_t n_emitters, const mt_camera *camera, const mt_medium *medium, void *stream,
-                          mt_scene *out) {
-    MT_CHECK_ARG(out != nullptr, "out is NULL");
-    *out = nullptr;
-    MT_CHECK_ARG(tris != nullptr && materials != nullptr && camera != nullptr, "tris, materials and camera must not be NULL");
-    MT_CHECK_ARG(n_tris >= 1 && n_tris < (1LL << 29), "n_tris = %lld outside [1, 2^29)", (long long)n_tris);
-    MT_CHECK_ARG(n_emitters >= 0 && (n_emitters == 0 || emitters != nullptr), "bad emitter list");
+// vertices finite and materials valid, else INVALID_ARGUMENT naming the first offending triangle
+static mt_status check_tris_materials(const float *tris, int64_t n_tris, const mt_material *materials) {
     // branch-free passes first (vectorisable); the offending element is located only on failure
     if (!all_finite(tris, (size_t)n_tris * 9)) {
         for (int64_t i = 0; i < n_tris * 9; ++i)
@@ -620,6 +648,21 @@ mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *
                          "triangle %lld: GGX roughness must lie in (0, 1]", (long long)i);
         }
     }
+    return MT_OK;
+}
+
+mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *materials, const mt_emitter *emitters,
+                          int32_t n_emitters, const mt_camera *camera, const mt_medium *medium, void *stream,
+                          mt_scene *out) {
+    MT_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MT_CHECK_ARG(tris != nullptr && materials != nullptr && camera != nullptr, "tris, materials and camera must not be NULL");
+    MT_CHECK_ARG(n_tris >= 1 && n_tris < (1LL << 29), "n_tris = %lld outside [1, 2^29)", (long long)n_tris);
+    MT_CHECK_ARG(n_emitters >= 0 && (n_emitters == 0 || emitters != nullptr), "bad emitter list");
+    // scenes of up to MT_HOST_CHECK_TRIS triangles are checked here; larger ones on the device
+    // after the upload (scanning 1.16M triangles on the host took 3.4 ms)
+    const bool check_on_device = n_tris > MT_HOST_CHECK_TRIS;
+    if (!check_on_device) MT_TRY(check_tris_materials(tris, n_tris, materials));
     for (int e = 0; e < n_emitters; ++e) {
         const mt_emitter &em = emitters[e];
         MT_CHECK_ARG(em.type == MT_EMITTER_AREA || em.type == MT_EMITTER_POINT, "emitter %d: unknown type", e);
@@ -649,11 +692,15 @@ mt_status mt_scene_create(const float *tris, int64_t n_tris, const mt_material *
         return MT_ERR_OUT_OF_MEMORY;
     }
     const mt_status st = scene_create_impl(tris, n_tris, materials, emitters, n_emitters, camera, medium,
-                                           (cudaStream_t)stream, sc);
+                                           (cudaStream_t)stream, sc, check_on_device);
     if (st != MT_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
         sc->al.free_all();
         delete sc;
+        if (st == MT_ERR_INVALID_ARGUMENT && check_on_device) {
+            const mt_status where = check_tris_materials(tris, n_tris, materials);  // names the element
+            (void)where;
+        }
         // return the build's pooled temporaries too: a failed creation keeps nothing
         int dev = 0;
         cudaMemPool_t pool;

@@ -125,3 +125,47 @@ def test_axis_parallel_camera_rays(oracle_mod, scenes_mod, form):
     assert ref["steady"][c, c].sum() > 0
     assert np.abs(g[c, c] - ref["steady"][c, c]).max() < 1e-4 * ref["steady"][c, c].max()
     assert _close_per_pixel(g[7:26, 7:26], ref["steady"][7:26, 7:26])
+
+
+@pytest.mark.parametrize("bad", ["nan_vertex", "inf_vertex", "ggx_roughness", "albedo", "type"])
+def test_large_scene_inputs_checked_on_the_device(scenes_mod, bad):
+    """Scenes above 65,536 triangles have their vertices and materials checked on
+    the device after the upload; an invalid one fails with the same error (and
+    the same message, naming the triangle) as the host check of small scenes,
+    and leaves nothing allocated behind."""
+    import torch
+    api = build_and_load()
+    sc = scenes_mod.diff_scene()  # 96,776 triangles
+    assert sc.n_tris > 1 << 16
+    k = sc.n_tris - 1234
+    kw = {}
+    if bad in ("nan_vertex", "inf_vertex"):
+        tris = sc.tris.copy()
+        tris[k, 1, 2] = np.nan if bad == "nan_vertex" else np.inf
+        kw["tris"] = tris
+        msg = f"non-finite vertex coordinate at triangle {k}"
+    elif bad == "ggx_roughness":
+        mt, ro = sc.mtype.copy(), sc.roughness.copy()
+        mt[k], ro[k] = api.MT_GGX_CONDUCTOR, 0.0
+        kw.update(mtype=mt, roughness=ro)
+        msg = f"triangle {k}: GGX roughness"
+    elif bad == "albedo":
+        al = sc.albedo.copy()
+        al[k, 2] = -0.5
+        kw["albedo"] = al
+        msg = f"triangle {k}: bad albedo"
+    else:
+        mt = sc.mtype.copy()
+        mt[k] = 7
+        kw["mtype"] = mt
+        msg = f"triangle {k}: unknown material type 7"
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(api.MtError) as e:
+        api.Scene(dataclasses.replace(sc, **kw))
+    assert e.value.status == api.MT_ERR_INVALID_ARGUMENT
+    assert msg in str(e.value), str(e.value)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    s = api.Scene(sc)  # the valid scene still loads
+    assert s.stats()["n_tris"] == sc.n_tris
