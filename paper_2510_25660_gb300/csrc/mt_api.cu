@@ -146,6 +146,7 @@ struct mt_scene_s {
     size_t wf_stmp_bytes = 0;
     uint32_t wf_sort_cap = 0;
     WfTiming wf_timing;  // stage times of wavefront renders (MT_OPT_STAGE_TIMING)
+    WfSync wf_sync;      // completion flag and events of wavefront renders
     float *delay_buf = nullptr;  // per-triangle scattering-delay means (mt_scene_set_delays)
     int *check_flag = nullptr;   // validation result of mt_scene_set_delays
     unsigned long long *wf_next = nullptr;
@@ -719,6 +720,7 @@ void mt_scene_destroy(mt_scene s) {
     if (s->nlos_graph.exec) cudaGraphExecDestroy(s->nlos_graph.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     mt_wf_timing_free(&s->wf_timing);
+    mt_wf_sync_free(&s->wf_sync);
     s->al.free_all();
     delete s;
 }
@@ -1067,8 +1069,9 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     }
     long long n = 0;
     WfTiming *tm = (cfg.options & MT_OPT_STAGE_TIMING) ? &s->wf_timing : nullptr;
+    MT_TRY(mt_wf_sync_init(&s->wf_sync));
     const mt_status r =
-        mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n, tm);
+        mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n, tm, &s->wf_sync);
     s->launches += n + 1;
     return r;
 }

@@ -146,6 +146,8 @@ struct WfParams {
     uint32_t *sh_perm;             // shadow rays in sorted order (record indices), null = queue order
     void *sort_tmp;
     size_t sort_tmp_bytes;
+    uint32_t *done_flag;  // mapped host word: the setup stage stores done_token in it once the queues
+    uint32_t done_token;  // have drained, else 0 (null: no flag); the token differs per render
 };
 
 size_t mt_wf_sort_bytes(uint32_t P);
@@ -176,5 +178,20 @@ mt_status mt_launch_render(const DevScene &s, const RenderParams &p, const Launc
                            cudaStream_t st);
 mt_status mt_launch_nlos(const DevScene &s, const NlosParams &p, const LaunchCfg &cfg, bool dump, bool counters,
                          cudaStream_t st);
+// Completion checks of wavefront renders without draining the stream: the setup
+// stage writes the "queues drained" flag into mapped host memory and the host
+// reads it after waiting on the event of an iteration a few launches back, so
+// the GPU always has queued work and no copy-engine transfer is involved.
+struct WfSync {
+    uint32_t *done_h = nullptr;  // mapped pinned word (host view)
+    uint32_t *done_d = nullptr;  // its device view
+    cudaEvent_t ev[8] = {};      // end of iteration i: ev[i % 8]
+    uint32_t token = 0;          // of the last render (a render still queued may write its own)
+    bool ready = false;
+};
+mt_status mt_wf_sync_init(WfSync *w);
+void mt_wf_sync_free(WfSync *w);
+
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p, int num_sms, bool dump, bool counters,
-                              cudaStream_t st, long long *launches, WfTiming *timing = nullptr);
+                              cudaStream_t st, long long *launches, WfTiming *timing = nullptr,
+                              WfSync *sync = nullptr);

@@ -296,6 +296,10 @@ __global__ void k_wf_setup(WfParams p, WfIter *it) {
     c[C_SH_CUR] = 0;
     c[C_FIN] = 0;
     c[C_DONE] = (cont + n_new == 0) ? 1u : 0u;
+    if (p.done_flag) {  // read by the host once this iteration's event has completed
+        *(volatile uint32_t *)p.done_flag = c[C_DONE] ? p.done_token : 0u;
+        __threadfence_system();
+    }
     *p.next_path = base + n_new;
 }
 
@@ -1349,6 +1353,27 @@ size_t mt_wf_sort_bytes(uint32_t P) {
     return bytes;
 }
 
+mt_status mt_wf_sync_init(WfSync *w) {
+    if (w->ready) return MT_OK;
+    void *h = nullptr;
+    MT_CUDA_TRY(cudaHostAlloc(&h, 64, cudaHostAllocMapped));
+    w->done_h = (uint32_t *)h;
+    *(volatile uint32_t *)w->done_h = 0u;
+    void *d = nullptr;
+    MT_CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
+    w->done_d = (uint32_t *)d;
+    for (int i = 0; i < 8; ++i) MT_CUDA_TRY(cudaEventCreateWithFlags(&w->ev[i], cudaEventDisableTiming));
+    w->ready = true;
+    return MT_OK;
+}
+
+void mt_wf_sync_free(WfSync *w) {
+    for (int i = 0; i < 8; ++i)
+        if (w->ev[i]) cudaEventDestroy(w->ev[i]);
+    if (w->done_h) cudaFreeHost(w->done_h);
+    *w = WfSync{};
+}
+
 void mt_wf_timing_free(WfTiming *t) {
     for (int i = 0; i < t->n_ev; ++i) cudaEventDestroy(t->ev[i]);
     free(t->ev);
@@ -1398,8 +1423,13 @@ mt_status wf_accumulate(WfTiming *t, unsigned long long n) {
 }  // namespace
 
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms, bool dump, bool counters,
-                              cudaStream_t st, long long *launches, WfTiming *timing) {
+                              cudaStream_t st, long long *launches, WfTiming *timing, WfSync *sync) {
     WfParams p = p0;
+    p.done_flag = sync && sync->ready ? sync->done_d : nullptr;
+    if (p.done_flag) {
+        sync->token = sync->token == 0xFFFFFFFFu ? 1u : sync->token + 1u;  // never 0
+        p.done_token = sync->token;
+    }
     const int grid = num_sms * 8;
     k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.qmode ? nullptr : p.free_q, p.P, p.counters,
                                                                                     p.next_path);
@@ -1549,21 +1579,34 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             std::swap(p.ps_m, p.ps_m_n);
             std::swap(p.ps_sig, p.ps_sig_n);
         }
-        // check for completion every few iterations (one small read-back)
+        // check for completion every few iterations: with the mapped flag, on the event of the
+        // iteration two back (the drained state persists, so a later iteration's flag is as good),
+        // which leaves two iterations queued; else one small read-back that drains the stream
+        if (p.done_flag) MT_CUDA_TRY(cudaEventRecord(sync->ev[iter & 7], st));
         if ((iter & 3) == 3 || iter + 1 == bound) {
             uint32_t done = 0;
-            MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            MT_CUDA_TRY(cudaStreamSynchronize(st));
+            if (p.done_flag && iter >= 2) {
+                MT_CUDA_TRY(cudaEventSynchronize(sync->ev[(iter - 2) & 7]));
+                done = *(volatile uint32_t *)sync->done_h == p.done_token ? 1u : 0u;
+            } else {
+                MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+                MT_CUDA_TRY(cudaStreamSynchronize(st));
+            }
             if (done) {
                 // shadow rays of the last shading pass (none once the queues have drained, but the
                 // fused form never leaves queued rays behind)
                 k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
                 MT_TRY(shadow_tail());
-                return timing ? wf_accumulate(timing, iter + 1) : MT_OK;
+                if (!timing) return MT_OK;
+                MT_CUDA_TRY(cudaStreamSynchronize(st));  // the stage events of every iteration have completed
+                return wf_accumulate(timing, iter + 1);
             }
         }
     }
-    if (timing) MT_TRY(wf_accumulate(timing, bound));
+    if (timing) {
+        MT_CUDA_TRY(cudaStreamSynchronize(st));
+        MT_TRY(wf_accumulate(timing, bound));
+    }
     // one more setup decides whether anything is left
     k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
     *launches += 1;
