@@ -31,7 +31,10 @@ sys.path.insert(0, ROOT)
 # scene creation: one band 153 ms, 2 equal bands 147, 4 equal bands 130.5, 8 equal bands 130.3;
 # with the current kernels: 160/144/128/80 rows 111.0 ms, 144/128/112/80/48 108.4,
 # 128/112/96/80/64/32 108.3, 112/96/96/80/64/40/24 108.9)
-E2E_BANDS = (128 / 512, 112 / 512, 96 / 512, 80 / 512, 64 / 512, 32 / 512)
+# end-to-end step: the frame as two windows (480 and 32 of 512 rows), each copied to the host in bands of
+# 16 rows as its bands finish (mt_render_to_host), so the first window's last copies overlap the second
+E2E_WINDOWS = (480 / 512, 32 / 512)
+E2E_BAND_ROWS = 16
 METRIC = "time-resolved path vertices/s on 1 GB300"  # both arms report the same metric
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = "large static scene: 1,164,296-triangle fBm heightfield + 200 icospheres, 4 area lights, " \
@@ -408,11 +411,10 @@ def main():
         # the step's inputs live in pinned host memory (numpy views of page-locked tensors)
         sc_host = dataclasses.replace(sc, **{k: torch.from_numpy(getattr(sc, k)).pin_memory().numpy()
                                              for k in ("tris", "albedo", "roughness", "mtype")})
-        # the frame renders in row bands (film windows); each finished band is copied to the host on a
-        # second stream while the next band renders
-        band_rows = [int(round(x * f.H)) for x in E2E_BANDS]
-        band_rows[-1] = f.H - sum(band_rows[:-1])
-        bands = len(band_rows)
+        # the frame renders as film windows; within each, every band of E2E_BAND_ROWS rows is copied to
+        # the host on a second stream as soon as its paths have finished (mt_render_to_host)
+        win_rows = [int(round(x * f.H)) for x in E2E_WINDOWS]
+        win_rows[-1] = f.H - sum(win_rows[:-1])
         copy_stream = torch.cuda.Stream()
         e_times, e_verts = [], 0
         for k in range(3):
@@ -421,15 +423,10 @@ def main():
             s2 = api.Scene(sc_host)
             autotune.apply(s2, "render", sc_host, f, spp, depth)
             r0 = 0
-            for rows in band_rows:
-                api.render(s2, rows, f.W, f.T, f.start_opl, f.bin_width, spp, seed, depth,
-                           out=(film[r0:r0 + rows], steady[r0:r0 + rows]), window=(f.H, r0))
-                done = torch.cuda.Event()
-                done.record(stream)
-                copy_stream.wait_event(done)
-                with torch.cuda.stream(copy_stream):
-                    pin[r0:r0 + rows].copy_(film[r0:r0 + rows], non_blocking=True)
-                    pin_s[r0:r0 + rows].copy_(steady[r0:r0 + rows], non_blocking=True)
+            for rows in win_rows:
+                api.render_to_host(s2, rows, f.W, f.T, f.start_opl, f.bin_width, spp, seed, depth,
+                                   pin[r0:r0 + rows], pin_s[r0:r0 + rows], E2E_BAND_ROWS, copy_stream,
+                                   out=(film[r0:r0 + rows], steady[r0:r0 + rows]), window=(f.H, r0))
                 r0 += rows
             torch.cuda.synchronize()
             e_times.append(time.perf_counter() - t0)
@@ -437,9 +434,9 @@ def main():
             del s2
         e2e = {"value": e_verts / min(e_times), "unit": "path vertices/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(film_bytes), "ms_per_step": 1000 * min(e_times),
-               "note": f"scene arrays from pinned host memory (BVH build included) + render in {bands} row "
-                       f"bands of {band_rows} rows (film windows) + each band's film and steady image copied to pinned host memory on a second stream "
-                       f"while the next band renders; best of 3"}
+               "note": f"scene arrays from pinned host memory (BVH build included) + render as film windows of "
+                       f"{win_rows} rows, each with its film and steady image copied to pinned host memory in bands "
+                       f"of {E2E_BAND_ROWS} rows on a second stream as the bands finish (mt_render_to_host); best of 3"}
 
     extras = {}
     if not args.no_extras and (rank == 0 or ws == 1):

@@ -172,12 +172,35 @@ mt_status mt_film_set_window(mt_film film, int32_t frame_H, int32_t row0);
  * form (the default) allocates nothing.  The wavefront form (MT_OPT_WAVEFRONT
  * in mt_set_launch) allocates its path pool on the first wavefront render of a
  * scene that needs a larger pool than the scene holds (a render of more paths,
- * up to the pool size of mt_set_wavefront_pool), synchronises `stream` every
- * few iterations, and refuses to run under stream capture when it would
- * allocate (INVALID_ARGUMENT).  Errors: INVALID_ARGUMENT (spp < 1, max_depth
- * outside [1, 64], film C != 3), OUT_OF_MEMORY (path pool), CUDA. */
+ * up to the pool size of mt_set_wavefront_pool), waits every few iterations
+ * until `stream` has finished the iteration two back (the host stays ahead of
+ * the GPU; nothing is copied for it), and refuses to run under stream capture
+ * when it would allocate (INVALID_ARGUMENT).  Errors: INVALID_ARGUMENT (spp < 1,
+ * max_depth outside [1, 64], film C != 3), OUT_OF_MEMORY (path pool), CUDA. */
 mt_status mt_render(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, int32_t max_depth,
                     uint64_t sample_offset, void *stream);
+
+/* mt_render, with the film and steady image copied to host memory band by band
+ * as the bands finish: host_film [H][W][T][3] and host_steady [H][W][3] (NULL
+ * exactly when the film has no steady image), caller-owned and page-locked for
+ * the copies to overlap the render.  The film's rows are cut into bands of
+ * band_rows rows (the last one shorter); in the wavefront form with its state in
+ * queue order, paths start in pixel order, so the top bands finish first: after
+ * every traversal pass a one-block pass flags each band whose paths have all
+ * finished and whose shadow rays have all been traced, and its copy is queued
+ * on copy_stream behind that iteration; the bands left at the end follow the
+ * render's last stage.  Any other form copies every band after the whole
+ * render.  Returns once every copy is queued (synchronise copy_stream before
+ * reading the host arrays).  As with mt_render, the render clears the film on
+ * `stream`: order it after earlier readers of the film (e.g. the copies of an
+ * earlier call on the same film, by making `stream` wait for copy_stream).
+ * Errors: those of mt_render, and
+ * INVALID_ARGUMENT (NULL host_film, host_steady given without a steady image or
+ * missing with one, band_rows < 1, more than 4096 bands, copy_stream equal to
+ * stream), OUT_OF_MEMORY (per-band counters). */
+mt_status mt_render_to_host(mt_scene scene, mt_film film, int32_t spp, uint64_t seed, int32_t max_depth,
+                            uint64_t sample_offset, int32_t band_rows, float *host_film, float *host_steady,
+                            void *stream, void *copy_stream);
 
 /* Relay-wall impulse responses H(x_l, x_s, t) for all scan pairs in one
  * persistent launch (Sec. 4.5): spp hidden-surface samples per pair (shared by

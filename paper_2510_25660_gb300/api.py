@@ -78,6 +78,7 @@ SIGNATURES = {
     "mt_scene_set_params": (C.c_int, [_P, _P, _P, _P, _P]),
     "mt_film_create": (C.c_int, [_I32, _I32, _I32, _I32, _F, _F, _P, _P, _U32, _P]),
     "mt_render": (C.c_int, [_P, _P, _I32, _U64, _I32, _U64, _P]),
+    "mt_render_to_host": (C.c_int, [_P, _P, _I32, _U64, _I32, _U64, _I32, _P, _P, _P, _P]),
     "mt_render_nlos": (C.c_int, [_P, _P, _P, _I32, _U64, _U64, _P]),
     "mt_render_backward": (C.c_int, [_P, _P, _P, _P, _I32, _U64, _I32, _U64, _P, _P, _P, _P]),
     "mt_sync": (C.c_int, [_P, _P]),
@@ -146,6 +147,18 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _hptr(t):
+    if t is None:
+        return None
+    assert not t.is_cuda and t.is_contiguous() and t.dtype == torch_float32(), "expected a contiguous host float32 tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def torch_float32():
+    import torch
+    return torch.float32
+
+
 # --- mirrors of the C entry points ---------------------------------------------
 def mt_last_error() -> str:
     return load().mt_last_error().decode()
@@ -165,6 +178,12 @@ def mt_film_create(H, W, T, Cc, start, width, d_film, d_steady, flags, out):
 
 def mt_render(scene, film, spp, seed, max_depth, sample_offset, stream):
     return _call("mt_render", scene, film, spp, seed, max_depth, sample_offset, stream)
+
+
+def mt_render_to_host(scene, film, spp, seed, max_depth, sample_offset, band_rows, host_film, host_steady, stream,
+                      copy_stream):
+    return _call("mt_render_to_host", scene, film, spp, seed, max_depth, sample_offset, band_rows, host_film,
+                 host_steady, stream, copy_stream)
 
 
 def mt_render_nlos(scene, film, scan, spp, seed, sample_offset, stream):
@@ -389,6 +408,19 @@ def render(scene: Scene, H, W, T, start, width, spp, seed, max_depth, sample_off
     film, steady = out if out is not None else new_film(H, W, T, 3)
     f = Film(film, steady, start, width, flags, window=window)
     mt_render(scene.h, f.h, spp, seed, max_depth, sample_offset, _stream(stream))
+    return film, steady
+
+
+def render_to_host(scene: Scene, H, W, T, start, width, spp, seed, max_depth, host_film, host_steady, band_rows,
+                   copy_stream, sample_offset=0, flags=0, out=None, stream=None, window=None):
+    """render() into the device film `out` (or a new one), with the film and
+    steady image copied band by band (band_rows rows) into the page-locked host
+    tensors host_film [H,W,T,3] / host_steady [H,W,3] on copy_stream as the
+    bands finish; synchronise copy_stream before reading them."""
+    film, steady = out if out is not None else new_film(H, W, T, 3)
+    f = Film(film, steady, start, width, flags, window=window)
+    mt_render_to_host(scene.h, f.h, spp, seed, max_depth, sample_offset, band_rows, _hptr(host_film),
+                      _hptr(host_steady), _stream(stream), _stream(copy_stream))
     return film, steady
 
 

@@ -147,6 +147,11 @@ struct mt_scene_s {
     uint32_t wf_sort_cap = 0;
     WfTiming wf_timing;  // stage times of wavefront renders (MT_OPT_STAGE_TIMING)
     WfSync wf_sync;      // completion flag and events of wavefront renders
+    WfStreamOut *wf_out = nullptr;  // set by mt_render_to_host for the duration of its render
+    unsigned long long *so_done = nullptr;  // its per-band buffers (so_cap bands)
+    uint32_t *so_mark = nullptr, *so_flag_h = nullptr, *so_flag_d = nullptr;
+    char *so_issued = nullptr;
+    uint32_t so_cap = 0;
     float *delay_buf = nullptr;  // per-triangle scattering-delay means (mt_scene_set_delays)
     int *check_flag = nullptr;   // validation result of mt_scene_set_delays
     unsigned long long *wf_next = nullptr;
@@ -602,6 +607,8 @@ static bool parallel_all(int64_t n, F f) {
 }
 }  // extern "C++"
 
+#define MT_MAX_BANDS 4096  // bands of mt_render_to_host
+
 #ifndef MT_HOST_CHECK_TRIS
 #define MT_HOST_CHECK_TRIS (1 << 16)
 #endif
@@ -721,6 +728,8 @@ void mt_scene_destroy(mt_scene s) {
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     mt_wf_timing_free(&s->wf_timing);
     mt_wf_sync_free(&s->wf_sync);
+    if (s->so_flag_h) cudaFreeHost(s->so_flag_h);
+    free(s->so_issued);
     s->al.free_all();
     delete s;
 }
@@ -1070,8 +1079,8 @@ static mt_status render_wavefront(mt_scene s, mt_film f, const RenderParams &rp,
     long long n = 0;
     WfTiming *tm = (cfg.options & MT_OPT_STAGE_TIMING) ? &s->wf_timing : nullptr;
     MT_TRY(mt_wf_sync_init(&s->wf_sync));
-    const mt_status r =
-        mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n, tm, &s->wf_sync);
+    const mt_status r = mt_launch_wavefront(s->dev, w, s->num_sms, dump, (f->flags & MT_COUNTERS) != 0, st, &n, tm,
+                                            &s->wf_sync, s->wf_out);
     s->launches += n + 1;
     return r;
 }
@@ -1149,6 +1158,74 @@ mt_status mt_render(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t m
                     void *stream) {
     return render_common(s, f, spp, seed, max_depth, sample_offset, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+mt_status mt_render_to_host(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,
+                            uint64_t sample_offset, int32_t band_rows, float *host_film, float *host_steady,
+                            void *stream, void *copy_stream) {
+    MT_CHECK_ARG(s != nullptr && f != nullptr, "scene or film is NULL");
+    MT_CHECK_ARG(host_film != nullptr, "host_film is NULL");
+    MT_CHECK_ARG((host_steady != nullptr) == (f->steady != nullptr),
+                 "host_steady must be given exactly when the film has a steady image");
+    MT_CHECK_ARG(f->C == 3, "path-traced films have C = 3");
+    MT_CHECK_ARG(band_rows >= 1, "band_rows must be >= 1");
+    const uint32_t n_bands = (uint32_t)((f->H + band_rows - 1) / band_rows);
+    MT_CHECK_ARG(n_bands <= MT_MAX_BANDS, "at most %d bands (band_rows too small for %d rows)", MT_MAX_BANDS, f->H);
+    cudaStream_t st = (cudaStream_t)stream, cp = (cudaStream_t)copy_stream;
+    MT_CHECK_ARG(cp != st, "copy_stream must differ from stream");
+    if (n_bands > s->so_cap) {
+        auto &al = s->al;
+        MT_TRY(al.alloc(&s->so_done, n_bands, "streamed output"));
+        MT_TRY(al.alloc(&s->so_mark, n_bands, "streamed output"));
+        if (s->so_flag_h) cudaFreeHost(s->so_flag_h);
+        s->so_flag_h = nullptr;
+        void *h = nullptr, *d = nullptr;
+        MT_CUDA_TRY(cudaHostAlloc(&h, 2 * n_bands * sizeof(uint32_t), cudaHostAllocMapped));
+        memset(h, 0, 2 * n_bands * sizeof(uint32_t));
+        s->so_flag_h = (uint32_t *)h;
+        MT_CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
+        s->so_flag_d = (uint32_t *)d;
+        char *iss = (char *)realloc(s->so_issued, n_bands);
+        if (!iss) {
+            mt::set_error("streamed output: out of host memory");
+            return MT_ERR_OUT_OF_MEMORY;
+        }
+        s->so_issued = iss;
+        s->so_cap = n_bands;
+    }
+    WfStreamOut out;
+    out.copy = cp;
+    out.h_film = host_film;
+    out.h_steady = host_steady;
+    out.d_film = f->film;
+    out.d_steady = f->steady;
+    out.film_row_bytes = (size_t)f->W * f->T * 3 * sizeof(float);
+    out.steady_row_bytes = (size_t)f->W * 3 * sizeof(float);
+    out.H = (uint32_t)f->H;
+    out.band_rows = (uint32_t)band_rows;
+    out.n_bands = n_bands;
+    out.band_done = s->so_done;
+    out.band_mark = s->so_mark;
+    out.flag_h = s->so_flag_h;
+    out.flag_d = s->so_flag_d;
+    out.issued = s->so_issued;
+    s->wf_out = &out;
+    const mt_status r = render_common(s, f, spp, seed, max_depth, sample_offset, 0, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, nullptr, 0, nullptr, st);
+    s->wf_out = nullptr;
+    MT_TRY(r);
+    if (!out.used) {  // another form: every band behind the whole render
+        cudaEvent_t ev;
+        MT_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        MT_CUDA_TRY(cudaEventRecord(ev, st));
+        MT_CUDA_TRY(cudaStreamWaitEvent(cp, ev, 0));
+        cudaEventDestroy(ev);
+        MT_CUDA_TRY(cudaMemcpyAsync(host_film, f->film, (size_t)f->H * out.film_row_bytes, cudaMemcpyDeviceToHost, cp));
+        if (host_steady)
+            MT_CUDA_TRY(cudaMemcpyAsync(host_steady, f->steady, (size_t)f->H * out.steady_row_bytes,
+                                        cudaMemcpyDeviceToHost, cp));
+    }
+    return MT_OK;
 }
 
 mt_status mt_render_polarized(mt_scene s, mt_film f, int32_t spp, uint64_t seed, int32_t max_depth,

@@ -148,6 +148,11 @@ struct WfParams {
     size_t sort_tmp_bytes;
     uint32_t *done_flag;  // mapped host word: the setup stage stores done_token in it once the queues
     uint32_t done_token;  // have drained, else 0 (null: no flag); the token differs per render
+    // streamed output (null: off): finished paths per band of band_rows film rows, bands flagged as
+    // complete, and the mapped host words per band that receive done_token and the flagging iteration
+    unsigned long long *band_done;
+    uint32_t *band_mark, *band_flag;
+    uint32_t band_rows, n_bands;
 };
 
 size_t mt_wf_sort_bytes(uint32_t P);
@@ -192,6 +197,26 @@ struct WfSync {
 mt_status mt_wf_sync_init(WfSync *w);
 void mt_wf_sync_free(WfSync *w);
 
+// Streamed output of a wavefront render (mt_render_to_host): shading counts the
+// finished paths of each band of film rows, a one-block pass after every
+// traversal pass flags the bands whose paths have all finished and whose shadow
+// rays have all been traced, in mapped host memory, and the host queues each
+// flagged band's copy on `copy` behind the event of the iteration that flagged
+// it; the bands left at the end are copied behind the render's last stage.
+struct WfStreamOut {
+    cudaStream_t copy = nullptr;
+    float *h_film = nullptr, *h_steady = nullptr;
+    const float *d_film = nullptr, *d_steady = nullptr;
+    size_t film_row_bytes = 0, steady_row_bytes = 0;
+    uint32_t H = 0, band_rows = 0, n_bands = 0;
+    unsigned long long *band_done = nullptr;  // device [n_bands]
+    uint32_t *band_mark = nullptr;            // device [n_bands]
+    uint32_t *flag_h = nullptr, *flag_d = nullptr;  // mapped host [2][n_bands] (host and device views):
+                                                    // the render token of a flagged band, then its iteration
+    char *issued = nullptr;                   // host [n_bands]: copy queued
+    bool used = false;                        // the render streamed its bands
+};
+
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p, int num_sms, bool dump, bool counters,
                               cudaStream_t st, long long *launches, WfTiming *timing = nullptr,
-                              WfSync *sync = nullptr);
+                              WfSync *sync = nullptr, WfStreamOut *out = nullptr);

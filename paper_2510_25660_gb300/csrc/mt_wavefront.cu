@@ -1211,6 +1211,15 @@ __global__ void __launch_bounds__(256, MT_WF_SHADE_MINB) k_wf_shade(const DevSce
             if (DUMP || MEDIA || BWD) p.sh_m[ss] = sh_m;  // read only by these forms' shadow stages
             if (BWD) p.sh_cb[ss] = sh_own;
         }
+        if (!BWD && p.band_done) {  // streamed output: a finished path counts toward its band of film rows
+            const unsigned dm = __ballot_sync(0xffffffffu, done);
+            if (done) {
+                const uint32_t band = (m.x / (uint32_t)p.W - (uint32_t)p.row0) / p.band_rows;
+                const unsigned peers = __match_any_sync(dm, band);
+                if ((threadIdx.x & 31) == __ffs(peers) - 1)
+                    atomicAdd(&p.band_done[band], (unsigned long long)__popc(peers));
+            }
+        }
         (void)valid;
     }
     warp_count(&s.counters[0], verts);
@@ -1334,6 +1343,23 @@ __global__ void __launch_bounds__(256, MT_WF_TRACE_MINB) k_wf_trace(const DevSce
     }
 }
 
+// streamed output: flag the bands whose paths have all finished (by the last
+// shading pass, whose shadow rays the traversal pass before this one traced)
+__global__ void k_wf_bands(const WfParams p, uint32_t iter) {
+    for (uint32_t k = threadIdx.x; k < p.n_bands; k += blockDim.x) {
+        if (p.band_mark[k]) continue;
+        const uint32_t rows = min(p.band_rows, (uint32_t)p.H - k * p.band_rows);
+        const unsigned long long need = (unsigned long long)rows * (unsigned long long)p.W * (unsigned long long)p.spp;
+        if (p.band_done[k] == need) {
+            p.band_mark[k] = 1u;
+            *(volatile uint32_t *)&p.band_flag[p.n_bands + k] = iter;  // the flagging iteration, then
+            __threadfence_system();
+            *(volatile uint32_t *)&p.band_flag[k] = p.done_token;   // this render's token
+        }
+    }
+    __threadfence_system();
+}
+
 __global__ void k_wf_init(uint32_t *free_q, uint32_t P, uint32_t *counters, unsigned long long *next_path) {
     if (free_q)  // slot-indexed pool only
         for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) free_q[i] = i;
@@ -1422,13 +1448,52 @@ mt_status wf_accumulate(WfTiming *t, unsigned long long n) {
 
 }  // namespace
 
+// queue the copies of the bands the host sees flagged (each behind the event of
+// the iteration that flagged it, which the event ring still holds), or, with
+// all_left, of every band not yet queued behind `last`
+static mt_status stream_out_bands(WfStreamOut *out, const WfSync *sync, cudaEvent_t last, bool all_left) {
+    for (uint32_t k = 0; k < out->n_bands; ++k) {
+        if (out->issued[k]) continue;
+        // a band pass of an earlier render still queued writes that render's token, never this one's
+        const bool f = *(volatile uint32_t *)&out->flag_h[k] == sync->token;
+        if (!f && !all_left) continue;
+        const uint32_t it = f ? *(volatile uint32_t *)&out->flag_h[out->n_bands + k] : 0u;
+        MT_CUDA_TRY(cudaStreamWaitEvent(out->copy, f ? sync->ev[it & 7u] : last, 0));
+        const uint32_t r0 = k * out->band_rows, rows = std::min(out->band_rows, out->H - r0);
+        MT_CUDA_TRY(cudaMemcpyAsync((char *)out->h_film + r0 * out->film_row_bytes,
+                                    (const char *)out->d_film + r0 * out->film_row_bytes, rows * out->film_row_bytes,
+                                    cudaMemcpyDeviceToHost, out->copy));
+        if (out->h_steady)
+            MT_CUDA_TRY(cudaMemcpyAsync((char *)out->h_steady + r0 * out->steady_row_bytes,
+                                        (const char *)out->d_steady + r0 * out->steady_row_bytes,
+                                        rows * out->steady_row_bytes, cudaMemcpyDeviceToHost, out->copy));
+        out->issued[k] = 1;
+    }
+    return MT_OK;
+}
+
 mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms, bool dump, bool counters,
-                              cudaStream_t st, long long *launches, WfTiming *timing, WfSync *sync) {
+                              cudaStream_t st, long long *launches, WfTiming *timing, WfSync *sync,
+                              WfStreamOut *out) {
     WfParams p = p0;
     p.done_flag = sync && sync->ready ? sync->done_d : nullptr;
     if (p.done_flag) {
         sync->token = sync->token == 0xFFFFFFFFu ? 1u : sync->token + 1u;  // never 0
         p.done_token = sync->token;
+    }
+    // streamed output: the forward form in queue order with the fused traversal pass
+    const bool streamed = out && p.done_flag && p.qmode && MT_WF_FUSE && !p.bwd && !p.mueller && !dump &&
+                          !(p.dynamic_fetch && !s.has_medium);
+    if (streamed) {
+        for (uint32_t k = 0; k < out->n_bands; ++k) out->issued[k] = 0;
+        MT_CUDA_TRY(cudaMemsetAsync(out->band_done, 0, out->n_bands * sizeof(unsigned long long), st));
+        MT_CUDA_TRY(cudaMemsetAsync(out->band_mark, 0, out->n_bands * sizeof(uint32_t), st));
+        p.band_done = out->band_done;
+        p.band_mark = out->band_mark;
+        p.band_flag = out->flag_d;
+        p.band_rows = out->band_rows;
+        p.n_bands = out->n_bands;
+        out->used = true;
     }
     const int grid = num_sms * 8;
     k_wf_init<<<std::max(1, std::min(grid, (int)((p.P + 255) / 256))), 256, 0, st>>>(p.qmode ? nullptr : p.free_q, p.P, p.counters,
@@ -1501,6 +1566,10 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
         } else {
             if (counters) k_wf_extend<false, true, false><<<grid, 256, 0, st>>>(s, p, qext);
             else k_wf_extend<false, false, false><<<grid, 256, 0, st>>>(s, p, qext);
+        }
+        if (streamed) {
+            k_wf_bands<<<1, 256, 0, st>>>(p, (uint32_t)iter);
+            *launches += 1;
         }
         if (timing) MT_TRY(wf_event(timing, iter, 2, st));
         if (p.mueller) {
@@ -1588,6 +1657,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             if (p.done_flag && iter >= 2) {
                 MT_CUDA_TRY(cudaEventSynchronize(sync->ev[(iter - 2) & 7]));
                 done = *(volatile uint32_t *)sync->done_h == p.done_token ? 1u : 0u;
+                if (streamed) MT_TRY(stream_out_bands(out, sync, nullptr, false));
             } else {
                 MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
                 MT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1597,6 +1667,10 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
                 // fused form never leaves queued rays behind)
                 k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
                 MT_TRY(shadow_tail());
+                if (streamed) {  // the bands not flagged yet, behind the last stage
+                    MT_CUDA_TRY(cudaEventRecord(sync->ev[(iter + 1) & 7], st));
+                    MT_TRY(stream_out_bands(out, sync, sync->ev[(iter + 1) & 7], true));
+                }
                 if (!timing) return MT_OK;
                 MT_CUDA_TRY(cudaStreamSynchronize(st));  // the stage events of every iteration have completed
                 return wf_accumulate(timing, iter + 1);
@@ -1611,6 +1685,10 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
     k_wf_setup<<<1, 1, 0, st>>>(p, p.iter);
     *launches += 1;
     MT_TRY(shadow_tail());
+    if (streamed) {
+        MT_CUDA_TRY(cudaEventRecord(sync->ev[bound & 7], st));
+        MT_TRY(stream_out_bands(out, sync, sync->ev[bound & 7], true));
+    }
     uint32_t done = 0;
     MT_CUDA_TRY(cudaMemcpyAsync(&done, p.counters + C_DONE, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     MT_CUDA_TRY(cudaStreamSynchronize(st));
