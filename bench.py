@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 # scene creation: one band 153 ms, 2 equal bands 147, 4 equal bands 130.5, 8 equal bands 130.3;
 # with the current kernels: 160/144/128/80 rows 111.0 ms, 144/128/112/80/48 108.4,
 # 128/112/96/80/64/32 108.3, 112/96/96/80/64/40/24 108.9)
-# end-to-end step: the frame as two windows (480 and 32 of 512 rows), each copied to the host in bands of
-# 16 rows as its bands finish (mt_render_to_host), so the first window's last copies overlap the second
-E2E_WINDOWS = (480 / 512, 32 / 512)
-E2E_BAND_ROWS = 16
+# end-to-end step: the frame as three windows (472, 32 and 8 of 512 rows), each copied to the host in
+# bands of 8 rows as its bands finish (mt_render_to_host), so a window's last copies overlap the next
+E2E_WINDOWS = (472 / 512, 32 / 512, 8 / 512)
+E2E_BAND_ROWS = 8
 METRIC = "time-resolved path vertices/s on 1 GB300"  # both arms report the same metric
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = "large static scene: 1,164,296-triangle fBm heightfield + 200 icospheres, 4 area lights, " \
