@@ -1648,11 +1648,12 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
             std::swap(p.ps_m, p.ps_m_n);
             std::swap(p.ps_sig, p.ps_sig_n);
         }
-        // check for completion every few iterations: with the mapped flag, on the event of the
+        // check for completion: with the mapped flag every second iteration, on the event of the
         // iteration two back (the drained state persists, so a later iteration's flag is as good),
-        // which leaves two iterations queued; else one small read-back that drains the stream
+        // which leaves two iterations queued and at most three empty ones at the end; else every
+        // fourth, with one small read-back that drains the stream
         if (p.done_flag) MT_CUDA_TRY(cudaEventRecord(sync->ev[iter & 7], st));
-        if ((iter & 3) == 3 || iter + 1 == bound) {
+        if ((p.done_flag ? (iter & 1) == 1 : (iter & 3) == 3) || iter + 1 == bound) {
             uint32_t done = 0;
             if (p.done_flag && iter >= 2) {
                 MT_CUDA_TRY(cudaEventSynchronize(sync->ev[(iter - 2) & 7]));
