@@ -1177,7 +1177,10 @@ mt_status mt_render_to_host(mt_scene s, mt_film f, int32_t spp, uint64_t seed, i
         auto &al = s->al;
         MT_TRY(al.alloc(&s->so_done, n_bands, "streamed output"));
         MT_TRY(al.alloc(&s->so_mark, n_bands, "streamed output"));
-        if (s->so_flag_h) cudaFreeHost(s->so_flag_h);
+        if (s->so_flag_h) {
+            MT_CUDA_TRY(cudaDeviceSynchronize());  // band passes of an earlier render may still write it
+            cudaFreeHost(s->so_flag_h);
+        }
         s->so_flag_h = nullptr;
         void *h = nullptr, *d = nullptr;
         MT_CUDA_TRY(cudaHostAlloc(&h, 2 * n_bands * sizeof(uint32_t), cudaHostAllocMapped));
