@@ -319,7 +319,11 @@ mt_status mt_scene_set_pulse(mt_scene scene, uint32_t shape, float a, float b);
 mt_status mt_scene_stats(mt_scene scene, int64_t *out);
 
 /* Launch configuration used by the next launches of this scene (set by the
- * autotuner; 0 keeps a field at its default):
+ * autotuner; 0 keeps a field at its default), per kind: MT_LAUNCH_RENDER,
+ * MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS (scan-point grids) and
+ * MT_LAUNCH_NLOS_EXHAUSTIVE (laser x sensor grids, whose scene default is 32
+ * sensors per tile with priv_bins = 0: the lanes of a warp take consecutive
+ * sensors and one hidden sample):
  *   threads      threads per CTA (32..256, multiple of 32)
  *   tile         RENDER/BACKWARD: pixels of one image row owned by one warp at
  *                a time; NLOS: scan rows owned by one CTA at a time
@@ -388,7 +392,8 @@ mt_status mt_set_wavefront_pool(mt_scene scene, int64_t max_paths);
 #define MT_OPT_REFILL(k) ((uint32_t)(k) << 8)
 #define MT_LAUNCH_RENDER 0
 #define MT_LAUNCH_BACKWARD 1
-#define MT_LAUNCH_NLOS 2
+#define MT_LAUNCH_NLOS 2            /* scan points (confocal grids) */
+#define MT_LAUNCH_NLOS_EXHAUSTIVE 3 /* laser x sensor grids; default 32 sensors per tile, no privatisation */
 
 void mt_scene_destroy(mt_scene scene);
 void mt_film_destroy(mt_film film);

@@ -26,7 +26,7 @@ MT_LAMBERT, MT_GGX_CONDUCTOR = 0, 1
 MT_EMITTER_AREA, MT_EMITTER_POINT = 0, 1
 MT_UNWARP, MT_ACCUMULATE, MT_PIXEL_CENTER, MT_COUNTERS = 1, 2, 4, 8
 MT_CONFOCAL, MT_EXHAUSTIVE = 0, 1
-MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS = 0, 1, 2
+MT_LAUNCH_RENDER, MT_LAUNCH_BACKWARD, MT_LAUNCH_NLOS, MT_LAUNCH_NLOS_EXHAUSTIVE = 0, 1, 2, 3
 MT_OPT_AGGREGATE, MT_OPT_NO_GRAPH, MT_OPT_WAVEFRONT, MT_OPT_DYNAMIC_FETCH, MT_OPT_WIDE_BVH = 1, 2, 4, 8, 16
 MT_OPT_SORT_RAYS, MT_OPT_STAGE_TIMING, MT_OPT_SORT_SHADOW = 32, 64, 128
 MT_PULSE_DELTA, MT_PULSE_BOX, MT_PULSE_GAUSSIAN, MT_PULSE_EXPONENTIAL = 0, 1, 2, 3

@@ -133,9 +133,13 @@ __global__ void __launch_bounds__(256) k_nlos(const DevScene s, const NlosParams
             nrows = (int)min((long long)p.tile, rows - row0);
         }
         const int work = nrows * p.spp;
+        // the exhaustive grid goes sensor-fastest: the lanes of a warp take consecutive sensors of the
+        // tile and share one hidden sample, so their shadow rays leave the same point y (262 -> 190 ms
+        // at 2-row tiles, 130 ms at 32-row tiles for 16x16 lasers x 64x64 sensors x 1024 samples);
+        // scan points go sample-fastest
         for (int j = threadIdx.x; j < work; j += blockDim.x) {
-            const int r = j / p.spp;
-            const int sj = j - r * p.spp;
+            const int r = exh ? j % nrows : j / p.spp;
+            const int sj = exh ? j / nrows : j - r * p.spp;
             const uint32_t smp = p.sample_offset + (uint32_t)sj;
             conns++;
             float H = 0.f, opl = 0.f;

@@ -67,3 +67,30 @@ def test_graph_replay_and_per_point_loop_agree(nlos, scenes_mod):
         ref = osc.render_nlos(pts[i:i + 1], None, False, T, start, width, 256, 5)
         assert rel_l2(si.cpu().numpy(), ref["steady"]) < 0.01
         assert rel_l2(fi.cpu().numpy(), ref["film"]) < 0.01
+
+
+@pytest.mark.parametrize("cfg", [(256, 2, 0, -1, 0), (256, 6, 0, -1, 1), (128, 64, 0, 0, 0), (256, 5, 0, 1000, 0)])
+def test_exhaustive_launch_configurations_agree(nlos, scenes_mod, cfg):
+    """Exhaustive grids launch with their own configuration kind (default: 32
+    sensors per tile, every splat in global memory, lanes sensor-fastest):
+    tiles that do or do not divide the sensors, shared-memory histograms of
+    every bin or of part of them, and warp aggregation give the default's film;
+    the scan-point kind's configuration does not apply to them."""
+    import torch
+    api, sc, s, osc = nlos
+    T, start, width = 4096, 0.0, 0.003
+    L = torch.from_numpy(scenes_mod.wall_grid(3, 3)).cuda()
+    S = torch.from_numpy(scenes_mod.wall_grid(7, 7)).cuda()
+    ref, ref_s = [x.clone() for x in api.render_nlos(s, L, S, api.MT_EXHAUSTIVE, T, start, width, 256, 3)]
+    threads, tile, cps, priv, agg = cfg
+    s.set_launch(api.MT_LAUNCH_NLOS, 32, 1, 0, 0, 0)  # scan-point kind only: no effect here
+    s.set_launch(api.MT_LAUNCH_NLOS_EXHAUSTIVE, threads, tile, cps, priv, api.MT_OPT_AGGREGATE if agg else 0)
+    try:
+        f, st = api.render_nlos(s, L, S, api.MT_EXHAUSTIVE, T, start, width, 256, 3)
+        s.sync()
+    finally:
+        s.set_launch(api.MT_LAUNCH_NLOS)
+        s.set_launch(api.MT_LAUNCH_NLOS_EXHAUSTIVE, 256, 32, 0, 0, 0)
+    assert ref.abs().max() > 0
+    assert rel_l2(f.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    assert rel_l2(st.cpu().numpy(), ref_s.cpu().numpy()) < 1e-5
