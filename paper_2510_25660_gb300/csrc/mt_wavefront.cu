@@ -232,7 +232,20 @@ __device__ __forceinline__ void em_grad_flush(const WfParams &p, const float *em
 // suffix sums over the vertex records turn the per-vertex sums of g * C into
 // the albedo and medium-albedo gradients (Sec. 4.4 path replay), then the slot
 // returns to the free stack.
+// Scenes of at most MT_FIN_SMEM_TRIS triangles sum the albedo gradients of a CTA
+// in shared memory and add them to global memory once: on a 36-triangle scene
+// every vertex of a warp adds to the same few entries, whose global atomics
+// then serialise (38.9 ms of a 101-ms backward pass in a medium).
+#ifndef MT_FIN_SMEM_TRIS
+#define MT_FIN_SMEM_TRIS 4096
+#endif
 __global__ void __launch_bounds__(256) k_wf_finalize(const DevScene s, const WfParams p) {
+    extern __shared__ float s_galb[];  // [3 n_tris] when n_tris <= MT_FIN_SMEM_TRIS
+    const bool smem = s.n_tris <= MT_FIN_SMEM_TRIS;
+    if (smem) {
+        for (int k = threadIdx.x; k < 3 * s.n_tris; k += blockDim.x) s_galb[k] = 0.f;
+        __syncthreads();
+    }
     const uint32_t n = p.counters[C_FIN];
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t n_round = ((n + 31u) / 32u) * 32u;
@@ -251,7 +264,7 @@ __global__ void __launch_bounds__(256) k_wf_finalize(const DevScene s, const WfP
                 const int tri = __float_as_int(a.w);
                 if (tri >= 0) {
                     if (gi.x != 0.f || gi.y != 0.f || gi.z != 0.f) {
-                        float *g = p.galb + (size_t)tri * 3;
+                        float *g = smem ? s_galb + 3 * tri : p.galb + (size_t)tri * 3;
                         atomicAdd(g, gi.x);
                         atomicAdd(g + 1, gi.y);
                         atomicAdd(g + 2, gi.z);
@@ -267,6 +280,11 @@ __global__ void __launch_bounds__(256) k_wf_finalize(const DevScene s, const WfP
     }
     for (int o = 16; o > 0; o >>= 1) gm += __shfl_xor_sync(0xffffffffu, gm, o);
     if ((threadIdx.x & 31) == 0 && gm != 0.f && p.gmed) atomicAdd(p.gmed, gm);
+    if (smem) {  // the CTA's sums, once
+        __syncthreads();
+        for (int k = threadIdx.x; k < 3 * s.n_tris; k += blockDim.x)
+            if (s_galb[k] != 0.f) atomicAdd(&p.galb[k], s_galb[k]);
+    }
 }
 
 template <typename T>
@@ -1607,7 +1625,7 @@ mt_status mt_launch_wavefront(const DevScene &s, const WfParams &p0, int num_sms
                 if (counters) k_wf_shadow<false, true, false, false, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
                 else k_wf_shadow<false, false, false, false, true><<<grid, 256, 0, st>>>(s, p, C_SHADOW);
             }
-            k_wf_finalize<<<grid, 256, 0, st>>>(s, p);
+            k_wf_finalize<<<grid, 256, s.n_tris <= MT_FIN_SMEM_TRIS ? 3 * (size_t)s.n_tris * sizeof(float) : 0, st>>>(s, p);
             *launches += 1;
         } else if (dyn) {
             if (counters) k_wf_trace_dyn<true, true><<<grid, 256, 0, st>>>(s, p, qa);
