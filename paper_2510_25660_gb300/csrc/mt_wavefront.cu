@@ -352,13 +352,7 @@ __global__ void __launch_bounds__(256) k_wf_generate(const DevScene s, const WfP
         st_pair<MT_WF_V8_GEN>(&p.o[slot], &p.d[slot], make_float4(s.cam_o.x, s.cam_o.y, s.cam_o.z, 0.f),
                 make_float4(d.x, d.y, d.z, 0.f));
         if (p.sig) p.sig[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p.mueller) {  // P = identity per colour, frame = the camera's horizontal axis
-#pragma unroll
-            for (int e = 0; e < 12; ++e) {
-                const int row = e & 3;
-                p.mueller[(size_t)slot * 12 + e] =
-                    make_float4(row == 0 ? 1.f : 0.f, row == 1 ? 1.f : 0.f, row == 2 ? 1.f : 0.f, row == 3 ? 1.f : 0.f);
-            }
+        if (p.mueller) {  // frame = the camera's horizontal axis (P = identity is implied at depth 1)
             const float3 xf = normalize(s.cam_r - d * dot(s.cam_r, d));
             p.xframe[slot] = make_float4(xf.x, xf.y, xf.z, 0.f);
         }
@@ -594,7 +588,14 @@ __global__ void __launch_bounds__(128) k_wf_shade_pol(const DevScene s, const Wf
             } else {
                 verts++;
                 Mueller P;
-                load_mueller(p, slot, P);
+                if (depth == 1) {  // a camera ray: identity per colour (not stored)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) P.m[c][e] = (e % 5 == 0) ? 1.f : 0.f;
+                } else {
+                    load_mueller(p, slot, P);
+                }
                 const float3 xf = xyz(p.xframe[slot]);
                 const int k = h.x, orig = h.y;
                 const float th = __int_as_float(h.z);
