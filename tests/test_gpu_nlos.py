@@ -94,3 +94,6 @@ def test_exhaustive_launch_configurations_agree(nlos, scenes_mod, cfg):
     assert ref.abs().max() > 0
     assert rel_l2(f.cpu().numpy(), ref.cpu().numpy()) < 1e-5
     assert rel_l2(st.cpu().numpy(), ref_s.cpu().numpy()) < 1e-5
+    with pytest.raises(api.MtError) as e:  # no launch kind beyond the exhaustive one
+        s.set_launch(api.MT_LAUNCH_NLOS_EXHAUSTIVE + 1)
+    assert e.value.status == api.MT_ERR_INVALID_ARGUMENT
