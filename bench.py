@@ -554,9 +554,9 @@ def profile_summary(csv_path, log_path, out_path):
     d = {"kernel": "k_wf_trace (timed form)", "kernel_hash": _kernel_hash(),
          "workload": "one render of the 1,164,296-triangle scene, 256x256 px, 256 spp, max_depth 8, T = 2048, "
                      "benchmark launch configuration (16.7 M paths, 4 fills of the path pool)",
-         "command": "python bench.py --profile trace > gpurun_out/trace.log && ncu --metrics "
+         "command": "python bench.py --profile trace > trace.log && ncu --metrics "
                     "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
-                    "-k regex:k_wf_trace --csv --log-file gpurun_out/trace_dram.csv python bench.py --profile trace",
+                    "-k regex:k_wf_trace --csv --log-file trace_dram.csv python bench.py --profile trace",
          "launches": len(launches), "rays": info["rays"], "dram_bytes_read": rd, "dram_bytes_write": wr,
          "gpu_time_ms_serialised": ms, "dram_bytes_per_ray": (rd + wr) / info["rays"]}
     old = json.load(open(out_path)) if os.path.exists(out_path) else {}

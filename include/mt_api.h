@@ -40,7 +40,7 @@ typedef enum {
     MT_ERR_OUT_OF_MEMORY = 2,
     MT_ERR_CUDA = 3,
     MT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (error word set by a kernel) */
-    MT_ERR_UNSUPPORTED = 5, /* valid request outside what this build implements */
+    MT_ERR_UNSUPPORTED = 5, /* valid request outside what the library implements */
     MT_ERR_INTERNAL = 6
 } mt_status;
 

@@ -954,7 +954,7 @@ static void trace_path(ctx_t *cx, int32_t px, int32_t py, int32_t lp, uint32_t s
         uint32_t ty = s->type[hit];
         double rgh = s->rough[hit];
         vl.tri[depth] = (int32_t)hit;
-        /* next-event estimation (BASELINE estimator: power-heuristic MIS) */
+        /* next-event estimation (with power-heuristic MIS) */
         if (s->n_units > 0 && strat != MO_STRAT_BSDF_ONLY) {
             rng4(seed, pix, smp, (uint32_t)depth, G_NEE, u);
             int64_t un = pick_unit(s, u[0]);
