@@ -4,8 +4,9 @@
 // costs).  Nodes with more than SMALL_T (256) triangles are split level by level,
 // each level binning fixed-size chunks of the node's index range in many CTAs
 // (shared-memory bins merged with global atomics), choosing the split with one
-// warp per node and partitioning stably per chunk.  Smaller nodes are built
-// completely by one CTA each with an explicit stack.  Leaves hold at most four
+// warp per node and partitioning stably per chunk (the partition also gathers
+// the children's centroid bounds).  Smaller nodes are built completely by one
+// CTA each with an explicit stack and CTA-local node ids.  Leaves hold at most four
 // triangles; a node of two to four triangles becomes a leaf when that is
 // cheaper under the SAH.  The binary tree is then collapsed into an 8-wide
 // tree (each wide node takes a binary node's two children and keeps replacing
@@ -43,8 +44,14 @@ constexpr int NB = 32;          // bins per axis
 #endif
 constexpr int SMALL_T = MT_BVH_SMALL_T;  // nodes at or below this size are built by one CTA
 constexpr int CHUNK = 4096;     // index positions binned/partitioned per CTA for large nodes
-constexpr int BIN_INTS = 13;    // count, box lo3 hi3, centroid lo3 hi3 (ordered ints)
-constexpr int SMALL_STACK = 96;
+// bins hold counts and boxes only: the children's centroid bounds come from the partition
+// pass, which reads every centroid anyway (six more atomics per bin and axis otherwise)
+constexpr int BIN_INTS = 7;     // count, box lo3 hi3 (ordered ints)
+constexpr int ilog2_ceil(int v) { return v <= 1 ? 0 : 1 + ilog2_ceil((v + 1) / 2); }
+// a subtree CTA pushes the larger child below the smaller one and pops the smaller first, so an
+// entry waits on the stack only below a descent into a child of at most half its parent's
+// triangles: fewer than ceil(log2 SMALL_T) entries wait below the two just pushed
+constexpr int SMALL_STACK = ilog2_ceil(SMALL_T) + 4;
 
 struct BNode {
     float lo[3], hi[3];
@@ -65,6 +72,7 @@ struct Decision {
     int32_t cntL, cntR; // partition cursors
     float llo[3], lhi[3], rlo[3], rhi[3];   // child boxes
     float lclo[3], lchi[3], rclo[3], rchi[3]; // child centroid bounds
+    int32_t cb[12];  // the same as ordered ints while the partition pass gathers them
 };
 
 struct Chunk {
@@ -108,8 +116,6 @@ __device__ __forceinline__ void bins_init(int *bins) {
         for (int k = 0; k < 3; ++k) {
             b[1 + k] = f2o(INFINITY);
             b[4 + k] = f2o(-INFINITY);
-            b[7 + k] = f2o(INFINITY);
-            b[10 + k] = f2o(-INFINITY);
         }
     }
 }
@@ -127,12 +133,6 @@ __device__ __forceinline__ void bins_add(int *bins, const float4 lo, const float
         atomicMax(&b[4], f2o(hi.x));
         atomicMax(&b[5], f2o(hi.y));
         atomicMax(&b[6], f2o(hi.z));
-        atomicMin(&b[7], f2o(c.x));
-        atomicMin(&b[8], f2o(c.y));
-        atomicMin(&b[9], f2o(c.z));
-        atomicMax(&b[10], f2o(c.x));
-        atomicMax(&b[11], f2o(c.y));
-        atomicMax(&b[12], f2o(c.z));
     }
 }
 
@@ -201,15 +201,6 @@ __device__ __forceinline__ void sweep_axis(const int *bins_axis, float &best_cos
     best_split = split;
 }
 
-__device__ __forceinline__ float warp_minf(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_maxf(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // block-wide exclusive scan of one int per thread; returns the total
 __device__ __forceinline__ int block_exscan(int v, int *s_warp, int &total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -233,6 +224,42 @@ __device__ __forceinline__ int block_exscan(int v, int *s_warp, int &total) {
     total = s_warp[nw - 1];
     __syncthreads();
     return before + x - v;
+}
+
+// centroid bounds of the two sides of a partition, as ordered ints:
+// [0, 3) left lower, [3, 6) left upper, [6, 9) right lower, [9, 12) right upper
+struct SideBounds {
+    int v[12];
+    __device__ __forceinline__ void init() {
+        for (int k = 0; k < 12; ++k) v[k] = f2o((k / 3) & 1 ? -INFINITY : INFINITY);
+    }
+    __device__ __forceinline__ void add(const float4 c, bool left) {
+        const int o[3] = {f2o(c.x), f2o(c.y), f2o(c.z)};
+        const int b = left ? 0 : 6;
+        for (int k = 0; k < 3; ++k) {
+            v[b + k] = min(v[b + k], o[k]);
+            v[b + 3 + k] = max(v[b + 3 + k], o[k]);
+        }
+    }
+    // warp reduction, then lane 0 merges into s (shared, initialised like init())
+    __device__ __forceinline__ void merge_into(int *s) const {
+        for (int k = 0; k < 12; ++k) {
+            const int r = (k / 3) & 1 ? __reduce_max_sync(0xffffffffu, v[k]) : __reduce_min_sync(0xffffffffu, v[k]);
+            if ((threadIdx.x & 31) == 0) {
+                if ((k / 3) & 1) atomicMax(&s[k], r);
+                else atomicMin(&s[k], r);
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ void cb_to_decision(const int *cb, Decision &d) {
+    for (int k = 0; k < 3; ++k) {
+        d.lclo[k] = o2f(cb[k]);
+        d.lchi[k] = o2f(cb[3 + k]);
+        d.rclo[k] = o2f(cb[6 + k]);
+        d.rchi[k] = o2f(cb[9 + k]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -304,8 +331,6 @@ __global__ void k_bin_chunks(const Chunk *chunks, const Task *tasks, const int *
         for (int k = 0; k < 3; ++k) {
             atomicMin(&d[1 + k], b[1 + k]);
             atomicMax(&d[4 + k], b[4 + k]);
-            atomicMin(&d[7 + k], b[7 + k]);
-            atomicMax(&d[10 + k], b[10 + k]);
         }
     }
 }
@@ -317,8 +342,6 @@ __global__ void k_init_bins(int *gbins, int n_tasks) {
         for (int k = 0; k < 3; ++k) {
             b[1 + k] = f2o(INFINITY);
             b[4 + k] = f2o(-INFINITY);
-            b[7 + k] = f2o(INFINITY);
-            b[10 + k] = f2o(-INFINITY);
         }
     }
 }
@@ -352,9 +375,9 @@ __device__ void decide(const int *bins, const Task &tk, Decision *dec) {
             d.lchi[k] = d.rchi[k] = tk.chi[k];
         }
     } else {
-        // lane i holds bin i of the split axis: the children's counts, boxes and centroid bounds
-        // are warp reductions over the bins on either side (min / max, so the same values as a
-        // sequential union)
+        // lane i holds bin i of the split axis: the children's counts and boxes are warp
+        // reductions over the bins on either side (min / max of the ordered ints, so the same
+        // values as a sequential union)
         static_assert(NB == 32, "one bin per lane");
         const int *b = bins + (ba * NB + lane) * BIN_INTS;
         const int cnt = b[0];
@@ -362,17 +385,15 @@ __device__ void decide(const int *bins, const Task &tk, Decision *dec) {
         d.axis = ba;
         d.split = bs;
         d.nL = __reduce_add_sync(0xffffffffu, left ? cnt : 0);
+        const int up = f2o(INFINITY), dn = f2o(-INFINITY);  // an empty bin holds these
         for (int k = 0; k < 3; ++k) {
-            const float blo = has ? o2f(b[1 + k]) : INFINITY, bhi = has ? o2f(b[4 + k]) : -INFINITY;
-            const float bclo = has ? o2f(b[7 + k]) : INFINITY, bchi = has ? o2f(b[10 + k]) : -INFINITY;
-            d.llo[k] = warp_minf(left ? blo : INFINITY);
-            d.lhi[k] = warp_maxf(left ? bhi : -INFINITY);
-            d.lclo[k] = warp_minf(left ? bclo : INFINITY);
-            d.lchi[k] = warp_maxf(left ? bchi : -INFINITY);
-            d.rlo[k] = warp_minf(left ? INFINITY : blo);
-            d.rhi[k] = warp_maxf(left ? -INFINITY : bhi);
-            d.rclo[k] = warp_minf(left ? INFINITY : bclo);
-            d.rchi[k] = warp_maxf(left ? -INFINITY : bchi);
+            const int blo = has ? b[1 + k] : up, bhi = has ? b[4 + k] : dn;
+            d.llo[k] = o2f(__reduce_min_sync(0xffffffffu, left ? blo : up));
+            d.lhi[k] = o2f(__reduce_max_sync(0xffffffffu, left ? bhi : dn));
+            d.rlo[k] = o2f(__reduce_min_sync(0xffffffffu, left ? up : blo));
+            d.rhi[k] = o2f(__reduce_max_sync(0xffffffffu, left ? dn : bhi));
+            d.cb[k] = d.cb[6 + k] = up;  // the centroid bounds are gathered by the partition pass
+            d.cb[3 + k] = d.cb[9 + k] = dn;
         }
     }
     if (lane == 0) *dec = d;
@@ -386,12 +407,17 @@ __global__ void k_partition_chunks(const Chunk *chunks, const Task *tasks, Decis
                                    const float4 *cen, int *tmp) {
     __shared__ int s_warp[32];
     __shared__ int s_base[2];
+    __shared__ int s_cb[12];
     const Chunk ch = chunks[blockIdx.x];
     const Task tk = tasks[ch.task];
     Decision *dec = &decs[ch.task];
     const int axis = dec->axis;
     if (axis < 0) return;
     const int split = dec->split, nL = dec->nL;
+    SideBounds sb;
+    sb.init();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 12; ++k) s_cb[k] = sb.v[k];
     for (int base = ch.begin; base < ch.end; base += blockDim.x) {
         const int i = base + threadIdx.x;
         int p = 0, left = 0;
@@ -401,6 +427,7 @@ __global__ void k_partition_chunks(const Chunk *chunks, const Task *tasks, Decis
             const float4 c = cen[p];
             const float cc = axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
             left = bin_of(cc, tk.clo[axis], tk.chi[axis]) <= split;
+            sb.add(c, left);
         }
         int totL;
         const int rankL = block_exscan(valid && left, s_warp, totL);
@@ -417,6 +444,13 @@ __global__ void k_partition_chunks(const Chunk *chunks, const Task *tasks, Decis
         }
         __syncthreads();
     }
+    sb.merge_into(s_cb);
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int k = threadIdx.x;
+        if ((k / 3) & 1) atomicMax(&dec->cb[k], s_cb[k]);
+        else atomicMin(&dec->cb[k], s_cb[k]);
+    }
 }
 
 __global__ void k_copy_chunks(const Chunk *chunks, const Decision *decs, int *idx, const int *tmp) {
@@ -425,29 +459,30 @@ __global__ void k_copy_chunks(const Chunk *chunks, const Decision *decs, int *id
     for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) idx[i] = tmp[i];
 }
 
+// child s (0 left, 1 right) of task tk under split d, with node id `id`: its task and its node, a leaf
+__device__ __forceinline__ void child_of(const Task &tk, const Decision &d, int s, int id, Task &t, BNode &nd) {
+    t.node = id;
+    t.first = s == 0 ? tk.first : tk.first + d.nL;
+    t.count = s == 0 ? d.nL : tk.count - d.nL;
+    t.depth = tk.depth + 1;
+    for (int k = 0; k < 3; ++k) {
+        t.box_lo[k] = s == 0 ? d.llo[k] : d.rlo[k];
+        t.box_hi[k] = s == 0 ? d.lhi[k] : d.rhi[k];
+        t.clo[k] = s == 0 ? d.lclo[k] : d.rclo[k];
+        t.chi[k] = s == 0 ? d.lchi[k] : d.rchi[k];
+        nd.lo[k] = t.box_lo[k];
+        nd.hi[k] = t.box_hi[k];
+    }
+    nd.left = nd.right = -1;
+    nd.first = t.first;
+    nd.count = t.count;
+}
+
 __device__ void make_child_tasks(const Task &tk, const Decision &d, int base, BNode *nodes, Task *c) {
     for (int s = 0; s < 2; ++s) {
-        Task t;
-        t.node = base + s;
-        t.first = s == 0 ? tk.first : tk.first + d.nL;
-        t.count = s == 0 ? d.nL : tk.count - d.nL;
-        t.depth = tk.depth + 1;
-        for (int k = 0; k < 3; ++k) {
-            t.box_lo[k] = s == 0 ? d.llo[k] : d.rlo[k];
-            t.box_hi[k] = s == 0 ? d.lhi[k] : d.rhi[k];
-            t.clo[k] = s == 0 ? d.lclo[k] : d.rclo[k];
-            t.chi[k] = s == 0 ? d.lchi[k] : d.rchi[k];
-        }
         BNode nd;
-        for (int k = 0; k < 3; ++k) {
-            nd.lo[k] = t.box_lo[k];
-            nd.hi[k] = t.box_hi[k];
-        }
-        nd.left = nd.right = -1;
-        nd.first = t.first;
-        nd.count = t.count;
-        nodes[t.node] = nd;
-        c[s] = t;
+        child_of(tk, d, s, base + s, c[s], nd);
+        nodes[base + s] = nd;
     }
     nodes[tk.node].left = base;
     nodes[tk.node].right = base + 1;
@@ -460,7 +495,9 @@ __global__ void k_children(const Task *tasks, int n_tasks, const Decision *decs,
     const Task tk = tasks[i];
     const int base = atomicAdd(&counters[0], 2);
     Task c[2];
-    make_child_tasks(tk, decs[i], base, nodes, c);
+    Decision d = decs[i];
+    if (d.axis >= 0) cb_to_decision(d.cb, d);
+    make_child_tasks(tk, d, base, nodes, c);
     for (int s = 0; s < 2; ++s) {
         if (c[s].count > SMALL_T) next[atomicAdd(&counters[1], 1)] = c[s];
         else small[atomicAdd(&counters[2], 1)] = c[s];
@@ -480,38 +517,53 @@ __device__ __forceinline__ bool leaf_better(const Task &tk, const Decision &d) {
 // triangles, one triangle per lane of a warp, without bins.  Every split that
 // binning can choose is the largest occupied bin of its left side (equal-cost
 // splits between two occupied bins go to the smallest index), i.e. the bin of
-// some triangle: each lane prices the split at its triangle's bin from the
-// same box unions and in the same operations, and the warp takes the smallest
-// (cost, split), then the first axis of smallest cost, as decide does.  bb
-// returns this lane's bins, side its side of the chosen split (1: left).
+// some triangle: each lane prices the split at its triangle's bin, on all three
+// axes in one pass over the triangles (one shuffle of the three bins packed in
+// one word and six of the box per triangle), from the same box unions and in
+// the same operations, and the warp takes the smallest (cost, split), then the
+// first axis of smallest cost, as decide does.  A lane that priced the chosen
+// split holds the children's boxes.  bb returns this lane's bins, side its side
+// of the chosen split (1: left).
 __device__ void decide_small(const Task &tk, const float lo[3], const float hi[3], const float cc[3], bool v,
                              int bb[3], Decision &d, bool &side) {
-    const int lane = threadIdx.x & 31;
     for (int a = 0; a < 3; ++a) bb[a] = v ? bin_of(cc[a], tk.clo[a], tk.chi[a]) : NB;
+    const int packed = bb[0] | (bb[1] << 6) | (bb[2] << 12);  // bins 0..NB fit six bits
+    int nl[3] = {0, 0, 0};
+    float L[3][6], R[3][6];  // per axis: lower corner, upper corner of the left / right side
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            L[a][k] = R[a][k] = INFINITY;
+            L[a][3 + k] = R[a][3 + k] = -INFINITY;
+        }
+    for (int j = 0; j < tk.count; ++j) {
+        const int pj = __shfl_sync(0xffffffffu, packed, j);
+        float bl[3], bh[3];
+        for (int k = 0; k < 3; ++k) {
+            bl[k] = __shfl_sync(0xffffffffu, lo[k], j);
+            bh[k] = __shfl_sync(0xffffffffu, hi[k], j);
+        }
+        for (int a = 0; a < 3; ++a) {
+            const bool inl = ((pj >> (6 * a)) & 63) <= bb[a];
+            nl[a] += inl ? 1 : 0;
+            for (int k = 0; k < 3; ++k) {
+                if (inl) {
+                    L[a][k] = fminf(L[a][k], bl[k]);
+                    L[a][3 + k] = fmaxf(L[a][3 + k], bh[k]);
+                } else {
+                    R[a][k] = fminf(R[a][k], bl[k]);
+                    R[a][3 + k] = fmaxf(R[a][3 + k], bh[k]);
+                }
+            }
+        }
+    }
     float bc = INFINITY;
     int ba = -1, bs = 0;
     for (int a = 0; a < 3; ++a) {
         const int s = bb[a];
-        int nl = 0;
-        float Ll[3] = {INFINITY, INFINITY, INFINITY}, Lh[3] = {-INFINITY, -INFINITY, -INFINITY};
-        float Rl[3] = {INFINITY, INFINITY, INFINITY}, Rh[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int j = 0; j < tk.count; ++j) {
-            const bool inl = __shfl_sync(0xffffffffu, bb[a], j) <= s;
-            nl += inl ? 1 : 0;
-            for (int k = 0; k < 3; ++k) {
-                const float lj = __shfl_sync(0xffffffffu, lo[k], j), hj = __shfl_sync(0xffffffffu, hi[k], j);
-                if (inl) {
-                    Ll[k] = fminf(Ll[k], lj);
-                    Lh[k] = fmaxf(Lh[k], hj);
-                } else {
-                    Rl[k] = fminf(Rl[k], lj);
-                    Rh[k] = fmaxf(Rh[k], hj);
-                }
-            }
-        }
         float cost = INFINITY;
         int split = v ? s : NB;
-        if (v && s < NB - 1 && nl > 0 && tk.count - nl > 0) cost = split_sah(Ll, Lh, nl, Rl, Rh, tk.count - nl);
+        if (v && s < NB - 1 && nl[a] > 0 && tk.count - nl[a] > 0)
+            cost = split_sah(&L[a][0], &L[a][3], nl[a], &R[a][0], &R[a][3], tk.count - nl[a]);
         for (int o = 16; o > 0; o >>= 1) {
             const float c2 = __shfl_xor_sync(0xffffffffu, cost, o);
             const int s2 = __shfl_xor_sync(0xffffffffu, split, o);
@@ -547,40 +599,94 @@ __device__ void decide_small(const Task &tk, const float lo[3], const float hi[3
     d.axis = ba;
     d.split = bs;
     d.nL = __popc(__ballot_sync(0xffffffffu, left));
-    for (int k = 0; k < 3; ++k) {
-        d.llo[k] = warp_minf(left ? lo[k] : INFINITY);
-        d.lhi[k] = warp_maxf(left ? hi[k] : -INFINITY);
-        d.lclo[k] = warp_minf(left ? cc[k] : INFINITY);
-        d.lchi[k] = warp_maxf(left ? cc[k] : -INFINITY);
-        d.rlo[k] = warp_minf(right ? lo[k] : INFINITY);
-        d.rhi[k] = warp_maxf(right ? hi[k] : -INFINITY);
-        d.rclo[k] = warp_minf(right ? cc[k] : INFINITY);
-        d.rchi[k] = warp_maxf(right ? cc[k] : -INFINITY);
+    // the lowest lane that priced (ba, bs): its unions are the children's boxes
+    const int src = __ffs(__ballot_sync(0xffffffffu, v && bsel == bs)) - 1;
+    for (int k = 0; k < 6; ++k) {
+        const float l = ba == 0 ? L[0][k] : (ba == 1 ? L[1][k] : L[2][k]);
+        const float r = ba == 0 ? R[0][k] : (ba == 1 ? R[1][k] : R[2][k]);
+        const float lv = __shfl_sync(0xffffffffu, l, src), rv = __shfl_sync(0xffffffffu, r, src);
+        if (k < 3) {
+            d.llo[k] = lv;
+            d.rlo[k] = rv;
+        } else {
+            d.lhi[k - 3] = lv;
+            d.rhi[k - 3] = rv;
+        }
     }
-    (void)lane;
+    // centroid bounds of either side: reductions over ordered ints
+    for (int k = 0; k < 3; ++k) {
+        const int o = f2o(cc[k]);
+        d.lclo[k] = o2f(__reduce_min_sync(0xffffffffu, left ? o : f2o(INFINITY)));
+        d.lchi[k] = o2f(__reduce_max_sync(0xffffffffu, left ? o : f2o(-INFINITY)));
+        d.rclo[k] = o2f(__reduce_min_sync(0xffffffffu, right ? o : f2o(INFINITY)));
+        d.rchi[k] = o2f(__reduce_max_sync(0xffffffffu, right ? o : f2o(-INFINITY)));
+    }
 }
 
-// one CTA builds the whole subtree of a small task
-// threads of the CTA that builds one small subtree (any multiple of 32): one
-// warp, so the barriers between its node steps cost little (11.0 ms against
-// 12.8 ms at 128 threads for the 1.16M-triangle scene; the same tree)
+// One CTA builds the whole subtree of a small task, node by node with an
+// explicit stack.  The nodes below the task's root get local ids in the CTA's
+// own region of `loc` (two slots per triangle of the task: a subtree of c
+// triangles has at most 2c - 2 nodes below its root, since every split leaves
+// both sides non-empty) and move to `nodes` with one allocation once the
+// subtree is complete, so no node step waits on a global atomic.
+// Threads of the CTA (any multiple of 32): one warp, so the barriers between
+// its node steps cost little (11.0 ms against 12.8 ms at 128 threads for the
+// 1.16M-triangle scene; the same tree).
 #ifndef MT_BVH_SMALL_THREADS
 #define MT_BVH_SMALL_THREADS 32
 #endif
-__global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task *small, BNode *nodes, int *idx, int *tmp,
-                                                     const float4 *plo, const float4 *phi, const float4 *cen,
-                                                     int *counters) {
+__global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task *small, BNode *nodes, BNode *loc_all,
+                                                                      int *idx, int *tmp, const float4 *plo,
+                                                                      const float4 *phi, const float4 *cen,
+                                                                      int *counters) {
     __shared__ int bins[3 * NB * BIN_INTS];
     __shared__ Task stack[SMALL_STACK];
-    __shared__ int s_sp;
+    __shared__ int s_sp, s_next, s_link[2], s_maxd, s_base;
     __shared__ Decision s_dec;
     __shared__ int s_leaf;
     __shared__ int s_warp[32];
     __shared__ Task s_tk;
+    const Task root = small[blockIdx.x];
+    BNode *loc = loc_all + 2 * (size_t)root.first;
+    const int cap = 2 * root.count - 2;
     if (threadIdx.x == 0) {
-        stack[0] = small[blockIdx.x];
+        stack[0] = root;
         s_sp = 1;
+        s_next = 0;
+        s_link[0] = s_link[1] = -1;
+        s_maxd = root.depth;
     }
+    // thread 0: the two children of tk under split d, written as leaves with the next local ids,
+    // linked to tk and pushed larger first (the smaller is built first)
+    auto split_node = [&](const Task &tk, const Decision &d) {
+        if (s_next + 2 > cap) {  // unreachable: both sides of a split are non-empty
+            atomicOr(&counters[4], 2);
+            return;
+        }
+        const int lb = s_next;
+        s_next = lb + 2;
+        Task c[2];
+        for (int q = 0; q < 2; ++q) {
+            BNode nd;
+            child_of(tk, d, q, lb + q, c[q], nd);
+            loc[lb + q] = nd;
+        }
+        if (tk.depth == root.depth) {  // the root keeps its global id
+            s_link[0] = lb;
+            s_link[1] = lb + 1;
+        } else {
+            loc[tk.node].left = lb;
+            loc[tk.node].right = lb + 1;
+        }
+        s_maxd = max(s_maxd, tk.depth + 1);
+        if (s_sp + 2 <= SMALL_STACK) {
+            const int big = c[1].count >= c[0].count ? 1 : 0;
+            stack[s_sp++] = c[big];
+            stack[s_sp++] = c[1 - big];
+        } else {
+            atomicOr(&counters[4], 1);  // stack overflow: the children stay leaves
+        }
+    };
     for (;;) {
         __syncthreads();
         const int sp_now = s_sp;  // every thread reads before thread 0 pops
@@ -589,15 +695,7 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
         if (threadIdx.x == 0) s_tk = stack[--s_sp];
         __syncthreads();
         const Task tk = s_tk;
-        if (tk.count <= 1) {
-            if (threadIdx.x == 0) {
-                nodes[tk.node].left = -1;
-                nodes[tk.node].right = -1;
-                atomicMax(&counters[3], tk.depth);
-            }
-            __syncthreads();
-            continue;
-        }
+        if (tk.count <= 1) continue;  // a leaf: its node was written as one
         if (MT_BVH_SMALL_THREADS == 32 && tk.count <= 32) {
             // a triangle per lane: the same decision as binning, without bins or barriers
             const bool v = threadIdx.x < tk.count;
@@ -613,14 +711,7 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
             Decision d;
             bool side;
             decide_small(tk, lo, hi, cc, v, bb, d, side);
-            if (leaf_better(tk, d)) {
-                if (threadIdx.x == 0) {
-                    nodes[tk.node].left = -1;
-                    nodes[tk.node].right = -1;
-                    atomicMax(&counters[3], tk.depth);
-                }
-                continue;
-            }
+            if (leaf_better(tk, d)) continue;
             if (d.axis >= 0) {  // stable partition in place: left triangles first, each side in order
                 const unsigned ml = __ballot_sync(0xffffffffu, side), mr = __ballot_sync(0xffffffffu, v && !side);
                 const unsigned lt = (1u << threadIdx.x) - 1u;
@@ -629,21 +720,7 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
                 if (v) idx[dst] = p;
                 __syncwarp();
             }
-            if (threadIdx.x == 0) {
-                const int base = atomicAdd(&counters[0], 2);
-                Task c[2];
-                make_child_tasks(tk, d, base, nodes, c);
-                if (s_sp + 2 <= SMALL_STACK) {
-                    stack[s_sp++] = c[1];
-                    stack[s_sp++] = c[0];
-                } else {
-                    atomicOr(&counters[4], 1);  // stack overflow: children stay leaves
-                    for (int q = 0; q < 2; ++q) {
-                        nodes[c[q].node].left = -1;
-                        nodes[c[q].node].right = -1;
-                    }
-                }
-            }
+            if (threadIdx.x == 0) split_node(tk, d);
             continue;
         }
         bins_init(bins);
@@ -655,21 +732,15 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
         __syncthreads();
         if (threadIdx.x < 32) decide(bins, tk, &s_dec);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const Decision &d = s_dec;
-            s_leaf = leaf_better(tk, d);
-            if (s_leaf) {
-                nodes[tk.node].left = -1;
-                nodes[tk.node].right = -1;
-                atomicMax(&counters[3], tk.depth);
-            }
-        }
+        if (threadIdx.x == 0) s_leaf = leaf_better(tk, s_dec);
         __syncthreads();
         if (s_leaf) continue;
         const int axis = s_dec.axis;
         if (axis >= 0) {
             const int split = s_dec.split, nL = s_dec.nL;
             int cL = 0, cR = 0;
+            SideBounds sb;
+            sb.init();
             for (int base = tk.first; base < tk.first + tk.count; base += blockDim.x) {
                 const int i = base + threadIdx.x;
                 const bool valid = i < tk.first + tk.count;
@@ -679,6 +750,7 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
                     const float4 c = cen[p];
                     const float cc = axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
                     left = bin_of(cc, tk.clo[axis], tk.chi[axis]) <= split;
+                    sb.add(c, left);
                 }
                 int totL;
                 const int rankL = block_exscan(valid && left, s_warp, totL);
@@ -690,26 +762,37 @@ __global__ void __launch_bounds__(MT_BVH_SMALL_THREADS) k_build_small(const Task
                 cL += totL;
                 cR += nvalid - totL;
             }
+            sb.merge_into(s_dec.cb);  // decide initialised s_dec.cb
             __syncthreads();
             for (int i = tk.first + threadIdx.x; i < tk.first + tk.count; i += blockDim.x) idx[i] = tmp[i];
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            const int base = atomicAdd(&counters[0], 2);
-            Task c[2];
-            make_child_tasks(tk, s_dec, base, nodes, c);
-            if (s_sp + 2 <= SMALL_STACK) {
-                stack[s_sp++] = c[1];
-                stack[s_sp++] = c[0];
-            } else {
-                atomicOr(&counters[4], 1);  // stack overflow: children stay leaves
-                for (int s = 0; s < 2; ++s) {
-                    nodes[c[s].node].left = -1;
-                    nodes[c[s].node].right = -1;
-                }
-            }
+            if (s_dec.axis >= 0) cb_to_decision(s_dec.cb, s_dec);
+            split_node(tk, s_dec);
         }
         __syncthreads();
+    }
+    // one allocation for the subtree, then its nodes move to their global ids
+    if (threadIdx.x == 0) {
+        const int u = s_next;
+        const int base = u > 0 ? atomicAdd(&counters[0], u) : 0;
+        if (u > 0) {
+            nodes[root.node].left = base + s_link[0];
+            nodes[root.node].right = base + s_link[1];
+        }
+        atomicMax(&counters[3], s_maxd);
+        s_base = base;
+    }
+    __syncthreads();
+    const int u = s_next, base = s_base;
+    for (int i = threadIdx.x; i < u; i += blockDim.x) {
+        BNode nd = loc[i];
+        if (nd.left >= 0) {
+            nd.left += base;
+            nd.right += base;
+        }
+        nodes[base + i] = nd;
     }
 }
 
@@ -849,10 +932,14 @@ __global__ void k_emit_root_leaf(const BNode *nodes, uint4 *out, float qlx, floa
 // One thread per wide node of the current level: collapse the binary subtree
 // below binary node wsrc[w] into up to eight children, give the children
 // slots by position, quantise their boxes, allocate the internal children
-// (wsrc of the next level) and the leaf triangles, record the new triangle
-// order in perm and point the binary leaves at it.
-__global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end, int *wsrc, uint4 *wnodes,
-                                int *wcount, int *perm, int e_min) {
+// (wsrc of the next level), place the leaf triangles, record the new triangle
+// order in perm and point the binary leaves at it.  The triangles of every
+// wide subtree occupy one range in depth-first order: the subtree of wide node
+// w starts at wstart[w] with the leaf children of w (in slot order), followed
+// by the subtrees of its internal children in slot order, so the order does
+// not depend on which thread runs first.
+__global__ void k_wide_collapse(BNode *nodes, const int *idx, int n_tris, int begin, int end, int *wsrc, int *wstart,
+                                uint4 *wnodes, int *wcount, int *perm, int e_min) {
     for (int w = begin + blockIdx.x * blockDim.x + threadIdx.x; w < end; w += gridDim.x * blockDim.x) {
         const int b = wsrc[w];
         int ch[8];
@@ -939,7 +1026,9 @@ __global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end
             else n_leaf_tris += max(0, nodes[ch[i]].count);
         }
         const int base = n_int ? atomicAdd(&wcount[0], n_int) : 0;
-        const int tbase = n_leaf_tris ? atomicAdd(&wcount[1], n_leaf_tris) : 0;
+        const int tbase = wstart[w];
+        if (n_leaf_tris) atomicAdd(&wcount[1], n_leaf_tris);  // the host checks that all triangles are placed
+        int tnext = tbase + n_leaf_tris;  // the first internal child's subtree follows the leaf triangles
         uint32_t imask = 0, meta[2] = {0, 0}, ql[3][2] = {{0, 0}, {0, 0}, {0, 0}}, qh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         int r_int = 0, off = 0;
         for (int q = 0; q < 8; ++q) {
@@ -964,8 +1053,14 @@ __global__ void k_wide_collapse(BNode *nodes, const int *idx, int begin, int end
             }
             if (cn.left >= 0) {
                 imask |= 1u << q;
+                wstart[base + r_int] = tnext;
+                tnext += cn.count;
                 wsrc[base + r_int++] = c;
             } else {
+                if (tbase < 0 || tbase + off + cn.count > n_tris) {  // inconsistent counts: the host check fails
+                    atomicAdd(&wcount[1], n_tris + 1);
+                    continue;
+                }
                 meta[h] |= (0x80u | ((uint32_t)(cn.count - 1) << 5) | (uint32_t)off) << sh;
                 for (int j = 0; j < cn.count; ++j) perm[tbase + off + j] = idx[cn.first + j];
                 cn.first = tbase + off;
@@ -1169,7 +1264,11 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
             MT_CUDA_TRY(cudaStreamSynchronize(st));
         }
     }
-    if (hc[2] > 0) k_build_small<<<hc[2], MT_BVH_SMALL_THREADS, 0, st>>>(small, nodes, idx, tmp, plo, phi, cen, counters);
+    if (hc[2] > 0) {
+        BNode *loc;
+        MT_TRY(tmpal.alloc(&loc, (size_t)2 * n, "bvh subtree nodes"));
+        k_build_small<<<hc[2], MT_BVH_SMALL_THREADS, 0, st>>>(small, nodes, loc, idx, tmp, plo, phi, cen, counters);
+    }
     MT_CUDA_TRY(cudaGetLastError());
     MT_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
     MT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1200,10 +1299,11 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
     // 8-wide tree, level by level; the leaves' triangle ranges move to the
     // wide order (perm) before the binary nodes are written
     {
-        int *wsrc, *wcount, *perm, *dbad;
+        int *wsrc, *wstart, *wcount, *perm, *dbad;
         uint4 *wtmp;
         const int max_w = std::max(1, n_build);
         MT_TRY(tmpal.alloc(&wsrc, max_w, "wide bvh sources"));
+        MT_TRY(tmpal.alloc(&wstart, max_w, "wide bvh triangle ranges"));
         MT_TRY(tmpal.alloc(&wtmp, (size_t)MT_WIDE_WORDS * max_w, "wide bvh nodes"));
         MT_TRY(tmpal.alloc(&wcount, 2, "wide bvh counters"));
         MT_TRY(tmpal.alloc(&perm, n, "wide bvh order"));
@@ -1211,6 +1311,7 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
         const int hw[2] = {1, 0}, zero = 0;
         MT_CUDA_TRY(cudaMemcpyAsync(wcount, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
         MT_CUDA_TRY(cudaMemcpyAsync(wsrc, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        MT_CUDA_TRY(cudaMemcpyAsync(wstart, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
         // smallest step: 2^-16 of the largest scene extent, far above the
         // rounding of the slab distances
         double mxe = 0.0;
@@ -1220,7 +1321,7 @@ mt_status mt_build_bvh(const float *d_tris, int32_t n, cudaStream_t st, mt::Allo
         int begin = 0, end = 1, levels = 0, hcount[2] = {1, 0};
         while (begin < end) {
             const int nl = end - begin;
-            k_wide_collapse<<<std::min(4096, (nl + 127) / 128), 128, 0, st>>>(nodes, idx, begin, end, wsrc, wtmp,
+            k_wide_collapse<<<std::min(4096, (nl + 127) / 128), 128, 0, st>>>(nodes, idx, n, begin, end, wsrc, wstart, wtmp,
                                                                               wcount, perm, e_min);
             MT_CUDA_TRY(cudaGetLastError());
             MT_CUDA_TRY(cudaMemcpyAsync(hcount, wcount, sizeof(hcount), cudaMemcpyDeviceToHost, st));
