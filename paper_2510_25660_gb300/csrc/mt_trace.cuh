@@ -209,6 +209,22 @@ struct TraceCnt {
     uint32_t nodes, tris;  // bytes of BVH nodes fetched, triangle records tested
 };
 
+// MT_LEAF_STEP bit 0 (closest hit), bit 1 (any hit): a leaf's triangles are
+// tested one per iteration of the traversal loop (the leaf reference advances
+// to the next triangle: first + 1, count - 1), so that in a warp whose lanes
+// meet leaves at different steps the diverging leaf work of one step is one
+// triangle test instead of up to four, while the other lanes go on with their
+// nodes.  The nodes visited, their order and the triangles tested are the
+// same, so are the hits.  Measured on the 1.16M-triangle scene (fused
+// traversal pass of the 512x512x256-spp render): 67.36 ms with the leaf's
+// triangles in an inner loop, 66.54 (closest hit only), 66.24 (any hit
+// only), 65.35 ms (both).
+#ifndef MT_LEAF_STEP
+#define MT_LEAF_STEP 3
+#endif
+#define MT_LEAF_MORE 0x60000000u                // count - 1 field of a leaf reference
+#define MT_LEAF_NEXT (1u - 0x20000000u)         // first + 1, count - 1 (mod 2^32)
+
 // MT_SMEM_STACK > 0: the first MT_SMEM_STACK entries of each thread's traversal
 // stack live in shared memory (CTAs of at most 256 threads), deeper ones in
 // local memory
@@ -257,6 +273,27 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
             if (h0) { ref = b.z; continue; }
             if (h1) { ref = b.w; continue; }
         } else {
+#if MT_LEAF_STEP & 1
+            // one triangle of the leaf per iteration; the rest stay in `ref`
+            const int k = (int)(ref & 0x1FFFFFFFu);
+            const float4 p0 = ldg_keep(&s.tris[3 * k]);
+            const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+            const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
+            if (CNT) cnt.tris++;
+            float t;
+            if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) {
+                const int id = __float_as_int(p0.w);
+                if (t < tbest || (t == tbest && id < best_id)) {
+                    tbest = t;
+                    best_k = k;
+                    best_id = id;
+                }
+            }
+            if (ref & MT_LEAF_MORE) {
+                ref += MT_LEAF_NEXT;
+                continue;
+            }
+#else
             const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
             for (int k = first; k < first + n; ++k) {
                 const float4 p0 = ldg_keep(&s.tris[3 * k]);
@@ -273,6 +310,7 @@ __device__ __forceinline__ int trace_closest_simple(const DevScene &s, const Ray
                     }
                 }
             }
+#endif
         }
         // pop the next entry whose entry distance does not exceed the best hit
         for (;;) {
@@ -331,6 +369,19 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
             if (h0) { ref = b.z; continue; }
             if (h1) { ref = b.w; continue; }
         } else {
+#if MT_LEAF_STEP & 2
+            const int k = (int)(ref & 0x1FFFFFFFu);
+            const float4 p0 = ldg_keep(&s.tris[3 * k]);
+            const float4 p1 = ldg_keep(&s.tris[3 * k + 1]);
+            const float4 p2 = ldg_keep(&s.tris[3 * k + 2]);
+            if (CNT) cnt.tris++;
+            float t;
+            if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) return true;
+            if (ref & MT_LEAF_MORE) {
+                ref += MT_LEAF_NEXT;
+                continue;
+            }
+#else
             const int first = (int)(ref & 0x1FFFFFFFu), n = (int)((ref >> 29) & 3u) + 1;
             for (int k = first; k < first + n; ++k) {
                 const float4 p0 = ldg_keep(&s.tris[3 * k]);
@@ -340,6 +391,7 @@ __device__ __forceinline__ bool trace_any_simple(const DevScene &s, const RayT &
                 float t;
                 if (tri_hit(r, xyz(p0), xyz(p1), xyz(p2), t) && t < tmax) return true;
             }
+#endif
         }
         if (sp == 0) return false;
         --sp;
