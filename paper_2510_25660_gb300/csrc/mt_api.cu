@@ -1177,6 +1177,9 @@ mt_status mt_render_to_host(mt_scene s, mt_film f, int32_t spp, uint64_t seed, i
     cudaStream_t st = (cudaStream_t)stream, cp = (cudaStream_t)copy_stream;
     MT_CHECK_ARG(cp != st, "copy_stream must differ from stream");
     if (n_bands > s->so_cap) {
+        // no capacity until every buffer below exists again, so a call after a failed
+        // allocation here grows them anew instead of using a released host flag array
+        s->so_cap = 0;
         auto &al = s->al;
         MT_TRY(al.alloc(&s->so_done, n_bands, "streamed output"));
         MT_TRY(al.alloc(&s->so_mark, n_bands, "streamed output"));
