@@ -124,13 +124,21 @@ def tune(scene, kind, sc, film, spp, depth, run, candidates, reps=3, budget_s=60
     return best
 
 
+TILES = (1, 2, 4, 8, 16)          # pixels per warp tile (renders) or scan rows per CTA tile (NLOS)
+PATHS_PER_THREAD = (1, 2, 4, 8, 0)  # wavefront form; 0 = the default pool (about 13 paths per thread)
+CTAS_PER_SM = (0, 4)              # 0 = as many as fit (occupancy), else a cap on resident CTAs per SM
+
+
 def candidates(kind, film_T, wavefront_only=False):
-    """The search space: for NLOS threads x scan rows per CTA tile x
-    privatisation (all bins / none) x warp-aggregated atomics; for renders
-    the persistent kernel's threads x pixels per warp tile x privatisation
-    depth (all that fit, none, T/4, T/2) x options (aggregation, deferred
-    refill), and the wavefront form at 1, 2, 4 and 8 paths per thread and
-    the default pool."""
+    """The search space, as (threads, tile, ctas_per_sm, priv_bins, options[,
+    paths_per_thread]) tuples.  NLOS: threads x scan rows per CTA tile x
+    CTAs per SM x privatisation (all bins / none) x warp-aggregated atomics.
+    Renders: first the wavefront form at 1, 2, 4 and 8 paths per thread and
+    the default pool (so that a time budget never cuts off the form that wins
+    on large workloads), then the persistent kernel's threads x pixels per
+    warp tile x CTAs per SM x privatisation depth (all that fit, none, T/4,
+    T/2) x options (aggregation, deferred refill).  Tiles or depths whose
+    shared memory does not fit fail to launch and are skipped by `tune`."""
     return _candidates(kind, film_T, wavefront_only)
 
 
@@ -138,19 +146,21 @@ def _candidates(kind, film_T, wavefront_only=False):
     out = []
     if kind == "nlos":
         for threads in (128, 256):
-            for tile in (1, 2, 4):
-                for priv in (-1, 0):
-                    for opt in (0, 1):
-                        out.append((threads, tile, 0, priv, opt))
+            for tile in TILES:
+                for cps in CTAS_PER_SM:
+                    for priv in (-1, 0):
+                        for opt in (0, 1):
+                            out.append((threads, tile, cps, priv, opt))
         return out
+    for ppt in PATHS_PER_THREAD:
+        out.append((256, 1, 0, 0, 4, ppt))
     if not wavefront_only:
         for threads in (128, 256):
-            for tile in (1, 2):
-                for priv in (-1, 0, film_T // 4, film_T // 2):
-                    for opt in (0, 1, 16 << 8):
-                        out.append((threads, tile, 0, priv, opt, 0))
-    for ppt in (1, 2, 4, 8, 0):  # wavefront form; 0 = the default pool (about 13 paths per thread)
-        out.append((256, 1, 0, 0, 4, ppt))
+            for tile in TILES:
+                for cps in CTAS_PER_SM:
+                    for priv in (-1, 0, film_T // 4, film_T // 2):
+                        for opt in (0, 1, 16 << 8):
+                            out.append((threads, tile, cps, priv, opt, 0))
     return out
 
 
