@@ -143,15 +143,30 @@ def _stream(stream=None):
 def _ptr(t):
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
 def _hptr(t):
     if t is None:
         return None
-    assert not t.is_cuda and t.is_contiguous() and t.dtype == torch_float32(), "expected a contiguous host float32 tensor"
+    if t.is_cuda or not t.is_contiguous() or t.dtype != torch_float32():
+        raise ValueError("expected a contiguous host float32 tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def _check_f32(tensors):
+    """The library writes `numel` float32 values through each (tensor, numel,
+    name)'s pointer: dtypes and sizes first, then memory."""
+    for t, numel, what in tensors:
+        if t.dtype != torch_float32():
+            raise ValueError(f"{what} must be float32, not {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{what} holds {t.numel()} values where the film needs {numel}")
+    for t, _, what in tensors:
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{what} must be a contiguous CUDA tensor")
 
 
 def torch_float32():
@@ -335,7 +350,8 @@ class Scene:
         """Per-triangle exponential scattering-delay means (metres), a device
         float32 tensor [n_tris] (copied); None removes them."""
         if tau is not None:
-            assert tau.is_cuda and tau.dtype.is_floating_point and tau.numel() == self.n_tris
+            if not (tau.is_cuda and tau.dtype.is_floating_point and tau.numel() == self.n_tris):
+                raise ValueError(f"delays must be a floating-point CUDA tensor of {self.n_tris} values")
             tau = tau.float().contiguous()
         mt_scene_set_delays(self.h, _ptr(tau) if tau is not None else None, _stream(stream))
 
@@ -376,9 +392,11 @@ class Film:
     """A film handle over caller-owned torch tensors."""
 
     def __init__(self, film, steady, start, width, flags=0, C_=None, window=None):
+        if film.dim() < (4 if C_ is None else 3):
+            raise ValueError(f"film must be [H, W, T, C], not {tuple(film.shape)}")
         H, W, T = film.shape[:3]
         Cc = film.shape[3] if C_ is None else C_
-        assert C_ is None or film[0, 0, 0].numel() == C_
+        _check_f32([(film, H * W * T * Cc, "film")] + ([] if steady is None else [(steady, H * W * Cc, "steady image")]))
         self.film, self.steady = film, steady
         h = C.c_void_p()
         mt_film_create(H, W, T, Cc, float(start), float(width), _ptr(film), _ptr(steady), int(flags), C.byref(h))
