@@ -156,14 +156,16 @@ def _hptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _check_f32(tensors):
-    """The library writes `numel` float32 values through each (tensor, numel,
-    name)'s pointer: dtypes and sizes first, then memory."""
+def _check_f32(tensors, at_least=False):
+    """The library reads or writes `numel` float32 values through each
+    (tensor, numel, name)'s pointer (None tensors are skipped): dtypes and
+    sizes first, then memory.  at_least: larger tensors are accepted."""
+    tensors = [x for x in tensors if x[0] is not None]
     for t, numel, what in tensors:
         if t.dtype != torch_float32():
             raise ValueError(f"{what} must be float32, not {t.dtype}")
-        if t.numel() != numel:
-            raise ValueError(f"{what} holds {t.numel()} values where the film needs {numel}")
+        if t.numel() < numel if at_least else t.numel() != numel:
+            raise ValueError(f"{what} holds {t.numel()} values where {numel} are needed")
     for t, _, what in tensors:
         if not (t.is_cuda and t.is_contiguous()):
             raise ValueError(f"{what} must be a contiguous CUDA tensor")
@@ -337,6 +339,9 @@ class Scene:
             self.h = None
 
     def set_params(self, albedo=None, radiance=None, medium_albedo=None, stream=None):
+        """Albedos [n_tris, 3], radiances [n_em, 3], medium albedo [1]: float32 CUDA tensors or None."""
+        _check_f32([(albedo, 3 * self.n_tris, "albedo"), (radiance, 3 * self.n_em, "radiance"),
+                    (medium_albedo, 1, "medium albedo")])
         mt_scene_set_params(self.h, _ptr(albedo), _ptr(radiance), _ptr(medium_albedo), _stream(stream))
 
     def stats(self) -> dict:
@@ -467,6 +472,7 @@ def render_tangent(scene: Scene, H, W, T, start, width, spp, seed, max_depth, da
     f = Film(film, steady, start, width, flags)
     da = None if dalbedo is None else dalbedo.float().contiguous()
     dr = None if dradiance is None else dradiance.float().contiguous()
+    _check_f32([(da, 3 * scene.n_tris, "albedo tangent"), (dr, 3 * scene.n_em, "radiance tangent")])
     mt_render_tangent(scene.h, f.h, _ptr(da), _ptr(dr), float(dmedium), spp, seed, max_depth, sample_offset,
                       _stream(stream))
     return film, steady
@@ -497,6 +503,9 @@ def render_backward(scene: Scene, T, start, width, spp, seed, max_depth, grad_fi
                torch.zeros(1, dtype=torch.float32, device="cuda"))
     galb, grad, gmed = out
     f = Film(grad_film, None, start, width, flags)
+    _check_f32([(grad_steady, H * W * 3, "steady-image gradient")])
+    _check_f32([(galb, 3 * scene.n_tris, "albedo gradient"), (grad, 3 * scene.n_em, "radiance gradient"),
+                (gmed, 1, "medium-albedo gradient")], at_least=True)
     mt_render_backward(scene.h, f.h, _ptr(grad_film), _ptr(grad_steady), spp, seed, max_depth, sample_offset,
                        _ptr(galb), _ptr(grad), _ptr(gmed), _stream(stream))
     del H, W

@@ -36,3 +36,23 @@ def test_pointer_helpers_refuse_the_wrong_memory():
     with pytest.raises(ValueError, match="host float32"):
         api._hptr(torch.zeros((4, 4)).t())
     assert api._hptr(torch.zeros(4)).value != 0
+
+
+def test_parameter_buffers_are_checked_before_the_library():
+    import types
+    scene = types.SimpleNamespace(n_tris=5, n_em=2, h=None)
+    with pytest.raises(ValueError, match="albedo must be float32"):
+        api.Scene.set_params(scene, albedo=torch.zeros((5, 3), dtype=torch.float64))
+    with pytest.raises(ValueError, match="albedo holds 12 values where 15"):
+        api.Scene.set_params(scene, albedo=torch.zeros((4, 3)))
+    with pytest.raises(ValueError, match="radiance holds 3 values where 6"):
+        api.Scene.set_params(scene, radiance=torch.zeros((1, 3)))
+    with pytest.raises(ValueError, match="medium albedo holds"):
+        api.Scene.set_params(scene, medium_albedo=torch.zeros(2))
+    with pytest.raises(ValueError, match="CUDA"):
+        api.Scene.set_params(scene, albedo=torch.zeros((5, 3)), radiance=torch.zeros((2, 3)))
+    # larger gradient accumulators are accepted, smaller ones are not
+    with pytest.raises(ValueError, match="gradient holds 2 values where 3"):
+        api._check_f32([(torch.zeros(2), 3, "gradient")], at_least=True)
+    with pytest.raises(ValueError, match="CUDA"):
+        api._check_f32([(torch.zeros(6), 3, "gradient"), (None, 9, "skipped")], at_least=True)
