@@ -513,6 +513,13 @@ def render_backward(scene: Scene, T, start, width, spp, seed, max_depth, grad_fi
 
 
 def make_scan(lasers, sensors, mode, wall_normal, wall_albedo, hidden):
+    """Scan grid of laser (and, for EXHAUSTIVE grids, sensor) points on the relay
+    wall: float32 CUDA tensors [n, 3]."""
+    for t, what in ((lasers, "laser points"), (sensors, "sensor points")):
+        if t is not None and (t.dim() != 2 or t.shape[1] != 3):
+            raise ValueError(f"{what} must be [n, 3], not {tuple(t.shape)}")
+    _check_f32([(lasers, 3 * lasers.shape[0], "laser points"),
+                (sensors, 3 * sensors.shape[0] if sensors is not None else 0, "sensor points")])
     return mt_scan(_ptr(lasers), int(lasers.shape[0]), _ptr(sensors) if sensors is not None else None,
                    int(sensors.shape[0]) if sensors is not None else 0, int(mode), _f3(wall_normal),
                    float(wall_albedo), int(hidden[0]), int(hidden[1]))

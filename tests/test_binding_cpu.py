@@ -56,3 +56,14 @@ def test_parameter_buffers_are_checked_before_the_library():
         api._check_f32([(torch.zeros(2), 3, "gradient")], at_least=True)
     with pytest.raises(ValueError, match="CUDA"):
         api._check_f32([(torch.zeros(6), 3, "gradient"), (None, 9, "skipped")], at_least=True)
+
+
+def test_scan_points_are_checked_before_the_library():
+    wall = dict(normal=(0.0, 0.0, 1.0), albedo=0.8)
+    with pytest.raises(ValueError, match=r"laser points must be \[n, 3\]"):
+        api.make_scan(torch.zeros((4, 2)), None, api.MT_CONFOCAL, wall["normal"], wall["albedo"], (0, 1))
+    with pytest.raises(ValueError, match="sensor points must be float32"):
+        api.make_scan(torch.zeros((4, 3)), torch.zeros((2, 3), dtype=torch.float64), api.MT_EXHAUSTIVE,
+                      wall["normal"], wall["albedo"], (0, 1))
+    with pytest.raises(ValueError, match="CUDA"):
+        api.make_scan(torch.zeros((4, 3)), None, api.MT_CONFOCAL, wall["normal"], wall["albedo"], (0, 1))
