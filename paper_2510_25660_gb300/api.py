@@ -441,6 +441,10 @@ def render_to_host(scene: Scene, H, W, T, start, width, spp, seed, max_depth, ho
     tensors host_film [H,W,T,3] / host_steady [H,W,3] on copy_stream as the
     bands finish; synchronise copy_stream before reading them."""
     film, steady = out if out is not None else new_film(H, W, T, 3)
+    # the library copies the whole film and steady image into these host buffers
+    for h, d, what in ((host_film, film, "host film"), (host_steady, steady, "host steady image")):
+        if h is not None and d is not None and h.numel() != d.numel():
+            raise ValueError(f"{what} holds {h.numel()} values where the film copies {d.numel()}")
     f = Film(film, steady, start, width, flags, window=window)
     mt_render_to_host(scene.h, f.h, spp, seed, max_depth, sample_offset, band_rows, _hptr(host_film),
                       _hptr(host_steady), _stream(stream), _stream(copy_stream))

@@ -67,3 +67,14 @@ def test_scan_points_are_checked_before_the_library():
                       wall["normal"], wall["albedo"], (0, 1))
     with pytest.raises(ValueError, match="CUDA"):
         api.make_scan(torch.zeros((4, 3)), None, api.MT_CONFOCAL, wall["normal"], wall["albedo"], (0, 1))
+
+
+def test_streamed_output_host_buffers_must_match_the_film():
+    H, W, T = 2, 3, 4
+    out = (torch.zeros((H, W, T, 3)), torch.zeros((H, W, 3)))
+    with pytest.raises(ValueError, match="host film holds 60 values where the film copies 72"):
+        api.render_to_host(None, H, W, T, 0.0, 1.0, 1, 1, 1, torch.zeros((H - 1, W + 2, T, 3)),
+                           torch.zeros((H, W, 3)), 1, None, out=out)
+    with pytest.raises(ValueError, match="host steady image holds"):
+        api.render_to_host(None, H, W, T, 0.0, 1.0, 1, 1, 1, torch.zeros((H, W, T, 3)), torch.zeros((H, W, 1)),
+                           1, None, out=out)
