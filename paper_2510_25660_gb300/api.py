@@ -650,7 +650,14 @@ def _autograd():
     return TransientRender
 
 
+_transient_render = None
+
+
 def __getattr__(name):
+    # built on first use, so that importing the binding does not import torch
+    global _transient_render
     if name == "TransientRender":
-        return _autograd()
+        if _transient_render is None:
+            _transient_render = _autograd()
+        return _transient_render
     raise AttributeError(name)

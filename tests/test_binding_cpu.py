@@ -78,3 +78,10 @@ def test_streamed_output_host_buffers_must_match_the_film():
     with pytest.raises(ValueError, match="host steady image holds"):
         api.render_to_host(None, H, W, T, 0.0, 1.0, 1, 1, 1, torch.zeros((H, W, T, 3)), torch.zeros((H, W, 1)),
                            1, None, out=out)
+
+
+def test_autograd_function_is_one_class():
+    assert api.TransientRender is api.TransientRender
+    assert issubclass(api.TransientRender, torch.autograd.Function)
+    with pytest.raises(AttributeError):
+        api.NoSuchName
