@@ -313,7 +313,7 @@ def perturbed_albedo(scene: Scene, seed: int = TARGET_SEED, amount: float = 0.2)
 
 def nlos_scene(seed: int = SCENE_SEED) -> Scene:
     """1x1 m relay wall at z=0 facing +z (albedo 0.8) and a hidden ~49k-triangle
-    mesh 0.5-1.5 m in front of it: two bumpy level-5 icospheres and an extruded
+    mesh 0.54-1.52 m in front of it: two bumpy level-5 icospheres and an extruded
     8-point star."""
     rng = np.random.default_rng(seed)
     wall = quad((-0.5, -0.5, 0.0), (0.5, -0.5, 0.0), (0.5, 0.5, 0.0), (-0.5, 0.5, 0.0))
